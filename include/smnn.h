@@ -1,0 +1,173 @@
+/*
+ * smnn.h -- C ABI of libsmnn, the batched linear-time solve of the reformulated
+ * Mechanistic Neural Network layer (Scalable Mechanistic Neural Networks,
+ * Chen et al., ICLR 2025), with hand-written CUDA kernels for sm_103a.
+ *
+ * The problem (Sec. 3.1).  A *system* is one (sequence b, dimension dd) pair with
+ * V = Q = 1: T steps, R+1 unknowns y_{t,0..R} per step (the value and its first R
+ * derivatives), and the weighted least-squares problem
+ *     y = argmin || W^{1/2} (A y - b) ||^2,   i.e.  M y = beta,  M = A^T W A   (Eq. 9)
+ * built from one governing row per step (Eq. 4: sum_r c_{t,r} y_{t,r} = d_t), the
+ * initial-value rows (Eq. 5: y_{t,r} = u_{t,r}, t <= T_init, r <= R_init) and the
+ * forward/backward Taylor smoothness rows between adjacent steps (Eq. 6-7, weight
+ * (w_smooth s_t^r)^2).  With the unknowns ordered by step (Sec. 3.2, Eq. m_partition)
+ * M is symmetric positive definite and block tridiagonal with (R+1)x(R+1) blocks:
+ * M_t on the diagonal and N_t at block (t+1, t); M_t, N_t and beta_t have the closed
+ * forms of App. A.2.  The library never forms A.
+ *
+ * Layouts (all arrays row-major, contiguous, caller-owned DEVICE memory unless stated):
+ *   uniform batch (desc.seq_T == NULL), S = B*D systems, system i = b*D + dd:
+ *     c  [B][D][T][R+1]   coefficients c_{t,r} of Eq. 4
+ *     d  [B][D][T]        right-hand sides d_t of Eq. 4
+ *     s  [B][T]           step sizes s_t (Eq. 6-7), shared by the D systems of a
+ *                         sequence; s[b][T-1] is unused
+ *     u  [B][D][T_init][R_init+1]   initial values of Eq. 5
+ *     y  [B][D][T][R+1]   solution (same layout as c)
+ *   ragged batch (desc.seq_T = per-sequence step counts T_b): the D systems of
+ *     sequence b are stored one after another, system i = b*D + dd starting at
+ *     step D*(T_0+...+T_{b-1}) + dd*T_b of c, d, y (c and y hold R+1 values per
+ *     step); s holds T_0+...+T_{B-1} entries, sequence b starting at T_0+...+T_{b-1};
+ *     u is [S][T_init][R_init+1].
+ *   Element type: float for SMNN_F32_REFINED and SMNN_F32, double for SMNN_F64.
+ *
+ * Streams: every compute call is asynchronous and ordered on the given stream
+ * (a cudaStream_t passed as void*; NULL = legacy default stream); it allocates
+ * nothing and does not synchronise.  Host return codes report argument, workspace
+ * and launch errors only.  Numerical failures go to the device array info[S]
+ * (int32): 0 ok; k > 0: a non-positive pivot was met at (1-based) step k of that
+ * system, and its outputs are NaN; -1: the refinement stop test
+ * (desc.refine_tol > 0) failed after the last sweep.
+ */
+#ifndef SMNN_H_
+#define SMNN_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Largest derivative order the kernels are compiled for (R+1 <= 4 unknowns/step). */
+#define SMNN_MAX_R 3
+
+typedef enum {
+  SMNN_OK = 0,
+  SMNN_ERR_INVALID_ARG = 1,   /* a pointer, size or parameter is out of range      */
+  SMNN_ERR_WORKSPACE = 2,     /* workspace/factor buffer missing or misaligned     */
+  SMNN_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed       */
+  SMNN_ERR_UNSUPPORTED = 4    /* valid request the library does not implement     */
+} smnn_status;
+
+typedef enum {
+  /* FP32 factorisation and substitution, accuracy won back by max_refine sweeps of
+   * iterative refinement whose residual r = beta - M y is evaluated in FP64 from the
+   * FP32 inputs (float arrays). */
+  SMNN_F32_REFINED = 0,
+  SMNN_F32 = 1,   /* FP32 factorisation and substitution only (float arrays)         */
+  SMNN_F64 = 2    /* plain FP64 block Cholesky of the same method (double arrays)    */
+} smnn_precision;
+
+typedef enum {
+  SMNN_ALGO_AUTO = 0,  /* autotuner table picks the level structure per (T, S, R)   */
+  SMNN_ALGO_SEQ = 1,   /* one sequential block-Cholesky sweep per system (Alg. 3, 4) */
+  SMNN_ALGO_CR = 2     /* chunked block cyclic reduction, parallel over T           */
+} smnn_algo;
+
+typedef struct smnn_desc {
+  int32_t R;              /* highest derivative order, 1..SMNN_MAX_R                */
+  int32_t R_init;         /* initial values for orders 0..R_init, 0 <= R_init <= R  */
+  int32_t T_init;         /* initial values for steps 1..T_init, 1 <= T_init <= T_b */
+  int32_t precision;      /* smnn_precision                                         */
+  int32_t algo;           /* smnn_algo                                              */
+  int32_t max_refine;     /* refinement sweeps for SMNN_F32_REFINED, 0..16          */
+  int32_t chunk;          /* level-0 chunk length for SMNN_ALGO_CR, 0 = autotuned   */
+  int32_t reserved0;      /* must be 0                                              */
+  double w_gov;           /* importance weights of Eq. 9 (unsquared; W holds their  */
+  double w_init;          /*   squares, App. A.1), >= 0                             */
+  double w_smooth;
+  double refine_tol;      /* > 0: info = -1 where the last sweep's ||dy||/||y|| > tol */
+  int64_t num_seq;        /* B >= 1                                                 */
+  int64_t dims_per_seq;   /* D >= 1                                                 */
+  int64_t T;              /* steps per sequence (uniform batch; ignored if seq_T)   */
+  const int64_t* seq_T;   /* HOST pointer to B step counts (ragged), or NULL; read  */
+                          /* only during smnn_plan_create                           */
+} smnn_desc;
+
+typedef struct smnn_plan_s* smnn_plan;
+
+typedef struct smnn_plan_stats {
+  int64_t num_systems;    /* S = B*D                                                */
+  int64_t total_steps;    /* sum over systems of T_i                                */
+  int32_t num_levels;     /* reduction levels of the solve (1 = sequential)         */
+  int32_t chunk[8];       /* chunk length per level                                 */
+  int32_t kernels_per_solve;
+  size_t workspace_bytes; /* as smnn_workspace_size                                 */
+  size_t factor_bytes;
+} smnn_plan_stats;
+
+/* Validate desc and build a plan: the level structure of the chunked reduction
+ * and its small device index tables.  This is the only call that allocates (device
+ * memory for the tables).  Returns SMNN_ERR_INVALID_ARG for out-of-range fields,
+ * SMNN_ERR_CUDA if the tables cannot be allocated.  The plan is bound to the device
+ * current at creation. */
+smnn_status smnn_plan_create(const smnn_desc* desc, smnn_plan* plan);
+
+/* Free a plan and its tables (synchronises the device first). NULL is a no-op. */
+smnn_status smnn_plan_destroy(smnn_plan plan);
+
+/* Level structure and buffer sizes of a plan (host call, no GPU work). */
+smnn_status smnn_plan_get_stats(smnn_plan plan, smnn_plan_stats* stats);
+
+/* Bytes of device workspace the compute calls need (workspace_bytes, 256-byte
+ * aligned base required), and the bytes of the optional saved factor (the Cholesky
+ * blocks L_t of Sec. 3.2 Eq. 11-12 in the plan's chunked order, with the fill
+ * blocks and reduced blocks of the reduction) that smnn_factor_solve can leave for
+ * smnn_backward. */
+smnn_status smnn_workspace_size(smnn_plan plan, size_t* workspace_bytes, size_t* factor_bytes);
+
+/* App. A.2: materialise M_t (lower triangle packed row by row: M_00, M_10, M_11,
+ * M_20, ..., (R+1)(R+2)/2 values), N_t (block (t+1,t), (R+1)^2 values row-major,
+ * zero for the last step of a system) and beta_t (R+1 values) for every step, laid
+ * out per step like y.  Testing and inspection aid; the solver forms these blocks
+ * in registers. */
+smnn_status smnn_assemble(smnn_plan plan, const void* c, const void* d, const void* s,
+                          const void* u, void* M, void* N, void* beta, void* stream);
+
+/* Forward pass (Alg. 1: Decompose, Alg. 3, then Substitute, Alg. 4, in the chunked
+ * cyclic-reduction order of the plan), fused with the assembly of App. A.2, plus
+ * max_refine refinement sweeps for SMNN_F32_REFINED.  Writes y and info.
+ * factor: NULL, or a factor_bytes buffer (256-byte aligned) that receives the factor
+ * for smnn_backward.  workspace: workspace_bytes of device scratch (256-byte aligned). */
+smnn_status smnn_factor_solve(smnn_plan plan, const void* c, const void* d, const void* s,
+                              const void* u, void* y, void* factor, int32_t* info,
+                              void* workspace, void* stream);
+
+/* Backward pass (Alg. 2 and Eq. 14): g = M^{-1} dl/dy with the same factor (refined
+ * like the forward pass), then the parameter gradients, fused per step as the chain
+ * rule through App. A.2's assembly:
+ *   gd_t = w_gov^2 c_t.g_t,   gc_t = w_gov^2 [(d_t - c_t.y_t) g_t - (c_t.g_t) y_t],
+ *   gu_{t,r} = w_init^2 g_{t,r},
+ *   gs_t = -w_smooth^2 d/ds_t sum_r s_t^{2r} (f+_r e+_r + f-_r e-_r), summed over the
+ *          D systems of the sequence, with e+ = exp(s_t N) y_t - y_{t+1},
+ *          e- = exp(-s_t N) y_{t+1} - y_t (f+- likewise on g, N the nilpotent shift);
+ *          gs of the last step of a sequence is 0.
+ * y: the forward solution; gy: dl/dy (layout of y).  factor: the buffer filled by
+ * smnn_factor_solve with the same inputs, or NULL to recompute the factor into the
+ * workspace.  Outputs gc, gd, gs, gu have the layouts of c, d, s, u. */
+smnn_status smnn_backward(smnn_plan plan, const void* c, const void* d, const void* s,
+                          const void* u, const void* y, const void* factor, const void* gy,
+                          void* gc, void* gd, void* gs, void* gu, int32_t* info,
+                          void* workspace, void* stream);
+
+/* Static string for a status code. */
+const char* smnn_status_string(smnn_status status);
+
+/* Number of kernels this library has launched in this process (all devices). */
+uint64_t smnn_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMNN_H_ */

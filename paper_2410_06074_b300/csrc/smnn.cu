@@ -1,0 +1,981 @@
+// smnn.cu -- libsmnn: kernels (sm_103a), plans and the C ABI declared in include/smnn.h.
+//
+// Kernels (one thread per chunk of L consecutive steps of one system):
+//   k_elim0     level 0: assemble M_t, N_t, beta_t in registers from {c, d, u, s}
+//               (App. A.2) and eliminate the chunk interior (block Cholesky, Alg. 3, in
+//               chunked order), or replay a stored factor on a new right-hand side
+//   k_elimN     level >= 1: the same on the separators' Schur complement
+//   k_backsubN  levels >= 1, then k_backsub0: back substitution (Alg. 4), writing y
+//   k_residual  refinement residual r = beta - M y (or gy - M g), evaluated in FP64
+//               row by row (governing, initial and smoothness rows of Eq. 4-7)
+//   k_grad      parameter gradients from y and g = M^{-1} dl/dy (Eq. 14 chained through
+//               App. A.2), FP64 internally, summed over the D systems sharing s
+//   k_assemble  materialises M_t, N_t, beta_t (inspection/testing aid)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/smnn.h"
+#include "smnn_chunk.cuh"
+
+using namespace smnn;
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+constexpr int kThreads = 128;
+constexpr int kTopMax = 64;        // a level with at most this many steps per system is one chunk
+constexpr int kMaxLevels = 8;
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// ----------------------------------------------------------------------------- device helpers
+
+// info[i] = min over reported failures (0 = none yet); refinement flags (< 0) are kept.
+__device__ __forceinline__ void record_fail(int32_t* info, int32_t v) {
+  int32_t old = *reinterpret_cast<volatile int32_t*>(info);
+  while (old == 0 || (old > 0 && v < old)) {
+    const int32_t prev = atomicCAS(info, old, v);
+    if (prev == old) break;
+    old = prev;
+  }
+}
+
+struct LevelTables {
+  const int32_t* csys;  // [G] system of each chunk
+  const int64_t* coff;  // [S+1] first chunk of each system
+  const int64_t* P;     // [S] steps of each system at this level
+  const int64_t* base;  // [S] first step of each system at this level
+  int64_t G;
+  int L;
+  int64_t stride0;      // level-0 steps per step of this level
+};
+
+template <class Tr, int NB>
+struct LevelBufs {
+  FactorView<Tr, NB> fac;
+  ChunkOut<Tr, NB> out;
+  Tr* xsep;  // [G][NB] values at this level's separators (= the next level's unknowns)
+};
+
+struct Problem0 {  // level-0 inputs
+  const void* c;
+  const void* d;
+  const void* s;
+  const void* u;
+  const int64_t* soff;  // [S] offset of each system's step sizes
+  double wg2, wi2, ws2;
+  int T_init, R_init;
+};
+
+template <class Tr, int NB>
+__device__ __forceinline__ CoefSource<Tr, NB> make_coef(const Problem0& p, const Tr* rhs, int64_t i,
+                                                        int64_t base, int64_t T) {
+  CoefSource<Tr, NB> src;
+  src.c = static_cast<const Tr*>(p.c) + base * NB;
+  src.d = static_cast<const Tr*>(p.d) + base;
+  src.s = static_cast<const Tr*>(p.s) + p.soff[i];
+  src.u = static_cast<const Tr*>(p.u) + i * int64_t(p.T_init) * (p.R_init + 1);
+  src.rhs = rhs ? rhs + base * NB : nullptr;
+  src.T = T;
+  src.wg2 = Tr(p.wg2);
+  src.wi2 = Tr(p.wi2);
+  src.ws2 = Tr(p.ws2);
+  src.T_init = p.T_init;
+  src.R_init = p.R_init;
+  return src;
+}
+
+template <class Tr, int NB>
+__device__ __forceinline__ ReducedSource<Tr, NB> make_reduced(const ChunkOut<Tr, NB>& prev,
+                                                              int64_t base, int64_t P) {
+  constexpr int NT = NB * (NB + 1) / 2;
+  ReducedSource<Tr, NB> src;
+  src.a_right = prev.a_right + base * NT;
+  src.a_left = prev.a_left + base * NT;
+  src.e_coup = prev.e_coup + base * NB * NB;
+  src.b_right = prev.b_right + base * NB;
+  src.b_left = prev.b_left + base * NB;
+  src.P = P;
+  return src;
+}
+
+// ----------------------------------------------------------------------------- kernels
+
+__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+__global__ void k_fill_f64(double* p, int64_t n, double v) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+template <class Tr, int NB, bool kFactor, bool kTop>
+__global__ void __launch_bounds__(kThreads) k_elim0(LevelTables lt, LevelBufs<Tr, NB> lb, Problem0 p,
+                                                    const Tr* rhs, int32_t* info) {
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= lt.G) return;
+  const int64_t i = lt.csys[g];
+  const int64_t k = g - lt.coff[i];
+  const int64_t T = lt.P[i];
+  const int64_t first = k * lt.L;
+  const int64_t last = min(first + lt.L, T) - 1;
+  const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, rhs, i, lt.base[i], T);
+  int64_t fail = elim_chunk<Tr, NB, kFactor>(src, first, last, k > 0, lb.fac, g, lb.out);
+  if (kTop) {
+    if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = last + 1;
+  }
+  if (kFactor && fail) record_fail(info + i, int32_t(fail));
+}
+
+template <class Tr, int NB, bool kFactor, bool kTop>
+__global__ void __launch_bounds__(kThreads) k_elimN(LevelTables lt, LevelBufs<Tr, NB> lb,
+                                                    ChunkOut<Tr, NB> prev, const int64_t* T0,
+                                                    int32_t* info) {
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= lt.G) return;
+  const int64_t i = lt.csys[g];
+  const int64_t k = g - lt.coff[i];
+  const int64_t P = lt.P[i];
+  const int64_t first = k * lt.L;
+  const int64_t last = min(first + lt.L, P) - 1;
+  const ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[i], P);
+  int64_t fail = elim_chunk<Tr, NB, kFactor>(src, first, last, k > 0, lb.fac, g, lb.out);
+  if (kTop) {
+    if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = last + 1;
+  }
+  if (kFactor && fail) {  // report the level-0 step of the failing separator
+    const int64_t step0 = min(fail * lt.stride0, T0[i]);
+    record_fail(info + i, int32_t(step0));
+  }
+}
+
+// Emit functor of level >= 1 back substitution: values of this level's unknowns.
+template <class Tr, int NB>
+struct EmitX {
+  Tr* x;
+  __device__ void operator()(int64_t t, const Tr (&v)[NB]) const {
+#pragma unroll
+    for (int a = 0; a < NB; ++a) x[t * NB + a] = v[a];
+  }
+};
+
+template <class Tr, int NB>
+__global__ void __launch_bounds__(kThreads) k_backsubN(LevelTables lt, LevelBufs<Tr, NB> lb,
+                                                       ChunkOut<Tr, NB> prev, Tr* x_prev) {
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= lt.G) return;
+  const int64_t i = lt.csys[g];
+  const int64_t k = g - lt.coff[i];
+  const int64_t P = lt.P[i];
+  const int64_t first = k * lt.L;
+  const int64_t last = min(first + lt.L, P) - 1;
+  const ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[i], P);
+  EmitX<Tr, NB> emit{x_prev + lt.base[i] * NB};
+  backsub_chunk<Tr, NB>(src, first, last, k > 0, lb.fac, g, lb.xsep + g * NB,
+                        k > 0 ? lb.xsep + (g - 1) * NB : nullptr, emit);
+}
+
+// Emit functor of level-0 back substitution: y (or y += dy), NaN for failed systems,
+// and optionally the squared norms of dy and y for the refinement stop test.
+template <class Tr, int NB, bool kAccum>
+struct EmitY {
+  Tr* y;
+  bool failed;
+  double dd, yy;
+  __device__ void operator()(int64_t t, const Tr (&v)[NB]) {
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      Tr out = v[a];
+      if (kAccum) {
+        const Tr yo = y[t * NB + a];
+        out = yo + v[a];
+        dd += double(v[a]) * double(v[a]);
+        yy += double(out) * double(out);
+      }
+      y[t * NB + a] = failed ? nan_t<Tr>() : out;
+    }
+  }
+};
+
+template <class Tr, int NB, bool kAccum>
+__global__ void __launch_bounds__(kThreads) k_backsub0(LevelTables lt, LevelBufs<Tr, NB> lb,
+                                                       Problem0 p, Tr* y, const int32_t* info,
+                                                       double* nrm) {
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= lt.G) return;
+  const int64_t i = lt.csys[g];
+  const int64_t k = g - lt.coff[i];
+  const int64_t T = lt.P[i];
+  const int64_t first = k * lt.L;
+  const int64_t last = min(first + lt.L, T) - 1;
+  const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, nullptr, i, lt.base[i], T);
+  EmitY<Tr, NB, kAccum> emit{y + lt.base[i] * NB, info[i] > 0, 0.0, 0.0};
+  backsub_chunk<Tr, NB>(src, first, last, k > 0, lb.fac, g, lb.xsep + g * NB,
+                        k > 0 ? lb.xsep + (g - 1) * NB : nullptr, emit);
+  if (kAccum && nrm) {
+    atomicAdd(nrm + 2 * i, emit.dd);
+    atomicAdd(nrm + 2 * i + 1, emit.yy);
+  }
+}
+
+__global__ void k_refine_check(const double* nrm, int64_t S, double tol, int32_t* info) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= S) return;
+  const double dd = nrm[2 * i], yy = nrm[2 * i + 1];
+  if (info[i] == 0 && !(dd <= tol * tol * yy)) info[i] = -1;
+}
+
+// ---- FP64 residual of the refinement ------------------------------------------------
+// (P v)_r = sum_k coef[k] v_{r+k},  (P^T v)_r = sum_k coef[k] v_{r-k},  coef[k] = (+-s)^k/k!
+template <int NB>
+__device__ __forceinline__ void taylor_fw(const double (&cf)[NB], const double (&v)[NB], double (&o)[NB]) {
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    double acc = v[NB - 1] * cf[NB - 1 - r];
+#pragma unroll
+    for (int q = NB - 2; q >= r; --q) acc = fma(cf[q - r], v[q], acc);
+    o[r] = acc;
+  }
+}
+template <int NB>
+__device__ __forceinline__ void taylor_tr(const double (&cf)[NB], const double (&v)[NB], double (&o)[NB]) {
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    double acc = v[0] * cf[r];
+#pragma unroll
+    for (int q = 1; q <= r; ++q) acc = fma(cf[r - q], v[q], acc);
+    o[r] = acc;
+  }
+}
+
+// Contributions of the 2(R+1) smoothness rows between steps t and t+1 (Eq. 6-7, weights
+// w_r = w_s^2 s^{2r}) to -(M x)_t and -(M x)_{t+1}: with e+ = exp(sN) x_t - x_{t+1} and
+// e- = exp(-sN) x_{t+1} - x_t (the rows' values),
+//   -(M x)_t     += w.e- - exp(sN)^T (w.e+),   -(M x)_{t+1} += w.e+ - exp(-sN)^T (w.e-).
+template <int NB>
+__device__ __forceinline__ void smooth_pair_residual(double s, double ws2, const double (&xa)[NB],
+                                                     const double (&xb)[NB], double (&ra)[NB],
+                                                     double (&rb)[NB]) {
+  double cp[NB], cm[NB], w[NB];
+  cp[0] = 1.0; cm[0] = 1.0;
+  double pk = 1.0;
+#pragma unroll
+  for (int k = 1; k < NB; ++k) {
+    pk *= s;
+    cp[k] = pk * inv_fact(k);
+    cm[k] = (k & 1) ? -cp[k] : cp[k];
+  }
+  w[0] = ws2;
+  const double s2 = s * s;
+#pragma unroll
+  for (int r = 1; r < NB; ++r) w[r] = w[r - 1] * s2;
+  double pa[NB], qb[NB], vp[NB], vm[NB], tp[NB], tm[NB];
+  taylor_fw<NB>(cp, xa, pa);
+  taylor_fw<NB>(cm, xb, qb);
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    vp[r] = w[r] * (pa[r] - xb[r]);
+    vm[r] = w[r] * (qb[r] - xa[r]);
+  }
+  taylor_tr<NB>(cp, vp, tp);
+  taylor_tr<NB>(cm, vm, tm);
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    ra[r] = vm[r] - tp[r];
+    rb[r] = vp[r] - tm[r];
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kThreads) k_residual(LevelTables lt, Problem0 p, const float* x,
+                                                       const float* rhs, float* r_out) {
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= lt.G) return;
+  const int64_t i = lt.csys[g];
+  const int64_t k = g - lt.coff[i];
+  const int64_t T = lt.P[i];
+  const int64_t first = k * lt.L;
+  const int64_t last = min(first + lt.L, T) - 1;
+  const int64_t base = lt.base[i];
+  const float* c = static_cast<const float*>(p.c) + base * NB;
+  const float* d = static_cast<const float*>(p.d) + base;
+  const float* s = static_cast<const float*>(p.s) + p.soff[i];
+  const float* u = static_cast<const float*>(p.u) + i * int64_t(p.T_init) * (p.R_init + 1);
+  const float* xs = x + base * NB;
+  const float* rh = rhs ? rhs + base * NB : nullptr;
+  float* ro = r_out + base * NB;
+
+  double xc[NB], carry[NB];
+#pragma unroll
+  for (int a = 0; a < NB; ++a) { xc[a] = double(xs[first * NB + a]); carry[a] = 0.0; }
+  if (first > 0) {
+    double xp[NB], dummy[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) xp[a] = double(xs[(first - 1) * NB + a]);
+    smooth_pair_residual<NB>(double(s[first - 1]), p.ws2, xp, xc, dummy, carry);
+  }
+  for (int64_t t = first; t <= last; ++t) {
+    double r[NB], cv[NB];
+    double cx = 0.0;
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      cv[a] = double(c[t * NB + a]);
+      cx = fma(cv[a], xc[a], cx);
+    }
+    if (rh) {
+      const double gres = -p.wg2 * cx;  // beta replaced by the explicit right-hand side
+#pragma unroll
+      for (int a = 0; a < NB; ++a) r[a] = fma(gres, cv[a], double(rh[t * NB + a])) + carry[a];
+    } else {
+      const double gres = p.wg2 * (double(d[t]) - cx);  // w_g^2 c_t (d_t - c_t . x_t)
+#pragma unroll
+      for (int a = 0; a < NB; ++a) r[a] = fma(gres, cv[a], carry[a]);
+    }
+    if (t < p.T_init) {
+#pragma unroll
+      for (int a = 0; a < NB; ++a)
+        if (a <= p.R_init)
+          r[a] += p.wi2 * ((rh ? 0.0 : double(u[t * (p.R_init + 1) + a])) - xc[a]);
+    }
+    if (t + 1 < T) {
+      double xn[NB], ra[NB];
+#pragma unroll
+      for (int a = 0; a < NB; ++a) xn[a] = double(xs[(t + 1) * NB + a]);
+      smooth_pair_residual<NB>(double(s[t]), p.ws2, xc, xn, ra, carry);
+#pragma unroll
+      for (int a = 0; a < NB; ++a) { r[a] += ra[a]; xc[a] = xn[a]; }
+    }
+#pragma unroll
+    for (int a = 0; a < NB; ++a) ro[t * NB + a] = float(r[a]);
+  }
+}
+
+// ---- parameter gradients ----------------------------------------------------------------
+struct GradTables {
+  const int32_t* sq_b;      // [Q] sequence of each sequence-chunk
+  const int32_t* sq_k;      // [Q] chunk index within the sequence
+  const int64_t* sys_base;  // [S] level-0 step base of each system
+  const int64_t* sys_T;     // [S]
+  const int64_t* seq_soff;  // [B] offset of each sequence's step sizes
+  int64_t Q;
+  int L;
+  int D;
+};
+
+// -w_s^2 d/ds sum_r s^{2r} (f+_r e+_r + f-_r e-_r) for the pair (t, t+1), g and y held fixed.
+template <int NB>
+__device__ __forceinline__ double smooth_pair_grad(double s, double ws2, const double (&ya)[NB],
+                                                   const double (&yb)[NB], const double (&ga)[NB],
+                                                   const double (&gb)[NB]) {
+  double cp[NB], cm[NB];
+  cp[0] = 1.0; cm[0] = 1.0;
+  double pk = 1.0;
+#pragma unroll
+  for (int k = 1; k < NB; ++k) {
+    pk *= s;
+    cp[k] = pk * inv_fact(k);
+    cm[k] = (k & 1) ? -cp[k] : cp[k];
+  }
+  double pya[NB], pga[NB], qyb[NB], qgb[NB];
+  taylor_fw<NB>(cp, ya, pya);
+  taylor_fw<NB>(cp, ga, pga);
+  taylor_fw<NB>(cm, yb, qyb);
+  taylor_fw<NB>(cm, gb, qgb);
+  double acc = 0.0;
+  double s2r = 1.0;     // s^{2r}
+  double ds2r = 0.0;    // d/ds s^{2r} = 2r s^{2r-1}
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    const double ep = pya[r] - yb[r], fp = pga[r] - gb[r];
+    const double em = qyb[r] - ya[r], fm = qgb[r] - ga[r];
+    // d/ds exp(+-sN) v = +-N exp(+-sN) v: component r takes component r+1
+    const double dep = r + 1 < NB ? pya[r + 1] : 0.0, dfp = r + 1 < NB ? pga[r + 1] : 0.0;
+    const double dem = r + 1 < NB ? -qyb[r + 1] : 0.0, dfm = r + 1 < NB ? -qgb[r + 1] : 0.0;
+    acc += ds2r * (fp * ep + fm * em) + s2r * (dfp * ep + fp * dep + dfm * em + fm * dem);
+    ds2r = (2.0 * r + 2.0) * s2r * s;
+    s2r *= s * s;
+  }
+  return -ws2 * acc;
+}
+
+template <class Tr, int NB>
+__global__ void __launch_bounds__(kThreads) k_grad(GradTables gt, Problem0 p, const Tr* y, const Tr* gv,
+                                                   const int32_t* info, Tr* gc, Tr* gd, Tr* gs, Tr* gu) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= gt.Q) return;
+  const int64_t b = gt.sq_b[q];
+  const int64_t kc = gt.sq_k[q];
+  const int64_t i0 = b * gt.D;
+  const int64_t T = gt.sys_T[i0];
+  const int64_t first = kc * gt.L;
+  const int64_t last = min(first + gt.L, T) - 1;
+  const Tr* s = static_cast<const Tr*>(p.s) + gt.seq_soff[b];
+  Tr* gso = gs + gt.seq_soff[b];
+  const int nu = p.T_init * (p.R_init + 1);
+  bool any_fail = false;
+  for (int dd = 0; dd < gt.D; ++dd) any_fail = any_fail || info[i0 + dd] > 0;
+  for (int64_t t = first; t <= last; ++t) {
+    double gsum = 0.0;
+    const bool pair = t + 1 < T;
+    const double st = pair ? double(s[t]) : 0.0;
+    for (int dd = 0; dd < gt.D; ++dd) {
+      const int64_t i = i0 + dd;
+      const int64_t base = gt.sys_base[i];
+      const Tr* c = static_cast<const Tr*>(p.c) + base * NB;
+      const Tr* d = static_cast<const Tr*>(p.d) + base;
+      const Tr* ys = y + base * NB;
+      const Tr* gs_ = gv + base * NB;
+      const bool failed = info[i] > 0;
+      double ya[NB], ga[NB], cv[NB];
+      double cy = 0.0, cg = 0.0;
+#pragma unroll
+      for (int a = 0; a < NB; ++a) {
+        ya[a] = double(ys[t * NB + a]);
+        ga[a] = double(gs_[t * NB + a]);
+        cv[a] = double(c[t * NB + a]);
+        cy = fma(cv[a], ya[a], cy);
+        cg = fma(cv[a], ga[a], cg);
+      }
+      const double e = double(d[t]) - cy;
+#pragma unroll
+      for (int a = 0; a < NB; ++a)
+        gc[(base + t) * NB + a] = failed ? nan_t<Tr>() : Tr(p.wg2 * (e * ga[a] - cg * ya[a]));
+      gd[base + t] = failed ? nan_t<Tr>() : Tr(p.wg2 * cg);
+      if (t < p.T_init) {
+        for (int a = 0; a <= p.R_init; ++a)
+          gu[i * nu + t * (p.R_init + 1) + a] = failed ? nan_t<Tr>() : Tr(p.wi2 * ga[a]);
+      }
+      if (pair) {
+        double yb[NB], gb[NB];
+#pragma unroll
+        for (int a = 0; a < NB; ++a) {
+          yb[a] = double(ys[(t + 1) * NB + a]);
+          gb[a] = double(gs_[(t + 1) * NB + a]);
+        }
+        gsum += smooth_pair_grad<NB>(st, p.ws2, ya, yb, ga, gb);
+      }
+    }
+    gso[t] = any_fail ? nan_t<Tr>() : Tr(gsum);
+  }
+}
+
+// ---- materialised assembly (App. A.2) ---------------------------------------------------
+template <class Tr, int NB>
+__global__ void __launch_bounds__(kThreads) k_assemble(LevelTables lt, Problem0 p, Tr* M, Tr* N, Tr* beta) {
+  constexpr int NT = NB * (NB + 1) / 2;
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= lt.G) return;
+  const int64_t i = lt.csys[g];
+  const int64_t k = g - lt.coff[i];
+  const int64_t T = lt.P[i];
+  const int64_t first = k * lt.L;
+  const int64_t last = min(first + lt.L, T) - 1;
+  const int64_t base = lt.base[i];
+  const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, nullptr, i, base, T);
+  for (int64_t t = first; t <= last; ++t) {
+    Tr a[NB][NB], e[NB][NB], v[NB];
+    src.A(t, a);
+    src.b(t, v);
+    if (t + 1 < T) src.E(t, e);
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      beta[(base + t) * NB + r] = v[r];
+#pragma unroll
+      for (int q = 0; q <= r; ++q) M[(base + t) * NT + tri(r, q)] = a[r][q];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) N[(base + t) * NB * NB + r * NB + q] = t + 1 < T ? e[r][q] : Tr(0);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- plan
+
+struct Level {
+  int L = 0;
+  int64_t G = 0, N = 0, stride0 = 1;
+  std::vector<int64_t> P, coff, base;
+  std::vector<int32_t> csys;
+  int32_t* d_csys = nullptr;
+  int64_t* d_coff = nullptr;
+  int64_t* d_P = nullptr;
+  int64_t* d_base = nullptr;
+  size_t o_lf = 0, o_h = 0, o_ar = 0, o_al = 0, o_ec = 0;  // factor region (bytes)
+  size_t o_z = 0, o_br = 0, o_bl = 0, o_xs = 0;            // solve region (bytes)
+};
+
+}  // namespace
+
+struct smnn_plan_s {
+  smnn_desc desc{};
+  int NB = 0;
+  int device = 0;
+  size_t esz = 4;
+  int64_t S = 0, B = 0, D = 0, N0 = 0;
+  std::vector<int64_t> sys_T, sys_off, sys_soff, seq_T, seq_soff;
+  int64_t* d_sys_soff = nullptr;
+  int64_t* d_sys_T = nullptr;
+  int64_t* d_sys_off = nullptr;
+  int64_t* d_seq_soff = nullptr;
+  int32_t* d_sq_b = nullptr;
+  int32_t* d_sq_k = nullptr;
+  int64_t Q = 0;
+  std::vector<Level> lv;
+  size_t factor_bytes = 0, solve_bytes = 0;
+  size_t o_r = 0, o_g = 0, o_nrm = 0;  // solve region (bytes)
+  void* tables = nullptr;              // one device allocation for every index table
+};
+
+namespace {
+
+// Chunk length per level.  SEQ: one level, one chunk per system (Alg. 3/4 as written).
+// CR/AUTO: level 0 takes chunks long enough to leave ~75k threads (at most 64 steps),
+// higher levels 32, until a level fits one chunk of <= kTopMax steps.
+std::vector<int> plan_levels(const smnn_desc& d, const std::vector<int64_t>& T, int64_t total) {
+  int64_t maxT = 1;
+  for (int64_t t : T) maxT = std::max(maxT, t);
+  std::vector<int> Ls;
+  if (d.algo == SMNN_ALGO_SEQ) {
+    Ls.push_back(int(maxT));
+    return Ls;
+  }
+  std::vector<int64_t> P = T;
+  int64_t maxP = maxT;
+  bool first = true;
+  while (maxP > kTopMax && int(Ls.size()) < kMaxLevels - 1) {
+    int L;
+    if (first && d.chunk > 0) {
+      L = d.chunk;
+    } else if (first) {
+      const int64_t want = total / 75000;
+      L = 4;
+      while (L * 2 <= want && L < 64) L *= 2;
+    } else {
+      L = 32;
+    }
+    first = false;
+    Ls.push_back(L);
+    maxP = 0;
+    for (auto& p : P) {
+      p = (p + L - 1) / L;
+      maxP = std::max(maxP, p);
+    }
+  }
+  Ls.push_back(int(std::max<int64_t>(maxP, 1)));
+  return Ls;
+}
+
+smnn_status build_plan(smnn_plan_s* pl) {
+  const smnn_desc& d = pl->desc;
+  const int NB = pl->NB;
+  const int NT = NB * (NB + 1) / 2;
+  const size_t es = pl->esz;
+  const int64_t S = pl->S;
+  const std::vector<int> Ls = plan_levels(d, pl->sys_T, pl->N0);
+  pl->lv.resize(Ls.size());
+  std::vector<int64_t> P = pl->sys_T, base = pl->sys_off;
+  int64_t stride0 = 1;
+  for (size_t l = 0; l < Ls.size(); ++l) {
+    Level& L = pl->lv[l];
+    L.L = Ls[l];
+    L.P = P;
+    L.base = base;
+    L.stride0 = stride0;
+    L.coff.assign(S + 1, 0);
+    for (int64_t i = 0; i < S; ++i) L.coff[i + 1] = L.coff[i] + (P[i] + L.L - 1) / L.L;
+    L.G = L.coff[S];
+    L.N = 0;
+    for (int64_t i = 0; i < S; ++i) L.N += P[i];
+    L.csys.resize(L.G);
+    for (int64_t i = 0; i < S; ++i)
+      for (int64_t g = L.coff[i]; g < L.coff[i + 1]; ++g) L.csys[g] = int32_t(i);
+    std::vector<int64_t> nP(S), nb(S);   // next level: one step per chunk
+    for (int64_t i = 0; i < S; ++i) { nP[i] = L.coff[i + 1] - L.coff[i]; nb[i] = L.coff[i]; }
+    P = nP;
+    base = nb;
+    stride0 *= L.L;
+  }
+  size_t f = 0, s = 0;  // buffer layout
+  for (auto& L : pl->lv) {
+    const size_t GL = size_t(L.G) * size_t(L.L);
+    L.o_lf = f; f += align_up(GL * NT * es);
+    L.o_h = f;  f += align_up(GL * NB * NB * es);
+    L.o_ar = f; f += align_up(size_t(L.G) * NT * es);
+    L.o_al = f; f += align_up(size_t(L.G) * NT * es);
+    L.o_ec = f; f += align_up(size_t(L.G) * NB * NB * es);
+    L.o_z = s;  s += align_up(GL * NB * es);
+    L.o_br = s; s += align_up(size_t(L.G) * NB * es);
+    L.o_bl = s; s += align_up(size_t(L.G) * NB * es);
+    L.o_xs = s; s += align_up(size_t(L.G) * NB * es);
+  }
+  pl->o_r = s;   s += align_up(size_t(pl->N0) * NB * es);
+  pl->o_g = s;   s += align_up(size_t(pl->N0) * NB * es);
+  pl->o_nrm = s; s += align_up(size_t(S) * 2 * sizeof(double));
+  pl->factor_bytes = f;
+  pl->solve_bytes = s;
+
+  // sequence chunks for the gradient kernel (level-0 chunk length)
+  std::vector<int32_t> sq_b, sq_k;
+  const int L0 = pl->lv[0].L;
+  for (int64_t b = 0; b < pl->B; ++b) {
+    const int64_t K = (pl->seq_T[b] + L0 - 1) / L0;
+    for (int64_t k = 0; k < K; ++k) { sq_b.push_back(int32_t(b)); sq_k.push_back(int32_t(k)); }
+  }
+  pl->Q = int64_t(sq_b.size());
+
+  size_t tb = 0;  // one device allocation for every table
+  for (auto& L : pl->lv) tb += align_up(L.G * 4) + align_up((S + 1) * 8) + 2 * align_up(S * 8);
+  tb += 3 * align_up(S * 8) + align_up(pl->B * 8) + 2 * align_up(pl->Q * 4);
+  if (cudaMalloc(&pl->tables, tb) != cudaSuccess) { pl->tables = nullptr; return SMNN_ERR_CUDA; }
+  std::vector<char> host(tb, 0);
+  char* hp = host.data();
+  char* dp = static_cast<char*>(pl->tables);
+  auto put = [&](const void* src, size_t n, auto** dst) {
+    if (n) std::memcpy(hp, src, n);
+    *dst = reinterpret_cast<std::remove_pointer_t<decltype(dst)>>(dp);
+    hp += align_up(n);
+    dp += align_up(n);
+  };
+  for (auto& L : pl->lv) {
+    put(L.csys.data(), L.G * 4, &L.d_csys);
+    put(L.coff.data(), (S + 1) * 8, &L.d_coff);
+    put(L.P.data(), S * 8, &L.d_P);
+    put(L.base.data(), S * 8, &L.d_base);
+  }
+  put(pl->sys_soff.data(), S * 8, &pl->d_sys_soff);
+  put(pl->sys_T.data(), S * 8, &pl->d_sys_T);
+  put(pl->sys_off.data(), S * 8, &pl->d_sys_off);
+  put(pl->seq_soff.data(), pl->B * 8, &pl->d_seq_soff);
+  put(sq_b.data(), pl->Q * 4, &pl->d_sq_b);
+  put(sq_k.data(), pl->Q * 4, &pl->d_sq_k);
+  if (cudaMemcpy(pl->tables, host.data(), tb, cudaMemcpyHostToDevice) != cudaSuccess) return SMNN_ERR_CUDA;
+  return SMNN_OK;
+}
+
+// ----------------------------------------------------------------------------- dispatch
+
+LevelTables tables_of(const Level& L) {
+  return LevelTables{L.d_csys, L.d_coff, L.d_P, L.d_base, L.G, L.L, L.stride0};
+}
+
+template <class Tr, int NB>
+LevelBufs<Tr, NB> bufs_of(const Level& L, char* fac, char* sol) {
+  LevelBufs<Tr, NB> b;
+  b.fac.lf = reinterpret_cast<Tr*>(fac + L.o_lf);
+  b.fac.h = reinterpret_cast<Tr*>(fac + L.o_h);
+  b.fac.z = reinterpret_cast<Tr*>(sol + L.o_z);
+  b.fac.G = L.G;
+  b.fac.L = L.L;
+  b.out.a_right = reinterpret_cast<Tr*>(fac + L.o_ar);
+  b.out.a_left = reinterpret_cast<Tr*>(fac + L.o_al);
+  b.out.e_coup = reinterpret_cast<Tr*>(fac + L.o_ec);
+  b.out.b_right = reinterpret_cast<Tr*>(sol + L.o_br);
+  b.out.b_left = reinterpret_cast<Tr*>(sol + L.o_bl);
+  b.xsep = reinterpret_cast<Tr*>(sol + L.o_xs);
+  return b;
+}
+
+inline unsigned nblocks(int64_t n) { return unsigned((n + kThreads - 1) / kThreads); }
+
+#define SMNN_LAUNCH(kern, n, st, ...)                                         \
+  do {                                                                        \
+    if ((n) > 0) {                                                            \
+      kern<<<nblocks(n), kThreads, 0, st>>>(__VA_ARGS__);                     \
+      g_launches.fetch_add(1, std::memory_order_relaxed);                     \
+      if (cudaGetLastError() != cudaSuccess) return SMNN_ERR_CUDA;            \
+    }                                                                         \
+  } while (0)
+
+Problem0 problem0(const smnn_plan_s* pl, const void* c, const void* d, const void* s, const void* u) {
+  Problem0 p;
+  p.c = c; p.d = d; p.s = s; p.u = u;
+  p.soff = pl->d_sys_soff;
+  p.wg2 = pl->desc.w_gov * pl->desc.w_gov;
+  p.wi2 = pl->desc.w_init * pl->desc.w_init;
+  p.ws2 = pl->desc.w_smooth * pl->desc.w_smooth;
+  p.T_init = pl->desc.T_init;
+  p.R_init = pl->desc.R_init;
+  return p;
+}
+
+// One pass of the chunked solve: eliminate level by level (factor or replay), then back
+// substitute into x (level-0 unknowns, y layout), optionally accumulating.
+template <class Tr, int NB>
+smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, bool factor,
+                       char* fac, char* sol, Tr* x, bool accum, int32_t* info, double* nrm,
+                       cudaStream_t st) {
+  const int nl = int(pl->lv.size());
+  for (int l = 0; l < nl; ++l) {
+    const Level& L = pl->lv[l];
+    const LevelTables lt = tables_of(L);
+    const LevelBufs<Tr, NB> lb = bufs_of<Tr, NB>(L, fac, sol);
+    const bool top = l == nl - 1;
+    if (l == 0) {
+      if (factor && top) SMNN_LAUNCH((k_elim0<Tr, NB, true, true>), L.G, st, lt, lb, p, rhs, info);
+      else if (factor) SMNN_LAUNCH((k_elim0<Tr, NB, true, false>), L.G, st, lt, lb, p, rhs, info);
+      else if (top) SMNN_LAUNCH((k_elim0<Tr, NB, false, true>), L.G, st, lt, lb, p, rhs, info);
+      else SMNN_LAUNCH((k_elim0<Tr, NB, false, false>), L.G, st, lt, lb, p, rhs, info);
+    } else {
+      const ChunkOut<Tr, NB> prev = bufs_of<Tr, NB>(pl->lv[l - 1], fac, sol).out;
+      if (factor && top) SMNN_LAUNCH((k_elimN<Tr, NB, true, true>), L.G, st, lt, lb, prev, pl->d_sys_T, info);
+      else if (factor) SMNN_LAUNCH((k_elimN<Tr, NB, true, false>), L.G, st, lt, lb, prev, pl->d_sys_T, info);
+      else if (top) SMNN_LAUNCH((k_elimN<Tr, NB, false, true>), L.G, st, lt, lb, prev, pl->d_sys_T, info);
+      else SMNN_LAUNCH((k_elimN<Tr, NB, false, false>), L.G, st, lt, lb, prev, pl->d_sys_T, info);
+    }
+  }
+  for (int l = nl - 1; l >= 1; --l) {
+    const Level& L = pl->lv[l];
+    const LevelBufs<Tr, NB> lb = bufs_of<Tr, NB>(L, fac, sol);
+    const LevelBufs<Tr, NB> pb = bufs_of<Tr, NB>(pl->lv[l - 1], fac, sol);
+    SMNN_LAUNCH((k_backsubN<Tr, NB>), L.G, st, tables_of(L), lb, pb.out, pb.xsep);
+  }
+  const Level& L0 = pl->lv[0];
+  const LevelBufs<Tr, NB> lb0 = bufs_of<Tr, NB>(L0, fac, sol);
+  if (accum) SMNN_LAUNCH((k_backsub0<Tr, NB, true>), L0.G, st, tables_of(L0), lb0, p, x, info, nrm);
+  else SMNN_LAUNCH((k_backsub0<Tr, NB, false>), L0.G, st, tables_of(L0), lb0, p, x, info, nrm);
+  return SMNN_OK;
+}
+
+template <class Tr, int NB>
+smnn_status factor_solve_t(const smnn_plan_s* pl, const void* c, const void* d, const void* s,
+                           const void* u, void* y, void* factor, int32_t* info, void* ws,
+                           cudaStream_t st) {
+  const Problem0 p = problem0(pl, c, d, s, u);
+  char* fac = factor ? static_cast<char*>(factor) : static_cast<char*>(ws);
+  char* sol = static_cast<char*>(ws) + pl->factor_bytes;
+  Tr* yy = static_cast<Tr*>(y);
+  SMNN_LAUNCH(k_fill_i32, pl->S, st, info, pl->S, 0);
+  smnn_status rc = solve_pass<Tr, NB>(pl, p, nullptr, true, fac, sol, yy, false, info, nullptr, st);
+  if (rc != SMNN_OK) return rc;
+  if constexpr (std::is_same<Tr, float>::value) {
+    if (pl->desc.precision == SMNN_F32_REFINED) {
+      float* r = reinterpret_cast<float*>(sol + pl->o_r);
+      double* nrm = reinterpret_cast<double*>(sol + pl->o_nrm);
+      const bool check = pl->desc.refine_tol > 0;
+      for (int it = 0; it < pl->desc.max_refine; ++it) {
+        const bool last = it + 1 == pl->desc.max_refine;
+        if (check && last) SMNN_LAUNCH(k_fill_f64, 2 * pl->S, st, nrm, 2 * pl->S, 0.0);
+        SMNN_LAUNCH((k_residual<NB>), pl->lv[0].G, st, tables_of(pl->lv[0]), p, yy, nullptr, r);
+        rc = solve_pass<Tr, NB>(pl, p, r, false, fac, sol, yy, true, info,
+                                check && last ? nrm : nullptr, st);
+        if (rc != SMNN_OK) return rc;
+      }
+      if (check && pl->desc.max_refine > 0)
+        SMNN_LAUNCH(k_refine_check, pl->S, st, nrm, pl->S, pl->desc.refine_tol, info);
+    }
+  }
+  return SMNN_OK;
+}
+
+template <class Tr, int NB>
+smnn_status backward_t(const smnn_plan_s* pl, const void* c, const void* d, const void* s,
+                       const void* u, const void* y, const void* factor, const void* gy, void* gc,
+                       void* gd, void* gs, void* gu, int32_t* info, void* ws, cudaStream_t st) {
+  const Problem0 p = problem0(pl, c, d, s, u);
+  char* fac = factor ? static_cast<char*>(const_cast<void*>(factor)) : static_cast<char*>(ws);
+  char* sol = static_cast<char*>(ws) + pl->factor_bytes;
+  Tr* g = reinterpret_cast<Tr*>(sol + pl->o_g);
+  const Tr* rhs = static_cast<const Tr*>(gy);
+  SMNN_LAUNCH(k_fill_i32, pl->S, st, info, pl->S, 0);
+  smnn_status rc = solve_pass<Tr, NB>(pl, p, rhs, factor == nullptr, fac, sol, g, false, info, nullptr, st);
+  if (rc != SMNN_OK) return rc;
+  if constexpr (std::is_same<Tr, float>::value) {
+    if (pl->desc.precision == SMNN_F32_REFINED) {
+      float* r = reinterpret_cast<float*>(sol + pl->o_r);
+      for (int it = 0; it < pl->desc.max_refine; ++it) {
+        SMNN_LAUNCH((k_residual<NB>), pl->lv[0].G, st, tables_of(pl->lv[0]), p, g, rhs, r);
+        rc = solve_pass<Tr, NB>(pl, p, r, false, fac, sol, g, true, info, nullptr, st);
+        if (rc != SMNN_OK) return rc;
+      }
+    }
+  }
+  GradTables gt{pl->d_sq_b, pl->d_sq_k, pl->d_sys_off, pl->d_sys_T, pl->d_seq_soff, pl->Q,
+                pl->lv[0].L, int(pl->D)};
+  SMNN_LAUNCH((k_grad<Tr, NB>), pl->Q, st, gt, p, static_cast<const Tr*>(y), g, info,
+              static_cast<Tr*>(gc), static_cast<Tr*>(gd), static_cast<Tr*>(gs), static_cast<Tr*>(gu));
+  return SMNN_OK;
+}
+
+template <class Tr, int NB>
+smnn_status assemble_t(const smnn_plan_s* pl, const void* c, const void* d, const void* s,
+                       const void* u, void* M, void* N, void* beta, cudaStream_t st) {
+  const Problem0 p = problem0(pl, c, d, s, u);
+  SMNN_LAUNCH((k_assemble<Tr, NB>), pl->lv[0].G, st, tables_of(pl->lv[0]), p, static_cast<Tr*>(M),
+              static_cast<Tr*>(N), static_cast<Tr*>(beta));
+  return SMNN_OK;
+}
+
+// Runs fn<Tr, NB>(...) for the plan's precision and block size.
+#define SMNN_DISPATCH(pl, fn, ...)                                                    \
+  do {                                                                                \
+    const bool f64 = (pl)->desc.precision == SMNN_F64;                                \
+    switch ((pl)->NB) {                                                               \
+      case 2: return f64 ? fn<double, 2>(__VA_ARGS__) : fn<float, 2>(__VA_ARGS__);    \
+      case 3: return f64 ? fn<double, 3>(__VA_ARGS__) : fn<float, 3>(__VA_ARGS__);    \
+      case 4: return f64 ? fn<double, 4>(__VA_ARGS__) : fn<float, 4>(__VA_ARGS__);    \
+      default: return SMNN_ERR_UNSUPPORTED;                                           \
+    }                                                                                 \
+  } while (0)
+
+inline bool aligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) % kAlign) == 0; }
+
+struct DeviceGuard {  // run on the plan's device, restore the caller's afterwards
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+// ----------------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+smnn_status smnn_plan_create(const smnn_desc* desc, smnn_plan* plan) {
+  if (!desc || !plan) return SMNN_ERR_INVALID_ARG;
+  *plan = nullptr;
+  const smnn_desc& d = *desc;
+  if (d.R < 1 || d.R > SMNN_MAX_R || d.R_init < 0 || d.R_init > d.R || d.T_init < 1) return SMNN_ERR_INVALID_ARG;
+  if (d.precision < SMNN_F32_REFINED || d.precision > SMNN_F64) return SMNN_ERR_INVALID_ARG;
+  if (d.algo < SMNN_ALGO_AUTO || d.algo > SMNN_ALGO_CR) return SMNN_ERR_INVALID_ARG;
+  if (d.max_refine < 0 || d.max_refine > 16 || d.chunk < 0 || d.chunk == 1 || d.reserved0 != 0)
+    return SMNN_ERR_INVALID_ARG;
+  if (d.num_seq < 1 || d.dims_per_seq < 1) return SMNN_ERR_INVALID_ARG;
+  if (!(d.w_gov >= 0) || !(d.w_init >= 0) || !(d.w_smooth >= 0) || !(d.refine_tol >= 0))
+    return SMNN_ERR_INVALID_ARG;
+  if (d.num_seq > INT32_MAX || d.num_seq * d.dims_per_seq > INT32_MAX) return SMNN_ERR_INVALID_ARG;
+  if (!d.seq_T && (d.T < 1 || d.T < d.T_init)) return SMNN_ERR_INVALID_ARG;
+  smnn_plan_s* pl = new (std::nothrow) smnn_plan_s();
+  if (!pl) return SMNN_ERR_INVALID_ARG;
+  pl->desc = d;
+  pl->desc.seq_T = nullptr;
+  pl->NB = d.R + 1;
+  pl->esz = d.precision == SMNN_F64 ? 8 : 4;
+  pl->B = d.num_seq;
+  pl->D = d.dims_per_seq;
+  pl->S = pl->B * pl->D;
+  pl->seq_T.resize(pl->B);
+  for (int64_t b = 0; b < pl->B; ++b) pl->seq_T[b] = d.seq_T ? d.seq_T[b] : d.T;
+  for (int64_t b = 0; b < pl->B; ++b) {
+    if (pl->seq_T[b] < 1 || pl->seq_T[b] < d.T_init || pl->seq_T[b] > (int64_t(1) << 31)) {
+      delete pl;
+      return SMNN_ERR_INVALID_ARG;
+    }
+  }
+  pl->seq_soff.resize(pl->B);
+  int64_t so = 0;
+  for (int64_t b = 0; b < pl->B; ++b) { pl->seq_soff[b] = so; so += pl->seq_T[b]; }
+  pl->sys_T.resize(pl->S); pl->sys_off.resize(pl->S); pl->sys_soff.resize(pl->S);
+  for (int64_t b = 0; b < pl->B; ++b)
+    for (int64_t dd = 0; dd < pl->D; ++dd) {
+      const int64_t i = b * pl->D + dd;
+      pl->sys_T[i] = pl->seq_T[b];
+      pl->sys_off[i] = pl->D * pl->seq_soff[b] + dd * pl->seq_T[b];
+      pl->sys_soff[i] = pl->seq_soff[b];
+    }
+  pl->N0 = pl->D * so;
+  if (cudaGetDevice(&pl->device) != cudaSuccess) { delete pl; return SMNN_ERR_CUDA; }
+  const smnn_status rc = build_plan(pl);
+  if (rc != SMNN_OK) {
+    if (pl->tables) cudaFree(pl->tables);
+    delete pl;
+    return rc;
+  }
+  *plan = pl;
+  return SMNN_OK;
+}
+
+smnn_status smnn_plan_destroy(smnn_plan plan) {
+  if (!plan) return SMNN_OK;
+  DeviceGuard dg(plan->device);
+  smnn_status rc = SMNN_OK;
+  if (plan->tables) {
+    if (cudaDeviceSynchronize() != cudaSuccess) rc = SMNN_ERR_CUDA;
+    if (cudaFree(plan->tables) != cudaSuccess) rc = SMNN_ERR_CUDA;
+  }
+  delete plan;
+  return rc;
+}
+
+smnn_status smnn_plan_get_stats(smnn_plan plan, smnn_plan_stats* st) {
+  if (!plan || !st) return SMNN_ERR_INVALID_ARG;
+  std::memset(st, 0, sizeof(*st));
+  st->num_systems = plan->S;
+  st->total_steps = plan->N0;
+  st->num_levels = int32_t(plan->lv.size());
+  for (size_t l = 0; l < plan->lv.size() && l < 8; ++l) st->chunk[l] = plan->lv[l].L;
+  st->kernels_per_solve = int32_t(2 * plan->lv.size());
+  st->workspace_bytes = plan->factor_bytes + plan->solve_bytes;
+  st->factor_bytes = plan->factor_bytes;
+  return SMNN_OK;
+}
+
+smnn_status smnn_workspace_size(smnn_plan plan, size_t* workspace_bytes, size_t* factor_bytes) {
+  if (!plan) return SMNN_ERR_INVALID_ARG;
+  if (workspace_bytes) *workspace_bytes = plan->factor_bytes + plan->solve_bytes;
+  if (factor_bytes) *factor_bytes = plan->factor_bytes;
+  return SMNN_OK;
+}
+
+smnn_status smnn_assemble(smnn_plan plan, const void* c, const void* d, const void* s, const void* u,
+                          void* M, void* N, void* beta, void* stream) {
+  if (!plan || !c || !d || !s || !u || !M || !N || !beta) return SMNN_ERR_INVALID_ARG;
+  DeviceGuard dg(plan->device);
+  if (!dg.ok) return SMNN_ERR_CUDA;
+  SMNN_DISPATCH(plan, assemble_t, plan, c, d, s, u, M, N, beta, static_cast<cudaStream_t>(stream));
+}
+
+smnn_status smnn_factor_solve(smnn_plan plan, const void* c, const void* d, const void* s,
+                              const void* u, void* y, void* factor, int32_t* info, void* workspace,
+                              void* stream) {
+  if (!plan || !c || !d || !s || !u || !y || !info) return SMNN_ERR_INVALID_ARG;
+  if (!workspace || !aligned(workspace) || (factor && !aligned(factor))) return SMNN_ERR_WORKSPACE;
+  DeviceGuard dg(plan->device);
+  if (!dg.ok) return SMNN_ERR_CUDA;
+  SMNN_DISPATCH(plan, factor_solve_t, plan, c, d, s, u, y, factor, info, workspace,
+                static_cast<cudaStream_t>(stream));
+}
+
+smnn_status smnn_backward(smnn_plan plan, const void* c, const void* d, const void* s, const void* u,
+                          const void* y, const void* factor, const void* gy, void* gc, void* gd,
+                          void* gs, void* gu, int32_t* info, void* workspace, void* stream) {
+  if (!plan || !c || !d || !s || !u || !y || !gy || !gc || !gd || !gs || !gu || !info)
+    return SMNN_ERR_INVALID_ARG;
+  if (!workspace || !aligned(workspace) || (factor && !aligned(factor))) return SMNN_ERR_WORKSPACE;
+  DeviceGuard dg(plan->device);
+  if (!dg.ok) return SMNN_ERR_CUDA;
+  SMNN_DISPATCH(plan, backward_t, plan, c, d, s, u, y, factor, gy, gc, gd, gs, gu, info, workspace,
+                static_cast<cudaStream_t>(stream));
+}
+
+const char* smnn_status_string(smnn_status status) {
+  switch (status) {
+    case SMNN_OK: return "SMNN_OK";
+    case SMNN_ERR_INVALID_ARG: return "SMNN_ERR_INVALID_ARG: invalid argument";
+    case SMNN_ERR_WORKSPACE: return "SMNN_ERR_WORKSPACE: workspace missing or misaligned";
+    case SMNN_ERR_CUDA: return "SMNN_ERR_CUDA: CUDA runtime error";
+    case SMNN_ERR_UNSUPPORTED: return "SMNN_ERR_UNSUPPORTED: unsupported request";
+  }
+  return "unknown smnn_status";
+}
+
+uint64_t smnn_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

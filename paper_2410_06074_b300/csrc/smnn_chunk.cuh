@@ -1,0 +1,535 @@
+// smnn_chunk.cuh -- per-step block algebra of the S-MNN solve (sm_103a kernels).
+//
+// Notation (Sec. 3.2): a system has steps t = 0..T-1 with NB = R+1 unknowns each.
+// M is block tridiagonal SPD: diagonal blocks A_t (= M_t), lower blocks E_t = block
+// (t+1, t) (= N_t), right-hand side b_t (= beta_t).  App. A.2 gives them in closed form:
+//   M_t    = w_gov^2 c_t c_t^T + w_init^2 U_t + w_smooth^2 S*_t
+//   N_t    = w_smooth^2 S**_t,   S**_t = -(S+_t F S+_t) - (S-_t F^T S-_t)
+//   beta_t = w_gov^2 c_t d_t + w_init^2 u_t
+// with F_ij = 1/(j-i)! (j >= i), S+-_t = diag((+-s_t)^r), S2_t = diag(s_t^{2r}) and
+//   S*_t = [t<T-1] (S+_t F^T F S+_t + S2_t) + [t>0] (S-_{t-1} F^T F S-_{t-1} + S2_{t-1}).
+// Entrywise: (S+ F^T F S+)_ab = s^{a+b} (F^T F)_ab, (S- F^T F S-)_ab = (-1)^{a+b} s^{a+b} (F^T F)_ab,
+//   (N_t)_ab = -w_smooth^2 s_t^{a+b} [ a<b: 1/(b-a)!,  a=b: 2,  a>b: (-1)^{a+b}/(a-b)! ].
+//
+// Chunked elimination (the parallel-in-T order of Alg. 3's block Cholesky): the steps of
+// a system are cut into chunks of L steps; the last step of each chunk is a separator and
+// the others are interior.  One thread eliminates its chunk's interior left to right (a
+// block Cholesky sweep that also carries the fill block coupling each interior step to
+// the previous chunk's separator), which leaves a block-tridiagonal SPD system on the
+// separators (the Schur complement), reduced the same way at the next level until one
+// chunk per system remains.  Back substitution walks the levels in reverse.  Per interior
+// step t of a chunk whose left separator is sigma:
+//   D_t  = current Schur diagonal of step t,  D_t = L_t L_t^T        (Cholesky)
+//   G_t  = coupling of step t to sigma,       H_t = L_t^{-1} G_t
+//   r_t  = current right-hand side,           z_t = L_t^{-1} r_t
+//   X_t  = L_t^{-1} E_t^T
+//   D_{t+1} = A_{t+1} - X_t^T X_t,  G_{t+1} = -X_t^T H_t,  r_{t+1} = b_{t+1} - X_t^T z_t
+//   sigma's diagonal -= H_t^T H_t,  sigma's rhs -= H_t^T z_t
+// and back substitution:  x_t = L_t^{-T} (z_t - X_t x_{t+1} - H_t x_sigma).
+// With one chunk per system this is the sequential block Cholesky of Alg. 3 followed by
+// the two substitution sweeps of Alg. 4.
+#pragma once
+#include <cstdint>
+#include <cmath>
+
+#if defined(__CUDACC__)
+#define SMNN_HD __host__ __device__ __forceinline__
+#else
+#define SMNN_HD inline
+#endif
+
+namespace smnn {
+
+constexpr double inv_fact(int k) { return k <= 1 ? 1.0 : inv_fact(k - 1) / double(k); }
+
+// (F^T F)_ab = sum_{k <= min(a,b)} 1/((a-k)! (b-k)!)
+constexpr double ftf_coef(int a, int b) {
+  double acc = 0.0;
+  for (int k = 0; k <= (a < b ? a : b); ++k) acc += inv_fact(a - k) * inv_fact(b - k);
+  return acc;
+}
+
+// (N_t)_ab / (-w_smooth^2 s^{a+b})
+constexpr double n_coef(int a, int b) {
+  return a < b ? inv_fact(b - a) : (a == b ? 2.0 : (((a + b) & 1) ? -inv_fact(a - b) : inv_fact(a - b)));
+}
+
+constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // packed lower, j <= i
+
+template <class Tr> SMNN_HD Tr rsqrt_t(Tr x);
+template <> SMNN_HD float rsqrt_t<float>(float x) {
+#ifdef __CUDA_ARCH__
+  return rsqrtf(x);
+#else
+  return 1.0f / std::sqrt(x);
+#endif
+}
+template <> SMNN_HD double rsqrt_t<double>(double x) {
+#ifdef __CUDA_ARCH__
+  return rsqrt(x);
+#else
+  return 1.0 / std::sqrt(x);
+#endif
+}
+
+template <class Tr> SMNN_HD Tr nan_t() { return Tr(NAN); }
+
+// ----------------------------------------------------------------------------- block ops
+
+// In-place Cholesky of the symmetric a (lower triangle read); afterwards a holds L below
+// and on the diagonal, inv[i] = 1/L_ii.  Returns false on a non-positive (or NaN) pivot.
+template <class Tr, int NB>
+SMNN_HD bool chol(Tr (&a)[NB][NB], Tr (&inv)[NB]) {
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    Tr djj = a[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) djj -= a[j][k] * a[j][k];
+    ok = ok && (djj > Tr(0));
+    const Tr rl = rsqrt_t<Tr>(djj);
+    inv[j] = rl;
+    a[j][j] = djj * rl;
+#pragma unroll
+    for (int i = j + 1; i < NB; ++i) {
+      Tr v = a[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) v -= a[i][k] * a[j][k];
+      a[i][j] = v * rl;
+    }
+  }
+  return ok;
+}
+
+// v <- L^{-1} v
+template <class Tr, int NB>
+SMNN_HD void trsv_l(const Tr (&l)[NB][NB], const Tr (&inv)[NB], Tr (&v)[NB]) {
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    Tr acc = v[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) acc -= l[i][k] * v[k];
+    v[i] = acc * inv[i];
+  }
+}
+
+// v <- L^{-T} v
+template <class Tr, int NB>
+SMNN_HD void trsv_lt(const Tr (&l)[NB][NB], const Tr (&inv)[NB], Tr (&v)[NB]) {
+#pragma unroll
+  for (int i = NB - 1; i >= 0; --i) {
+    Tr acc = v[i];
+#pragma unroll
+    for (int k = i + 1; k < NB; ++k) acc -= l[k][i] * v[k];
+    v[i] = acc * inv[i];
+  }
+}
+
+// X <- L^{-1} B^T  (column j of X solves L x = row j of B)
+template <class Tr, int NB>
+SMNN_HD void trsm_l_bt(const Tr (&l)[NB][NB], const Tr (&inv)[NB], const Tr (&b)[NB][NB],
+                       Tr (&x)[NB][NB]) {
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      Tr acc = b[j][i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) acc -= l[i][k] * x[k][j];
+      x[i][j] = acc * inv[i];
+    }
+  }
+}
+
+// X <- L^{-1} B
+template <class Tr, int NB>
+SMNN_HD void trsm_l(const Tr (&l)[NB][NB], const Tr (&inv)[NB], const Tr (&b)[NB][NB],
+                    Tr (&x)[NB][NB]) {
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      Tr acc = b[i][j];
+#pragma unroll
+      for (int k = 0; k < i; ++k) acc -= l[i][k] * x[k][j];
+      x[i][j] = acc * inv[i];
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- factor I/O
+
+// Factor of one level, stored chunk-interleaved so that a warp's threads (consecutive
+// chunks g) touch consecutive addresses: element e of in-chunk step j of chunk g sits at
+// [(e*L + j)*G + g].  lf holds L_t packed lower with the inverse diagonal, h the fill
+// blocks H_t, z the forward-sweep vectors z_t of the current right-hand side.
+template <class Tr, int NB>
+struct FactorView {
+  Tr* lf;
+  Tr* h;
+  Tr* z;
+  int64_t G;
+  int L;
+  SMNN_HD int64_t at(int e, int j, int64_t g) const { return (int64_t(e) * L + j) * G + g; }
+
+  SMNN_HD void store_l(int j, int64_t g, const Tr (&l)[NB][NB], const Tr (&inv)[NB]) const {
+#pragma unroll
+    for (int a = 0; a < NB; ++a)
+#pragma unroll
+      for (int b = 0; b <= a; ++b) lf[at(tri(a, b), j, g)] = a == b ? inv[a] : l[a][b];
+  }
+  SMNN_HD void load_l(int j, int64_t g, Tr (&l)[NB][NB], Tr (&inv)[NB]) const {
+#pragma unroll
+    for (int a = 0; a < NB; ++a)
+#pragma unroll
+      for (int b = 0; b <= a; ++b) {
+        const Tr v = lf[at(tri(a, b), j, g)];
+        if (a == b) inv[a] = v; else l[a][b] = v;
+      }
+  }
+  SMNN_HD void store_h(int j, int64_t g, const Tr (&m)[NB][NB]) const {
+#pragma unroll
+    for (int a = 0; a < NB; ++a)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) h[at(a * NB + b, j, g)] = m[a][b];
+  }
+  SMNN_HD void load_h(int j, int64_t g, Tr (&m)[NB][NB]) const {
+#pragma unroll
+    for (int a = 0; a < NB; ++a)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) m[a][b] = h[at(a * NB + b, j, g)];
+  }
+  SMNN_HD void store_z(int j, int64_t g, const Tr (&v)[NB]) const {
+#pragma unroll
+    for (int a = 0; a < NB; ++a) z[at(a, j, g)] = v[a];
+  }
+  SMNN_HD void load_z(int j, int64_t g, Tr (&v)[NB]) const {
+#pragma unroll
+    for (int a = 0; a < NB; ++a) v[a] = z[at(a, j, g)];
+  }
+};
+
+// Separator outputs of one chunk g (array of structs per chunk): the right part of the
+// separator's reduced diagonal and rhs, the left contributions destined to the previous
+// separator, and the coupling block between the two separators.
+template <class Tr, int NB>
+struct ChunkOut {
+  Tr* a_right;   // [G][NT]
+  Tr* a_left;    // [G][NT]
+  Tr* e_coup;    // [G][NB*NB]  block (sigma_k, sigma_{k-1})
+  Tr* b_right;   // [G][NB]
+  Tr* b_left;    // [G][NB]
+};
+
+// ----------------------------------------------------------------------------- sources
+
+// Level-0 blocks, assembled in registers from the paper's representation {c, d, u, s}
+// (App. A.2).  Pointers are already offset to the system.
+template <class Tr, int NB>
+struct CoefSource {
+  const Tr* c;     // [T][NB]
+  const Tr* d;     // [T]
+  const Tr* s;     // [T]
+  const Tr* u;     // [T_init][R_init+1]
+  const Tr* rhs;   // explicit right-hand side [T][NB], or nullptr for beta_t
+  int64_t T;
+  Tr wg2, wi2, ws2;
+  int T_init, R_init;
+
+  SMNN_HD void A(int64_t t, Tr (&a)[NB][NB]) const {
+    Tr cv[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) cv[r] = c[t * NB + r];
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+      for (int j = 0; j < NB; ++j) a[i][j] = wg2 * cv[i] * cv[j];
+    if (t < T_init) {
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r <= R_init) a[r][r] += wi2;
+    }
+    if (t + 1 < T) add_smooth<false>(s[t], a);
+    if (t > 0) add_smooth<true>(s[t - 1], a);
+  }
+
+  // w_s^2 ((S+- F^T F S+-) + S2) of the pair (t, t+1), seen from t (kMinus = false) or
+  // from t+1 (kMinus = true).
+  template <bool kMinus>
+  SMNN_HD void add_smooth(Tr st, Tr (&a)[NB][NB]) const {
+    Tr pw[2 * NB - 1];
+    pw[0] = Tr(1);
+#pragma unroll
+    for (int k = 1; k < 2 * NB - 1; ++k) pw[k] = pw[k - 1] * st;
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        Tr v = Tr(ftf_coef(i, j)) * pw[i + j];
+        if (kMinus && ((i + j) & 1)) v = -v;
+        if (i == j) v += pw[2 * i];
+        a[i][j] += ws2 * v;
+      }
+  }
+
+  SMNN_HD void b(int64_t t, Tr (&v)[NB]) const {
+    if (rhs) {
+#pragma unroll
+      for (int r = 0; r < NB; ++r) v[r] = rhs[t * NB + r];
+      return;
+    }
+    const Tr dt = d[t];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) v[r] = wg2 * c[t * NB + r] * dt;
+    if (t < T_init) {
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r <= R_init) v[r] += wi2 * u[t * (R_init + 1) + r];
+    }
+  }
+
+  // E_t = N_t = block (t+1, t), t < T-1
+  SMNN_HD void E(int64_t t, Tr (&e)[NB][NB]) const {
+    const Tr st = s[t];
+    Tr pw[2 * NB - 1];
+    pw[0] = Tr(1);
+#pragma unroll
+    for (int k = 1; k < 2 * NB - 1; ++k) pw[k] = pw[k - 1] * st;
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+      for (int j = 0; j < NB; ++j) e[i][j] = -ws2 * Tr(n_coef(i, j)) * pw[i + j];
+  }
+};
+
+// Level >= 1 blocks: the Schur complement on the previous level's separators, read from
+// that level's chunk outputs (pointers offset to the system's first chunk).
+template <class Tr, int NB>
+struct ReducedSource {
+  static constexpr int NT = NB * (NB + 1) / 2;
+  const Tr* a_right;
+  const Tr* a_left;
+  const Tr* e_coup;
+  const Tr* b_right;
+  const Tr* b_left;
+  int64_t P;  // steps of this system at this level
+
+  SMNN_HD void A(int64_t k, Tr (&a)[NB][NB]) const {
+    const bool nxt = k + 1 < P;
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) {
+        Tr v = a_right[k * NT + tri(i, j)];
+        if (nxt) v += a_left[(k + 1) * NT + tri(i, j)];
+        a[i][j] = v;
+        a[j][i] = v;
+      }
+  }
+  SMNN_HD void b(int64_t k, Tr (&v)[NB]) const {
+    const bool nxt = k + 1 < P;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) v[i] = b_right[k * NB + i] + (nxt ? b_left[(k + 1) * NB + i] : Tr(0));
+  }
+  SMNN_HD void E(int64_t k, Tr (&e)[NB][NB]) const {
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+      for (int j = 0; j < NB; ++j) e[i][j] = e_coup[(k + 1) * NB * NB + i * NB + j];
+  }
+};
+
+// ----------------------------------------------------------------------------- chunk sweeps
+
+// Eliminate the interior of chunk g (steps first..last-1, separator last).  kFactor: compute
+// and store L_t, H_t and the separator's reduced blocks; otherwise read the stored factor and
+// only carry the right-hand side.  Returns 0, or 1 + the step index of the first bad pivot.
+template <class Tr, int NB, bool kFactor, class Src>
+SMNN_HD int64_t elim_chunk(const Src& src, int64_t first, int64_t last, bool has_left,
+                           const FactorView<Tr, NB>& fac, int64_t g, const ChunkOut<Tr, NB>& out) {
+  constexpr int NT = NB * (NB + 1) / 2;
+  int64_t fail = 0;
+  Tr D[NB][NB], Gm[NB][NB], r[NB], Sl[NB][NB], bl[NB];
+  src.b(first, r);
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    bl[i] = Tr(0);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) { Sl[i][j] = Tr(0); Gm[i][j] = Tr(0); D[i][j] = Tr(0); }
+  }
+  if (kFactor) {
+    src.A(first, D);
+    if (has_left) src.E(first - 1, Gm);
+  }
+  for (int64_t t = first; t < last; ++t) {
+    const int j = int(t - first);
+    Tr Lm[NB][NB], inv[NB];
+    if (kFactor) {
+#pragma unroll
+      for (int a = 0; a < NB; ++a)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) Lm[a][b] = D[a][b];
+      if (!chol<Tr, NB>(Lm, inv) && fail == 0) fail = t + 1;
+      fac.store_l(j, g, Lm, inv);
+    } else {
+      fac.load_l(j, g, Lm, inv);
+    }
+    Tr z[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) z[a] = r[a];
+    trsv_l<Tr, NB>(Lm, inv, z);
+    fac.store_z(j, g, z);
+    Tr Hm[NB][NB];
+    if (has_left) {
+      if (kFactor) {
+        trsm_l<Tr, NB>(Lm, inv, Gm, Hm);
+        fac.store_h(j, g, Hm);
+#pragma unroll
+        for (int a = 0; a < NB; ++a)
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            Tr acc = Tr(0);
+#pragma unroll
+            for (int k = 0; k < NB; ++k) acc += Hm[k][a] * Hm[k][b];
+            Sl[a][b] -= acc;
+          }
+      } else {
+        fac.load_h(j, g, Hm);
+      }
+#pragma unroll
+      for (int a = 0; a < NB; ++a) {
+        Tr acc = Tr(0);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) acc += Hm[k][a] * z[k];
+        bl[a] -= acc;
+      }
+    }
+    Tr E[NB][NB], X[NB][NB];
+    src.E(t, E);
+    trsm_l_bt<Tr, NB>(Lm, inv, E, X);
+    src.b(t + 1, r);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      Tr acc = Tr(0);
+#pragma unroll
+      for (int k = 0; k < NB; ++k) acc += X[k][a] * z[k];
+      r[a] -= acc;
+    }
+    if (kFactor) {
+      src.A(t + 1, D);
+#pragma unroll
+      for (int a = 0; a < NB; ++a)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          Tr acc = Tr(0);
+#pragma unroll
+          for (int k = 0; k < NB; ++k) acc += X[k][a] * X[k][b];
+          D[a][b] -= acc;
+        }
+      if (has_left) {
+        Tr Gn[NB][NB];
+#pragma unroll
+        for (int a = 0; a < NB; ++a)
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            Tr acc = Tr(0);
+#pragma unroll
+            for (int k = 0; k < NB; ++k) acc += X[k][a] * Hm[k][b];
+            Gn[a][b] = -acc;
+          }
+#pragma unroll
+        for (int a = 0; a < NB; ++a)
+#pragma unroll
+          for (int b = 0; b < NB; ++b) Gm[a][b] = Gn[a][b];
+      }
+    }
+  }
+  if (kFactor) {
+#pragma unroll
+    for (int a = 0; a < NB; ++a)
+#pragma unroll
+      for (int b = 0; b <= a; ++b) {
+        out.a_right[g * NT + tri(a, b)] = D[a][b];
+        out.a_left[g * NT + tri(a, b)] = Sl[a][b];
+      }
+    if (has_left) {
+#pragma unroll
+      for (int a = 0; a < NB; ++a)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) out.e_coup[g * NB * NB + a * NB + b] = Gm[a][b];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < NB; ++a) {
+    out.b_right[g * NB + a] = r[a];
+    out.b_left[g * NB + a] = bl[a];
+  }
+  return fail;
+}
+
+// Solve the single remaining separator of a top-level chunk: x = A'^{-1} b' with A' the
+// chunk's reduced diagonal.  Returns false on a bad pivot.
+template <class Tr, int NB>
+SMNN_HD bool solve_top(const ChunkOut<Tr, NB>& out, int64_t g, Tr* x) {
+  constexpr int NT = NB * (NB + 1) / 2;
+  Tr a[NB][NB], inv[NB], v[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    v[i] = out.b_right[g * NB + i];
+#pragma unroll
+    for (int j = 0; j <= i; ++j) { a[i][j] = out.a_right[g * NT + tri(i, j)]; a[j][i] = a[i][j]; }
+  }
+  const bool ok = chol<Tr, NB>(a, inv);
+  trsv_l<Tr, NB>(a, inv, v);
+  trsv_lt<Tr, NB>(a, inv, v);
+#pragma unroll
+  for (int i = 0; i < NB; ++i) x[i] = v[i];
+  return ok;
+}
+
+// Back-substitute chunk g given its separators' values (x_left unused without a left
+// separator).  emit(t, x) receives every step of the chunk, separator included.
+template <class Tr, int NB, class Src, class Emit>
+SMNN_HD void backsub_chunk(const Src& src, int64_t first, int64_t last, bool has_left,
+                           const FactorView<Tr, NB>& fac, int64_t g, const Tr* x_right,
+                           const Tr* x_left, Emit& emit) {
+  Tr xn[NB], xl[NB];
+#pragma unroll
+  for (int a = 0; a < NB; ++a) {
+    xn[a] = x_right[a];
+    xl[a] = has_left ? x_left[a] : Tr(0);
+  }
+  emit(last, xn);
+  for (int64_t t = last - 1; t >= first; --t) {
+    const int j = int(t - first);
+    Tr Lm[NB][NB], inv[NB], v[NB], E[NB][NB], X[NB][NB];
+    fac.load_l(j, g, Lm, inv);
+    fac.load_z(j, g, v);
+    src.E(t, E);
+    trsm_l_bt<Tr, NB>(Lm, inv, E, X);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      Tr acc = Tr(0);
+#pragma unroll
+      for (int k = 0; k < NB; ++k) acc += X[a][k] * xn[k];
+      v[a] -= acc;
+    }
+    if (has_left) {
+      Tr Hm[NB][NB];
+      fac.load_h(j, g, Hm);
+#pragma unroll
+      for (int a = 0; a < NB; ++a) {
+        Tr acc = Tr(0);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) acc += Hm[a][k] * xl[k];
+        v[a] -= acc;
+      }
+    }
+    trsv_lt<Tr, NB>(Lm, inv, v);
+    emit(t, v);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) xn[a] = v[a];
+  }
+}
+
+}  // namespace smnn
