@@ -1,0 +1,444 @@
+#!/usr/bin/env python
+"""Benchmark of the S-MNN batched solve (Scalable Mechanistic Neural Networks, Sec. 3).
+
+One step = one forward solve (assembly, factorisation, substitution, two FP64-residual
+refinement sweeps) plus one adjoint pass (re-solve with dl/dy, refined, and the fused
+parameter gradients) over the whole workload, inputs resident in HBM.  Metric: time-steps
+solved per second (sum over systems of T), forward + adjoint.
+
+Default workload: B=512 sequences x D=8 dimensions x T=1024 steps, R=2 (4,194,304
+time-steps), SMNN_F32_REFINED.  Timing: W untimed warm-up steps, then K steps, each bracketed
+by CUDA events on the launching stream with a 256 MiB write between steps to flush L2;
+barrier + synchronize around the timed region; the max over ranks is reported.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank solves its own copy of the workload on its own GPU (systems are
+independent: weak scaling, no collective on the data path).  ``--impl reference`` times the
+FP64 CPU oracle on the host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from smnn_workloads import config2, mse_target  # noqa: E402
+
+WORKLOAD = "config2: B=512 D=8 T=1024 R=2, FP32 factor + 2 FP64-residual refinement sweeps, fwd+adjoint"
+METRIC = "time-steps solved/s fwd+bwd (FP32-refined, <=1e-6 vs FP64 oracle)"
+UNIT = "time-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0])); mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+# FP64 peak of this B300, measured with a DFMA-chain microbenchmark (8 independent chains
+# per thread, 148 x 4..8 CTAs of 256 threads): 0.562e12 DFMA/s = 1.125 TFLOP/s at
+# ~1.94 GHz, i.e. ~2 DFMA per SM per clock; FP32 measured 68.7 TFLOP/s the same way.
+FP64_PEAK_TFLOPS = 1.125
+
+
+def algorithmic_units(name: str, NB: int, D: int):
+    """Per-step algorithmic work of one launch of a kernel: (bound, amount, unit).
+    FP64 arithmetic kernels count FP64 operations per time-step (an FMA counts 2); the
+    memory-bound sweeps count the HBM bytes the method must move per time-step."""
+    if name == "k_residual":
+        # governing row: c.x (NB FMA), w*(d - c.x) (2), NB FMA into r;  pair of smoothness
+        # row blocks: two Taylor products (NB(NB-1)/2 FMA each + NB), 2*NB subs, 2*NB weight
+        # products, two transposed Taylor products (NB(NB-1)/2 FMA each + NB), 2*NB
+        # combinations, NB + 2 power products; NB accumulations
+        tay = NB * (NB - 1) // 2
+        fl = 2 * NB + 2 + 2 * NB + 2 * (2 * tay + NB) + 2 * NB + 2 * NB + 2 * (2 * tay + NB) \
+            + 2 * NB + NB + 2 + NB
+        return "alu", float(fl), "FLOP"
+    if name == "k_grad":
+        tay = NB * (NB - 1) // 2
+        fl = 4 * NB + 2 * NB + 3 + 4 * (2 * tay + NB) + 4 * NB + NB * 16
+        return "alu", float(fl), "FLOP"
+    # elimination / substitution sweeps: c (4 NB) + d (4) + s (4/D) read, y (4 NB) written
+    return "hbm", 8.0 * NB + 4.0 + 4.0 / D, "B"
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_2410_06074_b300 as pk
+    from paper_2410_06074_b300 import binding as Bd
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    prob = config2()
+    p32 = prob.cast(np.float32)
+    NB, D = prob.R + 1, prob.D
+    steps_per_pass = prob.steps
+    cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=pk.F32_REFINED,
+                         max_refine=2)
+    plan = pk.get_plan((prob.R, prob.B, prob.D, prob.T), cfg)
+    c, d, s, u = (torch.from_numpy(a).to(dev) for a in (p32.c, p32.d, p32.s, p32.u))
+    y = torch.empty_like(c)
+    info = torch.empty(plan.S, dtype=torch.int32, device=dev)
+    work = plan.workspace(dev)
+    factor = plan.factor_buffer(dev)
+    gc, gd, gs, gu = (torch.empty_like(t) for t in (c, d, s, u))
+    info_b = torch.empty_like(info)
+    # dl/dy of config 2's loss: mean over S*T of (y^(0) - tau)^2 at this workload's y
+    plan.factor_solve(c, d, s, u, y, info, work, factor=factor)
+    tau = torch.from_numpy(mse_target(prob).astype(np.float32)).to(dev)
+    gy = torch.zeros_like(y)
+    gy[..., 0] = 2.0 * (y[..., 0] - tau) / float(steps_per_pass)
+    torch.cuda.synchronize()
+
+    def step():
+        plan.factor_solve(c, d, s, u, y, info, work, factor=factor)
+        plan.backward(c, d, s, u, y, gy, gc, gd, gs, gu, info_b, work, factor=factor)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    n0 = Bd.launch_count()
+    Bd.profile_enable(True)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    Bd.profile_enable(False)
+    clocks = clk.summary()
+    launches = Bd.launch_count() - n0
+    barrier(ws)
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    total_ms = max_over_ranks(total_ms, ws)
+    ms_step = total_ms / args.steps
+    value = ws * steps_per_pass * args.steps / (total_ms / 1e3)
+    prof = Bd.profile_read()
+    assert int((info != 0).sum()) == 0 and int((info_b != 0).sum()) == 0, "solver reported failures"
+
+    # forward-only rate (same timing rules)
+    fw = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        fw[k][0].record(stream)
+        plan.factor_solve(c, d, s, u, y, info, work, factor=factor)
+        fw[k][1].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in fw), ws) / args.steps
+
+    # end to end through the public API with host buffers: H2D of the inputs and dl/dy,
+    # forward + adjoint, D2H of y and the four gradients, every step
+    host_in = [t.cpu().pin_memory() for t in (c, d, s, u, gy)]
+    host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (y, gc, gd, gs, gu)]
+    dev_in = [torch.empty_like(t) for t in (c, d, s, u, gy)]
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(ws)
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ee[k][0].record(stream)
+        for dt_, ht in zip(dev_in, host_in):
+            dt_.copy_(ht, non_blocking=True)
+        c2, d2, s2, u2, gy2 = dev_in
+        plan.factor_solve(c2, d2, s2, u2, y, info, work, factor=factor)
+        plan.backward(c2, d2, s2, u2, y, gy2, gc, gd, gs, gu, info_b, work, factor=factor)
+        for ht, dt_ in zip(host_out, (y, gc, gd, gs, gu)):
+            ht.copy_(dt_, non_blocking=True)
+        ee[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ee), ws) / args.steps
+    e2e_value = ws * steps_per_pass / (e2e_ms / 1e3)
+
+    # plain FP64 GPU block Cholesky of the same method, same inputs
+    fp64 = None
+    if not args.no_fp64:
+        cfg64 = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=pk.F64)
+        plan64 = pk.get_plan((prob.R, prob.B, prob.D, prob.T), cfg64)
+        c6, d6, s6, u6 = (t.double() for t in (c, d, s, u))
+        y6 = torch.empty_like(c6)
+        g6 = [torch.empty_like(t) for t in (c6, d6, s6, u6)]
+        gy6 = gy.double()
+        w6, f6 = plan64.workspace(dev), plan64.factor_buffer(dev)
+
+        def step64():
+            plan64.factor_solve(c6, d6, s6, u6, y6, info, w6, factor=f6)
+            plan64.backward(c6, d6, s6, u6, y6, gy6, *g6, info_b, w6, factor=f6)
+        for _ in range(max(3, args.warmup)):
+            step64()
+        e6 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            e6[k][0].record(stream)
+            step64()
+            e6[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(sum(a.elapsed_time(b) for a, b in e6), ws) / args.steps
+        fp64 = {"value": ws * steps_per_pass / (ms64 / 1e3), "ms_per_step": ms64,
+                "precision": "SMNN_F64"}
+
+    # roofline of the dominant kernel
+    peaks, peak_src = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("none", (1, 1.0))
+    name, (nl, tms) = dom
+    per_launch_ms = tms / max(nl, 1)
+    bound, per_step, unit = algorithmic_units(name, NB, D)
+    if bound == "alu":
+        achieved = per_step * steps_per_pass / (per_launch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s (FP64)", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "measured DFMA microbenchmark on this B300 (not in MEASURED_PEAKS.json)",
+                "per_step": per_step, "per_step_unit": "FP64 FLOP"}
+    else:
+        achieved = per_step * steps_per_pass / (per_launch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "peak_source": f"{peak_src} hbm_gbs", "per_step": per_step, "per_step_unit": "B"}
+    roof["traffic"] = None
+    roof["launch_ms"] = per_launch_ms
+    roof["share"] = tms / max(sum(v[1] for v in prof.values()), 1e-9)
+    step_bytes = (16 * NB + 8 + 8.0 / D + 8 * NB + 4 + 4.0 / D) * steps_per_pass
+    whole = {"algorithmic_GBps": step_bytes / (ms_step / 1e3) / 1e9,
+             "frac_of_hbm": step_bytes / (ms_step / 1e3) / 1e9 / peaks["hbm_gbs"],
+             "algorithmic_bytes_per_step": step_bytes / steps_per_pass}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 residual)",
+        "data": "synthetic (seeded config-2 generators: c~N(0,1), c2=1+|N|, d~N(0,1), s~U[0.01,0.1], u~N(0,1))",
+        "config": {"workload": WORKLOAD, "B": prob.B, "D": prob.D, "T": prob.T, "R": prob.R,
+                   "time_steps_per_pass": steps_per_pass, "precision": "SMNN_F32_REFINED",
+                   "max_refine": 2, "factor": "stored in forward, reused in backward",
+                   "l2": "256 MiB write between timed steps (outside the events)",
+                   "parallelism": f"replicas x{ws} (independent systems, no collective)"},
+        "fwd_only": {"value": ws * steps_per_pass / (fwd_ms / 1e3), "ms_per_step": fwd_ms},
+        "fp64_gpu": fp64,
+        "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in sorted(prof.items())},
+        "roofline": roof,
+        "whole_step_hbm": whole,
+    }
+    return out, (prob, p32, y, gc, gd, gs, gu, gy)
+
+
+# ----------------------------------------------------------------------------- oracle arm
+
+def oracle_timed(prob32, gy, systems, reps_target_s=10.0, cap_s=30.0):
+    """Oracle fwd+grad on the first `systems` systems of the FP32-rounded workload, repeated
+    until ~reps_target_s of wall time; returns (steps/s, cores, sample description, results)."""
+    import oracle as O
+    p64 = prob32.as_f64()
+    nseq = systems // prob32.D
+    sl = slice(0, nseq)
+    args = (O.Params(p64.R, p64.R_init, p64.T_init, p64.w_gov, p64.w_init, p64.w_smooth),
+            p64.c[sl], p64.d[sl], p64.s[sl], p64.u[sl], gy[sl])
+    cores = O.max_threads()
+    t0 = time.time()
+    res = O.gradient(*args)
+    reps, el = 1, time.time() - t0
+    while el < reps_target_s and el * (reps + 1) / reps < cap_s:
+        O.gradient(*args)
+        reps += 1
+        el = time.time() - t0
+    steps = nseq * prob32.D * prob32.T * reps
+    return steps / el, cores, f"{nseq * prob32.D} systems x T={prob32.T}, fwd+grad, {reps} reps, {el:.1f} s", res
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    prob = config2()
+    p32 = prob.cast(np.float32)
+    from smnn_workloads import upstream_gradient
+    gy = np.zeros_like(p32.c, dtype=np.float64)
+    gy[..., 0] = upstream_gradient(prob)[..., 0] / prob.steps
+    sample_sys = 256
+    import oracle as O
+    p64 = p32.as_f64()
+    nseq = sample_sys // prob.D
+    a = (O.Params(p64.R, p64.R_init, p64.T_init), p64.c[:nseq], p64.d[:nseq], p64.s[:nseq],
+         p64.u[:nseq], gy[:nseq])
+    for _ in range(args.warmup):
+        O.gradient(*a)
+    t0 = time.time()
+    for _ in range(args.steps):
+        O.gradient(*a)
+    el = time.time() - t0
+    steps = nseq * prob.D * prob.T * args.steps
+    v = steps / el
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded config-2 generators)",
+            "config": {"workload": WORKLOAD, "B": prob.B, "D": prob.D, "T": prob.T, "R": prob.R,
+                       "sample_per_step": f"{nseq * prob.D} of {prob.S} systems"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+                             "sample": f"{nseq * prob.D} systems x T={prob.T} per step, fwd+grad"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out, (prob, p32, y, gc, gd, gs, gu, gy) = run_ours(args, ws, rank, local)
+    if rank == 0 and not args.no_cpu_baseline:
+        gy_np = gy.double().cpu().numpy()
+        v, cores, sample, res = oracle_timed(p32, gy_np, systems=p32.S)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": sample}
+        yo, gco, gdo, gso, guo, info = res
+        def rel(a, b):
+            a = a.double().cpu().numpy().reshape(b.shape) if hasattr(a, "cpu") else a
+            return float(np.linalg.norm((a - b).reshape(-1)) / np.linalg.norm(b.reshape(-1)))
+        ys = y.double().cpu().numpy()
+        per_sys = np.linalg.norm((ys - yo).reshape(p32.S, -1), axis=1) / np.linalg.norm(yo.reshape(p32.S, -1), axis=1)
+        out["accuracy_vs_oracle"] = {"y_max_rel_l2_per_system": float(per_sys.max()),
+                                     "gc": rel(gc, gco), "gd": rel(gd, gdo), "gs": rel(gs, gso),
+                                     "gu": rel(gu, guo)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

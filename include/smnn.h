@@ -160,6 +160,23 @@ smnn_status smnn_backward(smnn_plan plan, const void* c, const void* d, const vo
                           void* gc, void* gd, void* gs, void* gu, int32_t* info,
                           void* workspace, void* stream);
 
+/* Per-kernel timing of this library's own launches, for benchmarks.  While enabled
+ * (enable != 0), every kernel launch is bracketed by two CUDA events recorded on the
+ * launch's stream; up to 65536 launches are kept, later ones are counted but not timed.
+ * smnn_profile_enable creates the events when called with enable != 0 and clears the
+ * record; it must not be called during stream capture. */
+smnn_status smnn_profile_enable(int enable);
+
+typedef struct smnn_kernel_time {
+  char name[48];          /* kernel name (template arguments stripped)             */
+  int64_t launches;       /* launches recorded while enabled                        */
+  double total_ms;        /* sum of their event-measured durations                  */
+} smnn_kernel_time;
+
+/* Synchronise on the recorded events and aggregate them by kernel name into out[0..n),
+ * at most max entries; *n receives the number of distinct kernels. */
+smnn_status smnn_profile_read(smnn_kernel_time* out, int max, int* n);
+
 /* Static string for a status code. */
 const char* smnn_status_string(smnn_status status);
 

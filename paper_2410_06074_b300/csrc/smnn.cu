@@ -30,6 +30,26 @@ namespace {
 
 std::atomic<uint64_t> g_launches{0};
 
+// ---- optional per-launch event timing (smnn_profile_enable / smnn_profile_read) ----
+constexpr int kProfMax = 65536;
+struct ProfRec { const char* name; cudaEvent_t e0, e1; };
+struct Profiler {
+  bool on = false;
+  int n = 0;
+  std::vector<ProfRec> rec;
+};
+Profiler g_prof;
+
+inline void prof_begin(const char* name, cudaStream_t st) {
+  if (g_prof.on && g_prof.n < int(g_prof.rec.size())) {
+    g_prof.rec[g_prof.n].name = name;
+    cudaEventRecord(g_prof.rec[g_prof.n].e0, st);
+  }
+}
+inline void prof_end(cudaStream_t st) {
+  if (g_prof.on && g_prof.n < int(g_prof.rec.size())) cudaEventRecord(g_prof.rec[g_prof.n++].e1, st);
+}
+
 constexpr int kThreads = 128;
 constexpr int kTopMax = 64;        // a level with at most this many steps per system is one chunk
 constexpr int kMaxLevels = 8;
@@ -690,7 +710,9 @@ inline unsigned nblocks(int64_t n) { return unsigned((n + kThreads - 1) / kThrea
 #define SMNN_LAUNCH(kern, n, st, ...)                                         \
   do {                                                                        \
     if ((n) > 0) {                                                            \
+      prof_begin(#kern, st);                                                  \
       kern<<<nblocks(n), kThreads, 0, st>>>(__VA_ARGS__);                     \
+      prof_end(st);                                                           \
       g_launches.fetch_add(1, std::memory_order_relaxed);                     \
       if (cudaGetLastError() != cudaSuccess) return SMNN_ERR_CUDA;            \
     }                                                                         \
@@ -977,5 +999,52 @@ const char* smnn_status_string(smnn_status status) {
 }
 
 uint64_t smnn_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+smnn_status smnn_profile_enable(int enable) {
+  if (enable) {
+    if (g_prof.rec.empty()) {
+      g_prof.rec.resize(kProfMax);
+      for (auto& r : g_prof.rec) {
+        if (cudaEventCreate(&r.e0) != cudaSuccess || cudaEventCreate(&r.e1) != cudaSuccess) {
+          g_prof.rec.clear();
+          return SMNN_ERR_CUDA;
+        }
+      }
+    }
+    g_prof.n = 0;
+  }
+  g_prof.on = enable != 0;
+  return SMNN_OK;
+}
+
+smnn_status smnn_profile_read(smnn_kernel_time* out, int max, int* n) {
+  if (!out || !n || max < 0) return SMNN_ERR_INVALID_ARG;
+  std::vector<smnn_kernel_time> agg;
+  for (int k = 0; k < g_prof.n; ++k) {
+    const ProfRec& r = g_prof.rec[k];
+    if (cudaEventSynchronize(r.e1) != cudaSuccess) return SMNN_ERR_CUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) return SMNN_ERR_CUDA;
+    // name: "(k_elim0<Tr, NB, true, true>)" -> "k_elim0"
+    const char* p = r.name;
+    while (*p == '(') ++p;
+    char nm[48] = {0};
+    int j = 0;
+    while (p[j] && p[j] != '<' && p[j] != ')' && j < 47) { nm[j] = p[j]; ++j; }
+    auto it = std::find_if(agg.begin(), agg.end(),
+                           [&](const smnn_kernel_time& a) { return std::strcmp(a.name, nm) == 0; });
+    if (it == agg.end()) {
+      smnn_kernel_time a{};
+      std::memcpy(a.name, nm, sizeof(nm));
+      agg.push_back(a);
+      it = agg.end() - 1;
+    }
+    it->launches += 1;
+    it->total_ms += ms;
+  }
+  *n = int(agg.size());
+  for (int k = 0; k < int(agg.size()) && k < max; ++k) out[k] = agg[k];
+  return SMNN_OK;
+}
 
 }  // extern "C"

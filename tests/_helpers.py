@@ -1,0 +1,88 @@
+"""Shared test plumbing: move a seeded Problem to the GPU, call the library through its
+binding, call the oracle on the same (rounded) inputs, and compare."""
+import numpy as np
+
+import oracle as O
+
+
+def oracle_params(prob):
+    return O.Params(prob.R, prob.R_init, prob.T_init, prob.w_gov, prob.w_init, prob.w_smooth)
+
+
+def dev(prob, dtype):
+    import torch
+    tt = torch.float64 if dtype == np.float64 else torch.float32
+    return tuple(torch.from_numpy(np.ascontiguousarray(a, dtype)).to("cuda", tt)
+                 for a in (prob.c, prob.d, prob.s, prob.u))
+
+
+def cfg_of(prob, precision, **kw):
+    from paper_2410_06074_b300 import SolveConfig
+    return SolveConfig(R_init=prob.R_init, T_init=prob.T_init, w_gov=prob.w_gov,
+                       w_init=prob.w_init, w_smooth=prob.w_smooth, precision=precision, **kw)
+
+
+def np_dtype(precision):
+    from paper_2410_06074_b300 import F64
+    return np.float64 if precision == F64 else np.float32
+
+
+def gpu_solve(prob, precision, **kw):
+    from paper_2410_06074_b300 import solve
+    dt = np_dtype(precision)
+    c, d, s, u = dev(prob, dt)
+    y, info = solve(c, d, s, u, cfg_of(prob, precision, **kw), D=prob.D, seq_T=prob.seq_T)
+    return y.double().cpu().numpy(), info.cpu().numpy()
+
+
+def gpu_grad(prob, gy, precision, store_factor=True, **kw):
+    import torch
+    from paper_2410_06074_b300 import get_plan, gradients, solve
+    from paper_2410_06074_b300.api import _shape_key
+    dt = np_dtype(precision)
+    c, d, s, u = dev(prob, dt)
+    cfg = cfg_of(prob, precision, **kw)
+    plan = get_plan(_shape_key(c, s, prob.D, prob.seq_T), cfg)
+    fac = plan.factor_buffer() if store_factor else None
+    y, info = solve(c, d, s, u, cfg, D=prob.D, seq_T=prob.seq_T, factor=fac)
+    gyt = torch.from_numpy(np.ascontiguousarray(gy, dt)).cuda()
+    gc, gd, gs, gu, info2 = gradients(c, d, s, u, y, gyt, cfg, D=prob.D, seq_T=prob.seq_T, factor=fac)
+    out = [t.double().cpu().numpy() for t in (y, gc, gd, gs, gu)]
+    return out + [info.cpu().numpy(), info2.cpu().numpy()]
+
+
+def rounded(prob, precision):
+    """The problem as the GPU sees it (inputs rounded to the working precision)."""
+    return prob.cast(np_dtype(precision)).as_f64()
+
+
+def oracle_solve(prob, nthreads=0):
+    return O.solve(oracle_params(prob), prob.c, prob.d, prob.s, prob.u, D=prob.D,
+                   seq_T=prob.seq_T, nthreads=nthreads)
+
+
+def oracle_grad(prob, gy, nthreads=0):
+    return O.gradient(oracle_params(prob), prob.c, prob.d, prob.s, prob.u, gy, D=prob.D,
+                      seq_T=prob.seq_T, nthreads=nthreads)
+
+
+def per_system(a, prob):
+    """Split a per-step array (uniform or ragged layout) into one flat vector per system."""
+    if prob.seq_T is None:
+        S = prob.B * prob.D
+        return [x.reshape(-1) for x in a.reshape(S, prob.T, -1)]
+    out, pos = [], 0
+    for Tb in prob.seq_T:
+        for _ in range(prob.D):
+            out.append(a[pos:pos + Tb].reshape(-1))
+            pos += Tb
+    return out
+
+
+def rel_err_per_system(got, ref, prob):
+    return np.array([np.linalg.norm(g - r) / max(np.linalg.norm(r), 1e-300)
+                     for g, r in zip(per_system(got, prob), per_system(ref, prob))])
+
+
+def rel_err(got, ref):
+    return float(np.linalg.norm((got - ref).reshape(-1)) / max(np.linalg.norm(ref.reshape(-1)), 1e-300))

@@ -1,0 +1,63 @@
+"""The C-ABI library loads, exports every symbol include/smnn.h declares, and rejects bad
+arguments before touching the GPU (runs on CPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "smnn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(smnn_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2410_06074_b300 import binding
+    names = declared_symbols()
+    assert len(names) >= 9
+    lib = ctypes.CDLL(binding.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in binding.SYMBOLS, n
+
+
+def test_status_strings_and_counter():
+    from paper_2410_06074_b300 import binding
+    for st in range(5):
+        assert binding.status_string(st).startswith("SMNN_")
+    assert binding.launch_count() >= 0
+
+
+@pytest.mark.parametrize("field,value", [("R", 0), ("R", 4), ("R_init", 3), ("T_init", 0),
+                                         ("precision", 7), ("algo", 5), ("max_refine", -1),
+                                         ("chunk", 1), ("reserved0", 1), ("num_seq", 0),
+                                         ("w_gov", -1.0), ("T", 0)])
+def test_plan_create_rejects_invalid_descriptors(field, value):
+    from paper_2410_06074_b300 import binding as B
+    d = B.Desc(2, 1, 1, B.F32_REFINED, B.ALGO_AUTO, 2, 0, 0, 1.0, 1.0, 1.0, 0.0, 2, 2, 16, None)
+    setattr(d, field, value)
+    h = ctypes.c_void_p()
+    assert B.lib.smnn_plan_create(ctypes.byref(d), ctypes.byref(h)) == B.SMNN_ERR_INVALID_ARG
+    assert not h.value
+
+
+def test_null_arguments_are_rejected():
+    from paper_2410_06074_b300 import binding as B
+    assert B.lib.smnn_plan_create(None, None) == B.SMNN_ERR_INVALID_ARG
+    assert B.lib.smnn_plan_destroy(None) == B.SMNN_OK
+    assert B.lib.smnn_workspace_size(None, None, None) == B.SMNN_ERR_INVALID_ARG
+    assert B.lib.smnn_factor_solve(*([None] * 10)) == B.SMNN_ERR_INVALID_ARG
+    assert B.lib.smnn_backward(*([None] * 15)) == B.SMNN_ERR_INVALID_ARG
+
+
+def test_ragged_seq_T_validation():
+    from paper_2410_06074_b300 import binding as B
+    seq = (ctypes.c_int64 * 3)(5, 0, 7)   # a zero-length sequence is invalid
+    d = B.Desc(2, 1, 1, 0, 0, 2, 0, 0, 1.0, 1.0, 1.0, 0.0, 3, 1, 0,
+               ctypes.cast(seq, ctypes.POINTER(ctypes.c_int64)))
+    h = ctypes.c_void_p()
+    assert B.lib.smnn_plan_create(ctypes.byref(d), ctypes.byref(h)) == B.SMNN_ERR_INVALID_ARG

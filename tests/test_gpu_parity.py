@@ -1,0 +1,224 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded inputs (GPU required).
+
+Tolerances (relative L2 per system unless stated):
+  SMNN_F64             1e-9   (kappa(M) ~ 1e6 on the R=2 generators; FP64 rounding ~ kappa*1e-16)
+  SMNN_F32_REFINED     1e-6   (the stated refined target; two FP64-residual sweeps)
+  SMNN_F32 unrefined   5e-3   (FP32 factor alone: ~kappa * 2^-24 in practice ~1e-3)
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from smnn_workloads import Problem, config1, random_problem, upstream_gradient
+from _helpers import (gpu_grad, gpu_solve, oracle_grad, oracle_solve, per_system, rel_err,
+                      rel_err_per_system, rounded)
+
+pytestmark = pytest.mark.gpu
+
+TOL_F64, TOL_REF, TOL_F32 = 1e-9, 1e-6, 5e-3
+
+
+def P():
+    import paper_2410_06074_b300 as pk
+    return pk
+
+
+def ragged_problem(seq_T, D=1, R=2, seed=5, s_lo=0.01, s_hi=0.1):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    seq_T = np.asarray(seq_T, np.int64)
+    N = int(D * seq_T.sum())
+    c = rng.standard_normal((N, R + 1)); c[:, R] = 1 + np.abs(c[:, R])
+    d = rng.standard_normal(N)
+    s = rng.uniform(s_lo, s_hi, int(seq_T.sum()))
+    u = rng.standard_normal((len(seq_T) * D, 1, R))
+    return Problem("ragged test", R, R - 1, 1, len(seq_T), D, None, c, d, s, u, seq_T=seq_T)
+
+
+# ----------------------------------------------------------------------------- forward
+
+@pytest.mark.parametrize("algo,chunk", [("SEQ", 0), ("CR", 0), ("CR", 4), ("CR", 7)])
+def test_config1_fp64_matches_dense_oracle(algo, chunk):
+    pk = P()
+    prob = config1()
+    y, info = gpu_solve(prob, pk.F64, algo=getattr(pk, "ALGO_" + algo), chunk=chunk)
+    yo, info_o = O.solve(O.Params(2, 1, 1), prob.c, prob.d, prob.s, prob.u, mode="dense")
+    assert (info == 0).all() and (info_o == 0).all()
+    for g, r in zip(per_system(y, prob), per_system(yo, prob)):
+        assert np.abs(g - r).max() <= TOL_F64 * np.abs(r).max()
+
+
+@pytest.mark.parametrize("T,algo,chunk", [(1000, "CR", 0), (1000, "CR", 8), (4099, "CR", 64),
+                                          (4099, "SEQ", 0), (333, "CR", 2), (64, "CR", 0)])
+def test_refined_fp32_forward(T, algo, chunk):
+    pk = P()
+    prob = random_problem(7, 3, 2, T, 2)
+    y, info = gpu_solve(prob, pk.F32_REFINED, algo=getattr(pk, "ALGO_" + algo), chunk=chunk)
+    yo, _ = oracle_solve(rounded(prob, pk.F32_REFINED))
+    assert (info == 0).all()
+    assert rel_err_per_system(y, yo, prob).max() <= TOL_REF
+
+
+@pytest.mark.parametrize("T,chunk", [(1000, 0), (2500, 16)])
+def test_fp64_forward(T, chunk):
+    pk = P()
+    prob = random_problem(8, 2, 3, T, 2)
+    y, info = gpu_solve(prob, pk.F64, chunk=chunk)
+    yo, _ = oracle_solve(prob)
+    assert rel_err_per_system(y, yo, prob).max() <= TOL_F64
+
+
+def test_unrefined_fp32_error_band():
+    pk = P()
+    prob = random_problem(9, 4, 2, 1024, 2)
+    y, info = gpu_solve(prob, pk.F32, max_refine=0)
+    yo, _ = oracle_solve(rounded(prob, pk.F32))
+    e = rel_err_per_system(y, yo, prob)
+    assert e.max() <= TOL_F32
+    y1, _ = gpu_solve(prob, pk.F32_REFINED, max_refine=1)
+    e1 = rel_err_per_system(y1, yo, prob)
+    assert e1.max() < e.max() * 0.05      # one sweep contracts the error by > 20x
+
+
+@pytest.mark.parametrize("R", [1, 3])
+def test_other_orders(R):
+    pk = P()
+    prob = random_problem(10, 2, 2, 1500, R, s_lo=0.1, s_hi=0.5)
+    y, info = gpu_solve(prob, pk.F32_REFINED)
+    yo, _ = oracle_solve(rounded(prob, pk.F32_REFINED))
+    assert (info == 0).all()
+    assert rel_err_per_system(y, yo, prob).max() <= TOL_REF
+    y, info = gpu_solve(prob, pk.F64)
+    yo, _ = oracle_solve(prob)
+    assert rel_err_per_system(y, yo, prob).max() <= TOL_F64
+
+
+def test_initial_values_over_several_steps_and_weights():
+    pk = P()
+    prob = random_problem(11, 2, 2, 700, 2, R_init=2, T_init=3, w=(0.7, 1.9, 1.3))
+    for prec, tol in ((pk.F64, TOL_F64), (pk.F32_REFINED, TOL_REF)):
+        y, info = gpu_solve(prob, prec)
+        yo, _ = oracle_solve(rounded(prob, prec))
+        assert rel_err_per_system(y, yo, prob).max() <= tol
+
+
+@pytest.mark.parametrize("seq_T", [[1, 2, 3, 5, 64, 65, 1000, 3001], [4096, 17, 2049]])
+def test_ragged_batch(seq_T):
+    pk = P()
+    prob = ragged_problem(seq_T, D=2)
+    for prec, tol in ((pk.F64, TOL_F64), (pk.F32_REFINED, TOL_REF)):
+        y, info = gpu_solve(prob, prec)
+        yo, info_o = oracle_solve(rounded(prob, prec))
+        assert (info == info_o).all()
+        assert rel_err_per_system(y, yo, prob).max() <= tol
+
+
+def test_exact_polynomial_recovery_on_gpu():
+    """Degree-<=R polynomial trajectories satisfy every row exactly (any c, any s)."""
+    pk = P()
+    R, T = 2, 2000
+    rng = np.random.Generator(np.random.PCG64(12))
+    coef = rng.standard_normal(R + 1)
+    s = rng.uniform(0.05, 0.3, T)      # kappa(M) stays ~1e6 (tiny steps make FP64 lose digits)
+    tau = np.concatenate([[0.0], np.cumsum(s[:-1])])
+    y = np.stack([np.polynomial.polynomial.polyval(tau, np.polynomial.polynomial.polyder(coef, r)
+                                                   if r else coef) for r in range(R + 1)], -1)
+    c = rng.standard_normal((T, R + 1)); c[:, R] = 1 + np.abs(c[:, R])
+    d = np.sum(c * y, axis=1)
+    prob = Problem("poly", R, 1, 1, 1, 1, T, c[None, None], d[None, None], s[None],
+                   y[None, None, :1, :2])
+    yg, info = gpu_solve(prob, pk.F64)
+    assert np.abs(yg[0, 0] - y).max() <= 1e-9 * np.abs(y).max()
+
+
+def test_assemble_matches_appendix_blocks():
+    import torch
+    from test_oracle_pins import appendix_a2_blocks
+    pk = P()
+    prob = random_problem(13, 2, 2, 50, 3, R_init=1, T_init=2, w=(1.2, 0.8, 1.5))
+    c, d, s, u = (torch.from_numpy(a).cuda() for a in (prob.c, prob.d, prob.s, prob.u))
+    cfg = pk.SolveConfig(R_init=1, T_init=2, w_gov=1.2, w_init=0.8, w_smooth=1.5, precision=pk.F64)
+    plan = pk.get_plan((3, 2, 2, 50), cfg)
+    nb, nt = 4, 10
+    M = torch.empty(2, 2, 50, nt, dtype=torch.float64, device="cuda")
+    N = torch.empty(2, 2, 50, nb * nb, dtype=torch.float64, device="cuda")
+    beta = torch.empty(2, 2, 50, nb, dtype=torch.float64, device="cuda")
+    plan.assemble(c, d, s, u, M, N, beta)
+    M, N, beta = M.cpu().numpy(), N.cpu().numpy(), beta.cpu().numpy()
+    il = np.tril_indices(nb)
+    for b in range(2):
+        for dd in range(2):
+            Ma, Na, ba = appendix_a2_blocks(3, 1, 2, 1.2, 0.8, 1.5, prob.c[b, dd], prob.d[b, dd],
+                                            prob.s[b], prob.u[b, dd])
+            order = [(i, j) for i in range(nb) for j in range(i + 1)]
+            Mp = np.stack([[Ma[t][i, j] for (i, j) in order] for t in range(50)])
+            np.testing.assert_allclose(M[b, dd], Mp, rtol=1e-13, atol=1e-14)
+            np.testing.assert_allclose(N[b, dd, :49], Na.reshape(49, -1), rtol=1e-13, atol=1e-14)
+            assert (N[b, dd, 49] == 0).all()
+            np.testing.assert_allclose(beta[b, dd], ba, rtol=1e-13, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------- failures
+
+def test_info_reports_bad_pivots_and_nan_fills():
+    pk = P()
+    prob = random_problem(14, 1, 3, 40, 2)
+    c = prob.c.copy(); c[0, 1, 9, 0] = np.nan          # system 1: NaN at 1-based step 10
+    bad = Problem("nan", 2, 1, 1, 1, 3, 40, c, prob.d, prob.s, prob.u)
+    for prec in (pk.F64, pk.F32_REFINED):
+        for chunk in (0, 4, 10):
+            y, info = gpu_solve(bad, prec, chunk=chunk)
+            assert info[1] == 10, (prec, chunk, info)
+            assert info[0] == 0 and info[2] == 0
+            assert np.isnan(y[0, 1]).all() and np.isfinite(y[0, [0, 2]]).all()
+    # T = 1 with c = 0 and w_init = 0: M = 0 exactly
+    one = random_problem(15, 1, 1, 1, 2)
+    z = Problem("zero", 2, 1, 1, 1, 1, 1, np.zeros_like(one.c), one.d, one.s, one.u, w_init=0.0)
+    y, info = gpu_solve(z, pk.F64)
+    assert info[0] == 1 and np.isnan(y).all()
+
+
+# ----------------------------------------------------------------------------- gradients
+
+@pytest.mark.parametrize("store_factor", [True, False])
+def test_gradients_fp64_match_oracle(store_factor):
+    pk = P()
+    prob = random_problem(16, 2, 3, 300, 2, T_init=2, w=(1.1, 0.9, 1.3))
+    gy = upstream_gradient(prob)
+    y, gc, gd, gs, gu, info, info2 = gpu_grad(prob, gy, pk.F64, store_factor=store_factor, chunk=8)
+    yo, gco, gdo, gso, guo, info_o = oracle_grad(prob, gy)
+    for a, b in ((y, yo), (gc, gco), (gd, gdo), (gs, gso), (gu, guo)):
+        assert rel_err(a, b) <= 1e-8, rel_err(a, b)
+
+
+@pytest.mark.parametrize("T,chunk", [(1024, 0), (777, 16)])
+def test_gradients_refined_fp32_match_oracle(T, chunk):
+    pk = P()
+    prob = random_problem(17, 2, 4, T, 2)
+    gy = upstream_gradient(prob)
+    r = rounded(prob, pk.F32_REFINED)
+    y, gc, gd, gs, gu, info, info2 = gpu_grad(prob, gy.astype(np.float32), pk.F32_REFINED, chunk=chunk)
+    yo, gco, gdo, gso, guo, _ = oracle_grad(r, gy.astype(np.float32).astype(np.float64))
+    for name, a, b in (("y", y, yo), ("gc", gc, gco), ("gd", gd, gdo), ("gs", gs, gso), ("gu", gu, guo)):
+        assert rel_err(a, b) <= TOL_REF, (name, rel_err(a, b))
+
+
+def test_saved_and_recomputed_factor_give_identical_gradients():
+    pk = P()
+    prob = random_problem(18, 2, 2, 900, 2)
+    gy = upstream_gradient(prob).astype(np.float32)
+    a = gpu_grad(prob, gy, pk.F32_REFINED, store_factor=True)
+    b = gpu_grad(prob, gy, pk.F32_REFINED, store_factor=False)
+    for x, z in zip(a[:5], b[:5]):
+        np.testing.assert_array_equal(x, z)
+
+
+def test_gradcheck_config2_slice():
+    """torch.autograd.gradcheck of SmnnSolve on the B=2, D=1, T=16 slice, FP64 path."""
+    import torch
+    from smnn_workloads import config2_slice
+    pk = P()
+    prob = config2_slice()
+    c, d, s, u = (torch.from_numpy(a).cuda().requires_grad_(True) for a in (prob.c, prob.d, prob.s, prob.u))
+    cfg = pk.SolveConfig(R_init=1, T_init=1, precision=pk.F64)
+    f = lambda c, d, s, u: pk.smnn_layer(c, d, s, u, cfg)[0]
+    assert torch.autograd.gradcheck(f, (c, d, s, u), eps=1e-6, atol=1e-6, rtol=1e-4)
