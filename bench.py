@@ -183,6 +183,55 @@ def algorithmic_units(name: str, NB: int, D: int):
 
 # ----------------------------------------------------------------------------- our arm
 
+class Variant:
+    """One precision mode of the library on the benchmark workload: its plan and buffers."""
+
+    def __init__(self, pk, prob, precision, dev, inputs, factor=True):
+        import torch
+        self.precision = precision
+        cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=precision,
+                             max_refine=2, adjoint_refine=3)
+        self.plan = pk.get_plan((prob.R, prob.B, prob.D, prob.T), cfg)
+        dt = self.plan.dtype
+        self.c, self.d, self.s, self.u = (t.to(dt) for t in inputs)
+        self.y = torch.empty_like(self.c)
+        self.info = torch.empty(self.plan.S, dtype=torch.int32, device=dev)
+        self.info_b = torch.empty_like(self.info)
+        self.work = self.plan.workspace(dev)
+        self.factor = self.plan.factor_buffer(dev) if factor else None
+        self.gc, self.gd, self.gs, self.gu = (torch.empty_like(t) for t in (self.c, self.d, self.s, self.u))
+        self.gy = None
+
+    def forward(self, c=None, d=None, s=None, u=None):
+        self.plan.factor_solve(c if c is not None else self.c, d if d is not None else self.d,
+                               s if s is not None else self.s, u if u is not None else self.u,
+                               self.y, self.info, self.work, factor=self.factor)
+
+    def backward(self, c=None, d=None, s=None, u=None, gy=None):
+        self.plan.backward(c if c is not None else self.c, d if d is not None else self.d,
+                           s if s is not None else self.s, u if u is not None else self.u,
+                           self.y, gy if gy is not None else self.gy, self.gc, self.gd, self.gs,
+                           self.gu, self.info_b, self.work, factor=self.factor)
+
+    def step(self):
+        self.forward()
+        self.backward()
+
+
+def timed(fn, steps, stream, flush):
+    """Sum of per-step CUDA-event durations; a 256 MiB write flushes L2 between steps."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        fn()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_2410_06074_b300 as pk
@@ -194,167 +243,96 @@ def run_ours(args, ws, rank, local):
     p32 = prob.cast(np.float32)
     NB, D = prob.R + 1, prob.D
     steps_per_pass = prob.steps
-    cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=pk.F32_REFINED,
-                         max_refine=2)
-    plan = pk.get_plan((prob.R, prob.B, prob.D, prob.T), cfg)
-    c, d, s, u = (torch.from_numpy(a).to(dev) for a in (p32.c, p32.d, p32.s, p32.u))
-    y = torch.empty_like(c)
-    info = torch.empty(plan.S, dtype=torch.int32, device=dev)
-    work = plan.workspace(dev)
-    factor = plan.factor_buffer(dev)
-    gc, gd, gs, gu = (torch.empty_like(t) for t in (c, d, s, u))
-    info_b = torch.empty_like(info)
-    # dl/dy of config 2's loss: mean over S*T of (y^(0) - tau)^2 at this workload's y
-    plan.factor_solve(c, d, s, u, y, info, work, factor=factor)
-    tau = torch.from_numpy(mse_target(prob).astype(np.float32)).to(dev)
-    gy = torch.zeros_like(y)
-    gy[..., 0] = 2.0 * (y[..., 0] - tau) / float(steps_per_pass)
-    torch.cuda.synchronize()
-
-    def step():
-        plan.factor_solve(c, d, s, u, y, info, work, factor=factor)
-        plan.backward(c, d, s, u, y, gy, gc, gd, gs, gu, info_b, work, factor=factor)
-
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
+    inputs = [torch.from_numpy(a).to(dev) for a in (p32.c, p32.d, p32.s, p32.u)]
     stream = torch.cuda.current_stream()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    barrier(ws)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    variants = {"F32_REFINED_DF": Variant(pk, prob, pk.F32_REFINED_DF, dev, inputs),
+                "F32_REFINED": Variant(pk, prob, pk.F32_REFINED, dev, inputs)}
+    # dl/dy of config 2's loss, mean over S*T of (y^(0) - tau)^2, at this workload's y
+    v0 = variants["F32_REFINED_DF"]
+    v0.forward()
+    tau = torch.from_numpy(mse_target(prob).astype(np.float32)).to(dev)
+    gy = torch.zeros_like(v0.y)
+    gy[..., 0] = 2.0 * (v0.y[..., 0] - tau) / float(steps_per_pass)
+    for v in variants.values():
+        v.gy = gy
+    if not args.no_fp64:
+        v64 = Variant(pk, prob, pk.F64, dev, inputs)
+        v64.gy = gy.double()
+        variants["F64"] = v64
     torch.cuda.synchronize()
-    n0 = Bd.launch_count()
-    Bd.profile_enable(True)
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            evs[k][0].record(stream)
-            step()
-            evs[k][1].record(stream)
+
+    results = {}
+    for name, v in variants.items():
+        for _ in range(args.warmup):
+            v.step()
         torch.cuda.synchronize()
-    Bd.profile_enable(False)
-    clocks = clk.summary()
-    launches = Bd.launch_count() - n0
-    barrier(ws)
-    total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    total_ms = max_over_ranks(total_ms, ws)
-    ms_step = total_ms / args.steps
-    value = ws * steps_per_pass * args.steps / (total_ms / 1e3)
-    prof = Bd.profile_read()
-    assert int((info != 0).sum()) == 0 and int((info_b != 0).sum()) == 0, "solver reported failures"
+        barrier(ws)
+        n0 = Bd.launch_count()
+        Bd.profile_enable(True)
+        with ClockSampler(local) as clk:
+            ms = timed(v.step, args.steps, stream, flush)
+        Bd.profile_enable(False)
+        launches = Bd.launch_count() - n0
+        prof = Bd.profile_read()
+        ms = max_over_ranks(ms, ws) / args.steps
+        fwd_ms = max_over_ranks(timed(v.forward, args.steps, stream, flush), ws) / args.steps
+        assert int((v.info != 0).sum()) == 0 and int((v.info_b != 0).sum()) == 0, f"{name}: solver failures"
+        results[name] = {"ms_per_step": ms, "value": ws * steps_per_pass / (ms / 1e3),
+                         "fwd_ms_per_step": fwd_ms, "fwd_value": ws * steps_per_pass / (fwd_ms / 1e3),
+                         "gpu_launches": launches, "clocks": clk.summary(), "profile": prof}
+    return prob, p32, variants, results, stream, flush, dev
 
-    # forward-only rate (same timing rules)
-    fw = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        fw[k][0].record(stream)
-        plan.factor_solve(c, d, s, u, y, info, work, factor=factor)
-        fw[k][1].record(stream)
-    torch.cuda.synchronize()
-    fwd_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in fw), ws) / args.steps
 
-    # end to end through the public API with host buffers: H2D of the inputs and dl/dy,
-    # forward + adjoint, D2H of y and the four gradients, every step
-    host_in = [t.cpu().pin_memory() for t in (c, d, s, u, gy)]
-    host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (y, gc, gd, gs, gu)]
-    dev_in = [torch.empty_like(t) for t in (c, d, s, u, gy)]
+def e2e_and_roofline(prob, v, res, ws, args, stream, flush):
+    """End-to-end rate through the public API with host buffers, and the roofline of the
+    dominant kernel of variant v."""
+    import torch
+    NB, D, steps_per_pass = prob.R + 1, prob.D, prob.steps
+    host_in = [t.cpu().pin_memory() for t in (v.c, v.d, v.s, v.u, v.gy)]
+    host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (v.y, v.gc, v.gd, v.gs, v.gu)]
+    dev_in = [torch.empty_like(t) for t in (v.c, v.d, v.s, v.u, v.gy)]
     h2d = sum(t.numel() * t.element_size() for t in host_in)
     d2h = sum(t.numel() * t.element_size() for t in host_out)
-    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    barrier(ws)
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        ee[k][0].record(stream)
+
+    def e2e_step():
         for dt_, ht in zip(dev_in, host_in):
             dt_.copy_(ht, non_blocking=True)
         c2, d2, s2, u2, gy2 = dev_in
-        plan.factor_solve(c2, d2, s2, u2, y, info, work, factor=factor)
-        plan.backward(c2, d2, s2, u2, y, gy2, gc, gd, gs, gu, info_b, work, factor=factor)
-        for ht, dt_ in zip(host_out, (y, gc, gd, gs, gu)):
+        v.forward(c2, d2, s2, u2)
+        v.backward(c2, d2, s2, u2, gy2)
+        for ht, dt_ in zip(host_out, (v.y, v.gc, v.gd, v.gs, v.gu)):
             ht.copy_(dt_, non_blocking=True)
-        ee[k][1].record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ee), ws) / args.steps
-    e2e_value = ws * steps_per_pass / (e2e_ms / 1e3)
+    e2e_step()
+    barrier(ws)
+    e2e_ms = max_over_ranks(timed(e2e_step, args.steps, stream, flush), ws) / args.steps
 
-    # plain FP64 GPU block Cholesky of the same method, same inputs
-    fp64 = None
-    if not args.no_fp64:
-        cfg64 = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=pk.F64)
-        plan64 = pk.get_plan((prob.R, prob.B, prob.D, prob.T), cfg64)
-        c6, d6, s6, u6 = (t.double() for t in (c, d, s, u))
-        y6 = torch.empty_like(c6)
-        g6 = [torch.empty_like(t) for t in (c6, d6, s6, u6)]
-        gy6 = gy.double()
-        w6, f6 = plan64.workspace(dev), plan64.factor_buffer(dev)
-
-        def step64():
-            plan64.factor_solve(c6, d6, s6, u6, y6, info, w6, factor=f6)
-            plan64.backward(c6, d6, s6, u6, y6, gy6, *g6, info_b, w6, factor=f6)
-        for _ in range(max(3, args.warmup)):
-            step64()
-        e6 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            e6[k][0].record(stream)
-            step64()
-            e6[k][1].record(stream)
-        torch.cuda.synchronize()
-        ms64 = max_over_ranks(sum(a.elapsed_time(b) for a, b in e6), ws) / args.steps
-        fp64 = {"value": ws * steps_per_pass / (ms64 / 1e3), "ms_per_step": ms64,
-                "precision": "SMNN_F64"}
-
-    # roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("none", (1, 1.0))
-    name, (nl, tms) = dom
+    prof = res["profile"]
+    name, (nl, tms) = max(prof.items(), key=lambda kv: kv[1][1])
     per_launch_ms = tms / max(nl, 1)
     bound, per_step, unit = algorithmic_units(name, NB, D)
     if bound == "alu":
         achieved = per_step * steps_per_pass / (per_launch_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s (FP64)", "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "measured DFMA microbenchmark on this B300 (not in MEASURED_PEAKS.json)",
-                "per_step": per_step, "per_step_unit": "FP64 FLOP"}
+                "peak_source": "measured DFMA microbenchmark on this B300 (not in MEASURED_PEAKS.json)"}
     else:
         achieved = per_step * steps_per_pass / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "peak_source": f"{peak_src} hbm_gbs", "per_step": per_step, "per_step_unit": "B"}
-    roof["traffic"] = None
-    roof["launch_ms"] = per_launch_ms
-    roof["share"] = tms / max(sum(v[1] for v in prof.values()), 1e-9)
-    step_bytes = (16 * NB + 8 + 8.0 / D + 8 * NB + 4 + 4.0 / D) * steps_per_pass
-    whole = {"algorithmic_GBps": step_bytes / (ms_step / 1e3) / 1e9,
-             "frac_of_hbm": step_bytes / (ms_step / 1e3) / 1e9 / peaks["hbm_gbs"],
-             "algorithmic_bytes_per_step": step_bytes / steps_per_pass}
-
-    out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 residual)",
-        "data": "synthetic (seeded config-2 generators: c~N(0,1), c2=1+|N|, d~N(0,1), s~U[0.01,0.1], u~N(0,1))",
-        "config": {"workload": WORKLOAD, "B": prob.B, "D": prob.D, "T": prob.T, "R": prob.R,
-                   "time_steps_per_pass": steps_per_pass, "precision": "SMNN_F32_REFINED",
-                   "max_refine": 2, "factor": "stored in forward, reused in backward",
-                   "l2": "256 MiB write between timed steps (outside the events)",
-                   "parallelism": f"replicas x{ws} (independent systems, no collective)"},
-        "fwd_only": {"value": ws * steps_per_pass / (fwd_ms / 1e3), "ms_per_step": fwd_ms},
-        "fp64_gpu": fp64,
-        "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches,
-        "clocks": clocks,
-        "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in sorted(prof.items())},
-        "roofline": roof,
-        "whole_step_hbm": whole,
-    }
-    return out, (prob, p32, y, gc, gd, gs, gu, gy)
+                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"}
+    roof.update({"traffic": None, "per_step": per_step, "per_step_unit": unit,
+                 "launch_ms": per_launch_ms,
+                 "share": tms / max(sum(x[1] for x in prof.values()), 1e-9)})
+    step_bytes = (16 * NB + 8 + 8.0 / D + 8 * NB + 4 + 4.0 / D)
+    whole = {"algorithmic_bytes_per_step": step_bytes,
+             "algorithmic_GBps": step_bytes * steps_per_pass / (res["ms_per_step"] / 1e3) / 1e9}
+    whole["frac_of_hbm"] = whole["algorithmic_GBps"] / peaks["hbm_gbs"]
+    e2e = {"value": ws * steps_per_pass / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    return e2e, roof, whole
 
 
 # ----------------------------------------------------------------------------- oracle arm
@@ -413,6 +391,17 @@ def run_reference(args, ws, rank):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def accuracy(v, oracle_res, S):
+    yo, gco, gdo, gso, guo, _ = oracle_res
+    def rel(t, ref):
+        a = t.double().cpu().numpy().reshape(ref.shape)
+        return float(np.linalg.norm((a - ref).ravel()) / np.linalg.norm(ref.ravel()))
+    ys = v.y.double().cpu().numpy()
+    per = np.linalg.norm((ys - yo).reshape(S, -1), axis=1) / np.linalg.norm(yo.reshape(S, -1), axis=1)
+    return {"y_max_rel_l2_per_system": float(per.max()), "gc": rel(v.gc, gco), "gd": rel(v.gd, gdo),
+            "gs": rel(v.gs, gso), "gu": rel(v.gu, guo)}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
@@ -421,21 +410,49 @@ def main():
         if out is not None:
             print(json.dumps(out), flush=True)
         return
-    out, (prob, p32, y, gc, gd, gs, gu, gy) = run_ours(args, ws, rank, local)
+    prob, p32, variants, results, stream, flush, dev = run_ours(args, ws, rank, local)
+    # accuracy of every variant against the FP64 oracle on the full workload (rank 0)
+    cpu = None
+    acc = {}
     if rank == 0 and not args.no_cpu_baseline:
-        gy_np = gy.double().cpu().numpy()
-        v, cores, sample, res = oracle_timed(p32, gy_np, systems=p32.S)
-        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": sample}
-        yo, gco, gdo, gso, guo, info = res
-        def rel(a, b):
-            a = a.double().cpu().numpy().reshape(b.shape) if hasattr(a, "cpu") else a
-            return float(np.linalg.norm((a - b).reshape(-1)) / np.linalg.norm(b.reshape(-1)))
-        ys = y.double().cpu().numpy()
-        per_sys = np.linalg.norm((ys - yo).reshape(p32.S, -1), axis=1) / np.linalg.norm(yo.reshape(p32.S, -1), axis=1)
-        out["accuracy_vs_oracle"] = {"y_max_rel_l2_per_system": float(per_sys.max()),
-                                     "gc": rel(gc, gco), "gd": rel(gd, gdo), "gs": rel(gs, gso),
-                                     "gu": rel(gu, guo)}
+        gy_np = variants["F32_REFINED_DF"].gy.double().cpu().numpy()
+        v_cpu, cores, sample, ores = oracle_timed(p32, gy_np, systems=p32.S)
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        for name, v in variants.items():
+            acc[name] = accuracy(v, ores, p32.S)
+    ok = [n for n in ("F32_REFINED_DF", "F32_REFINED")
+          if n in acc and max(acc[n].values()) <= 1e-6]
+    pool = ok if ok else ["F32_REFINED"]
+    head = max(pool, key=lambda n: results[n]["value"])
+    r = results[head]
+    e2e, roof, whole = e2e_and_roofline(prob, variants[head], r, ws, args, stream, flush)
+    prec_txt = {"F32_REFINED_DF": "FP32 factor + float-float residual refinement",
+                "F32_REFINED": "FP32 factor + FP64 residual refinement"}[head]
+    out = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (float-float residual)" if head == "F32_REFINED_DF" else "f32 (f64 residual)",
+        "data": "synthetic (seeded config-2 generators: c~N(0,1), c2=1+|N|, d~N(0,1), s~U[0.01,0.1], u~N(0,1))",
+        "config": {"workload": WORKLOAD, "B": prob.B, "D": prob.D, "T": prob.T, "R": prob.R,
+                   "time_steps_per_pass": prob.steps, "precision": "SMNN_" + head,
+                   "solver": prec_txt, "max_refine": 2, "adjoint_refine": 3,
+                   "factor": "stored in forward, reused in backward",
+                   "l2": "256 MiB write between timed steps (outside the events)",
+                   "parallelism": f"replicas x{ws} (independent systems, no collective)"},
+        "fwd_only": {"value": r["fwd_value"], "ms_per_step": r["fwd_ms_per_step"]},
+        "e2e": e2e,
+        "gpu_launches": r["gpu_launches"],
+        "clocks": r["clocks"],
+        "roofline": roof,
+        "whole_step_hbm": whole,
+        "variants": {n: {k: x[k] for k in ("value", "ms_per_step", "fwd_value", "fwd_ms_per_step")}
+                     for n, x in results.items()},
+        "kernels": {k: {"launches": x[0], "total_ms": x[1]} for k, x in sorted(r["profile"].items())},
+        "accuracy_vs_oracle": acc,
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(out), flush=True)
 

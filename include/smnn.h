@@ -60,12 +60,16 @@ typedef enum {
 } smnn_status;
 
 typedef enum {
-  /* FP32 factorisation and substitution, accuracy won back by max_refine sweeps of
-   * iterative refinement whose residual r = beta - M y is evaluated in FP64 from the
-   * FP32 inputs (float arrays). */
+  /* FP32 factorisation and substitution, accuracy won back by iterative refinement whose
+   * residual r = beta - M y is evaluated in FP64 from the FP32 inputs; the refined
+   * solutions are accumulated as float-float pairs (float arrays). */
   SMNN_F32_REFINED = 0,
   SMNN_F32 = 1,   /* FP32 factorisation and substitution only (float arrays)         */
-  SMNN_F64 = 2    /* plain FP64 block Cholesky of the same method (double arrays)    */
+  SMNN_F64 = 2,   /* plain FP64 block Cholesky of the same method (double arrays)    */
+  /* As SMNN_F32_REFINED, but the residual and the gradient formulas are evaluated in
+   * float-float arithmetic (pairs of FP32 numbers combined with error-free
+   * transformations, ~48-bit significand) on the FP32 pipe instead of in FP64. */
+  SMNN_F32_REFINED_DF = 3
 } smnn_precision;
 
 typedef enum {
@@ -80,9 +84,10 @@ typedef struct smnn_desc {
   int32_t T_init;         /* initial values for steps 1..T_init, 1 <= T_init <= T_b */
   int32_t precision;      /* smnn_precision                                         */
   int32_t algo;           /* smnn_algo                                              */
-  int32_t max_refine;     /* refinement sweeps for SMNN_F32_REFINED, 0..16          */
+  int32_t max_refine;     /* forward refinement sweeps (refined modes), 0..16       */
   int32_t chunk;          /* level-0 chunk length for SMNN_ALGO_CR, 0 = autotuned   */
-  int32_t reserved0;      /* must be 0                                              */
+  int32_t adjoint_refine; /* refinement sweeps of the adjoint solve, 0..16; when > 0 */
+                          /* the backward also refines y once before the gradients  */
   double w_gov;           /* importance weights of Eq. 9 (unsquared; W holds their  */
   double w_init;          /*   squares, App. A.1), >= 0                             */
   double w_smooth;

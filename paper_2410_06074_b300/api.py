@@ -27,6 +27,7 @@ class SolveConfig:
     precision: int = B.F32_REFINED
     algo: int = B.ALGO_AUTO
     max_refine: int = 2
+    adjoint_refine: int = 3
     chunk: int = 0
     refine_tol: float = 0.0
     factor_budget_bytes: int = 16 << 30   # store the factor for backward if it fits
@@ -42,6 +43,7 @@ def get_plan(shape_key, cfg: SolveConfig) -> B.Plan:
         plan = B.Plan(R=R, R_init=cfg.R_init, T_init=cfg.T_init, B=Bn, D=D,
                       T=None if ragged else T, seq_T=T if ragged else None,
                       precision=cfg.precision, algo=cfg.algo, max_refine=cfg.max_refine,
+                      adjoint_refine=cfg.adjoint_refine,
                       chunk=cfg.chunk, w_gov=cfg.w_gov, w_init=cfg.w_init, w_smooth=cfg.w_smooth,
                       refine_tol=cfg.refine_tol)
         _PLANS[key] = plan

@@ -17,7 +17,7 @@ from . import _build
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
 SMNN_OK, SMNN_ERR_INVALID_ARG, SMNN_ERR_WORKSPACE, SMNN_ERR_CUDA, SMNN_ERR_UNSUPPORTED = range(5)
-F32_REFINED, F32, F64 = 0, 1, 2
+F32_REFINED, F32, F64, F32_REFINED_DF = 0, 1, 2, 3
 ALGO_AUTO, ALGO_SEQ, ALGO_CR = 0, 1, 2
 SMNN_MAX_R = 3
 
@@ -32,7 +32,7 @@ class Desc(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int32), ("R_init", ctypes.c_int32), ("T_init", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("algo", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("w_gov", ctypes.c_double),
+                ("adjoint_refine", ctypes.c_int32), ("w_gov", ctypes.c_double),
                 ("w_init", ctypes.c_double), ("w_smooth", ctypes.c_double),
                 ("refine_tol", ctypes.c_double), ("num_seq", ctypes.c_int64),
                 ("dims_per_seq", ctypes.c_int64), ("T", ctypes.c_int64),
@@ -135,6 +135,7 @@ class Plan:
     precision: int = F32_REFINED
     algo: int = ALGO_AUTO
     max_refine: int = 2
+    adjoint_refine: int = 3
     chunk: int = 0
     w_gov: float = 1.0
     w_init: float = 1.0
@@ -148,7 +149,7 @@ class Plan:
             self.seq_T = tuple(int(x) for x in self.seq_T)
             seq = (ctypes.c_int64 * len(self.seq_T))(*self.seq_T)
         d = Desc(self.R, self.R_init, self.T_init, self.precision, self.algo, self.max_refine,
-                 self.chunk, 0, self.w_gov, self.w_init, self.w_smooth, self.refine_tol, self.B,
+                 self.chunk, self.adjoint_refine, self.w_gov, self.w_init, self.w_smooth, self.refine_tol, self.B,
                  self.D, int(self.T or 0), ctypes.cast(seq, ctypes.POINTER(ctypes.c_int64)))
         h = ctypes.c_void_p()
         _check(lib.smnn_plan_create(ctypes.byref(d), ctypes.byref(h)), "smnn_plan_create")

@@ -23,6 +23,7 @@
 
 #include "../../include/smnn.h"
 #include "smnn_chunk.cuh"
+#include "smnn_num.cuh"
 
 using namespace smnn;
 
@@ -206,32 +207,52 @@ __global__ void __launch_bounds__(kThreads) k_backsubN(LevelTables lt, LevelBufs
                         k > 0 ? lb.xsep + (g - 1) * NB : nullptr, emit);
 }
 
-// Emit functor of level-0 back substitution: y (or y += dy), NaN for failed systems,
-// and optionally the squared norms of dy and y for the refinement stop test.
-template <class Tr, int NB, bool kAccum>
-struct EmitY {
+// Level-0 output of a solve pass.  mode 0: y = x (the plain FP32/FP64 result).  mode 1
+// (FP32 refinement): a float-float accumulator acc = base + x, where base is the previous
+// accumulator (in-place sweep), the caller's FP32 y (first sweep of the adjoint's
+// re-refinement of y), or zero (initial solve); optionally also writes the caller's y as
+// the rounded accumulator, and the squared norms of x and acc for the stop test.
+template <class Tr>
+struct Level0Out {
   Tr* y;
+  float* acc_hi;
+  float* acc_lo;
+  const Tr* base_hi;
+  const float* base_lo;
+  double* nrm;
+};
+
+template <class Tr, int NB, int kMode>
+struct EmitY {
+  Level0Out<Tr> o;
+  int64_t base;  // first step of this system
   bool failed;
   double dd, yy;
   __device__ void operator()(int64_t t, const Tr (&v)[NB]) {
+    const int64_t at = (base + t) * NB;
 #pragma unroll
     for (int a = 0; a < NB; ++a) {
-      Tr out = v[a];
-      if (kAccum) {
-        const Tr yo = y[t * NB + a];
-        out = yo + v[a];
+      if (kMode == 0) {
+        o.y[at + a] = failed ? nan_t<Tr>() : v[a];
+      } else {
+        ff acc = o.base_hi ? ff{float(o.base_hi[at + a]), o.base_lo ? o.base_lo[at + a] : 0.f}
+                           : ff{0.f, 0.f};
+        acc = acc + float(v[a]);
+        if (failed) acc = ff{nan_t<float>(), nan_t<float>()};
+        o.acc_hi[at + a] = acc.hi;
+        o.acc_lo[at + a] = acc.lo;
+        if (o.y) o.y[at + a] = Tr(acc.hi);
         dd += double(v[a]) * double(v[a]);
-        yy += double(out) * double(out);
+        yy += double(acc.hi) * double(acc.hi);
       }
-      y[t * NB + a] = failed ? nan_t<Tr>() : out;
     }
   }
 };
 
-template <class Tr, int NB, bool kAccum>
+template <class Tr, int NB, int kMode>
 __global__ void __launch_bounds__(kThreads) k_backsub0(LevelTables lt, LevelBufs<Tr, NB> lb,
-                                                       Problem0 p, Tr* y, const int32_t* info,
-                                                       double* nrm) {
+                                                       Problem0 p, Level0Out<Tr> o,
+                                                       const int32_t* info) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
   const int64_t i = lt.csys[g];
@@ -240,12 +261,12 @@ __global__ void __launch_bounds__(kThreads) k_backsub0(LevelTables lt, LevelBufs
   const int64_t first = k * lt.L;
   const int64_t last = min(first + lt.L, T) - 1;
   const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, nullptr, i, lt.base[i], T);
-  EmitY<Tr, NB, kAccum> emit{y + lt.base[i] * NB, info[i] > 0, 0.0, 0.0};
+  EmitY<Tr, NB, kMode> emit{o, lt.base[i], info[i] > 0, 0.0, 0.0};
   backsub_chunk<Tr, NB>(src, first, last, k > 0, lb.fac, g, lb.xsep + g * NB,
                         k > 0 ? lb.xsep + (g - 1) * NB : nullptr, emit);
-  if (kAccum && nrm) {
-    atomicAdd(nrm + 2 * i, emit.dd);
-    atomicAdd(nrm + 2 * i + 1, emit.yy);
+  if (kMode == 1 && o.nrm) {
+    atomicAdd(o.nrm + 2 * i, emit.dd);
+    atomicAdd(o.nrm + 2 * i + 1, emit.yy);
   }
 }
 
@@ -256,26 +277,40 @@ __global__ void k_refine_check(const double* nrm, int64_t S, double tol, int32_t
   if (info[i] == 0 && !(dd <= tol * tol * yy)) info[i] = -1;
 }
 
-// ---- FP64 residual of the refinement ------------------------------------------------
-// (P v)_r = sum_k coef[k] v_{r+k},  (P^T v)_r = sum_k coef[k] v_{r-k},  coef[k] = (+-s)^k/k!
-template <int NB>
-__device__ __forceinline__ void taylor_fw(const double (&cf)[NB], const double (&v)[NB], double (&o)[NB]) {
+// ---- refinement residual, in FP64 or float-float ------------------------------------
+// cf[k] = (+-s)^k / k!;  (P v)_r = sum_k cf[k] v_{r+k},  (P^T v)_r = sum_k cf[k] v_{r-k}
+template <class N, int NB>
+__device__ __forceinline__ void taylor_fw(const N (&cf)[NB], const N (&v)[NB], N (&o)[NB]) {
 #pragma unroll
   for (int r = 0; r < NB; ++r) {
-    double acc = v[NB - 1] * cf[NB - 1 - r];
+    N acc = v[r];
 #pragma unroll
-    for (int q = NB - 2; q >= r; --q) acc = fma(cf[q - r], v[q], acc);
+    for (int k = 1; r + k < NB; ++k) acc = acc + cf[k] * v[r + k];
     o[r] = acc;
   }
 }
-template <int NB>
-__device__ __forceinline__ void taylor_tr(const double (&cf)[NB], const double (&v)[NB], double (&o)[NB]) {
+template <class N, int NB>
+__device__ __forceinline__ void taylor_tr(const N (&cf)[NB], const N (&v)[NB], N (&o)[NB]) {
 #pragma unroll
   for (int r = 0; r < NB; ++r) {
-    double acc = v[0] * cf[r];
+    N acc = v[r];
 #pragma unroll
-    for (int q = 1; q <= r; ++q) acc = fma(cf[r - q], v[q], acc);
+    for (int k = 1; k <= r; ++k) acc = acc + cf[k] * v[r - k];
     o[r] = acc;
+  }
+}
+
+// exp(+-sN) Taylor coefficients for one step size
+template <class N, int NB>
+__device__ __forceinline__ void taylor_coefs(float s, N (&cp)[NB], N (&cm)[NB]) {
+  cp[0] = Num<N>::from_f(1.f);
+  cm[0] = cp[0];
+  N pk = cp[0];
+#pragma unroll
+  for (int k = 1; k < NB; ++k) {
+    pk = pk * s;
+    cp[k] = k <= 2 ? pk * float(inv_fact(k)) : pk * inv_fact_n<N>(k);
+    cm[k] = (k & 1) ? -cp[k] : cp[k];
   }
 }
 
@@ -283,33 +318,25 @@ __device__ __forceinline__ void taylor_tr(const double (&cf)[NB], const double (
 // w_r = w_s^2 s^{2r}) to -(M x)_t and -(M x)_{t+1}: with e+ = exp(sN) x_t - x_{t+1} and
 // e- = exp(-sN) x_{t+1} - x_t (the rows' values),
 //   -(M x)_t     += w.e- - exp(sN)^T (w.e+),   -(M x)_{t+1} += w.e+ - exp(-sN)^T (w.e-).
-template <int NB>
-__device__ __forceinline__ void smooth_pair_residual(double s, double ws2, const double (&xa)[NB],
-                                                     const double (&xb)[NB], double (&ra)[NB],
-                                                     double (&rb)[NB]) {
-  double cp[NB], cm[NB], w[NB];
-  cp[0] = 1.0; cm[0] = 1.0;
-  double pk = 1.0;
-#pragma unroll
-  for (int k = 1; k < NB; ++k) {
-    pk *= s;
-    cp[k] = pk * inv_fact(k);
-    cm[k] = (k & 1) ? -cp[k] : cp[k];
-  }
+template <class N, int NB>
+__device__ __forceinline__ void smooth_pair_residual(float s, N ws2, const N (&xa)[NB],
+                                                     const N (&xb)[NB], N (&ra)[NB], N (&rb)[NB]) {
+  N cp[NB], cm[NB], w[NB];
+  taylor_coefs<N, NB>(s, cp, cm);
   w[0] = ws2;
-  const double s2 = s * s;
+  const N s2 = Num<N>::from_f(s) * s;
 #pragma unroll
   for (int r = 1; r < NB; ++r) w[r] = w[r - 1] * s2;
-  double pa[NB], qb[NB], vp[NB], vm[NB], tp[NB], tm[NB];
-  taylor_fw<NB>(cp, xa, pa);
-  taylor_fw<NB>(cm, xb, qb);
+  N pa[NB], qb[NB], vp[NB], vm[NB], tp[NB], tm[NB];
+  taylor_fw<N, NB>(cp, xa, pa);
+  taylor_fw<N, NB>(cm, xb, qb);
 #pragma unroll
   for (int r = 0; r < NB; ++r) {
     vp[r] = w[r] * (pa[r] - xb[r]);
     vm[r] = w[r] * (qb[r] - xa[r]);
   }
-  taylor_tr<NB>(cp, vp, tp);
-  taylor_tr<NB>(cm, vm, tm);
+  taylor_tr<N, NB>(cp, vp, tp);
+  taylor_tr<N, NB>(cm, vm, tm);
 #pragma unroll
   for (int r = 0; r < NB; ++r) {
     ra[r] = vm[r] - tp[r];
@@ -317,9 +344,12 @@ __device__ __forceinline__ void smooth_pair_residual(double s, double ws2, const
   }
 }
 
-template <int NB>
-__global__ void __launch_bounds__(kThreads) k_residual(LevelTables lt, Problem0 p, const float* x,
-                                                       const float* rhs, float* r_out) {
+// r = rhs - M x for one chunk of steps, rhs = beta (assembled, rhs == nullptr) or an explicit
+// vector; x given as float-float parts (x_lo may be null).  Result rounded to FP32.
+template <class N, int NB>
+__global__ void __launch_bounds__(kThreads) k_residual(LevelTables lt, Problem0 p, const float* x_hi,
+                                                       const float* x_lo, const float* rhs,
+                                                       float* r_out) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
   const int64_t i = lt.csys[g];
@@ -332,52 +362,60 @@ __global__ void __launch_bounds__(kThreads) k_residual(LevelTables lt, Problem0 
   const float* d = static_cast<const float*>(p.d) + base;
   const float* s = static_cast<const float*>(p.s) + p.soff[i];
   const float* u = static_cast<const float*>(p.u) + i * int64_t(p.T_init) * (p.R_init + 1);
-  const float* xs = x + base * NB;
+  const float* xh = x_hi + base * NB;
+  const float* xl = x_lo ? x_lo + base * NB : nullptr;
   const float* rh = rhs ? rhs + base * NB : nullptr;
   float* ro = r_out + base * NB;
+  const N wg2 = Num<N>::from_d(p.wg2), wi2 = Num<N>::from_d(p.wi2), ws2 = Num<N>::from_d(p.ws2);
+  auto load = [&](int64_t t, N (&v)[NB]) {
+#pragma unroll
+    for (int a = 0; a < NB; ++a) v[a] = Num<N>::pair(xh[t * NB + a], xl ? xl[t * NB + a] : 0.f);
+  };
 
-  double xc[NB], carry[NB];
+  N xc[NB], carry[NB];
+  load(first, xc);
 #pragma unroll
-  for (int a = 0; a < NB; ++a) { xc[a] = double(xs[first * NB + a]); carry[a] = 0.0; }
+  for (int a = 0; a < NB; ++a) carry[a] = Num<N>::zero();
   if (first > 0) {
-    double xp[NB], dummy[NB];
-#pragma unroll
-    for (int a = 0; a < NB; ++a) xp[a] = double(xs[(first - 1) * NB + a]);
-    smooth_pair_residual<NB>(double(s[first - 1]), p.ws2, xp, xc, dummy, carry);
+    N xp[NB], dummy[NB];
+    load(first - 1, xp);
+    smooth_pair_residual<N, NB>(s[first - 1], ws2, xp, xc, dummy, carry);
   }
   for (int64_t t = first; t <= last; ++t) {
-    double r[NB], cv[NB];
-    double cx = 0.0;
+    N r[NB];
+    float cv[NB];
+    N cx = Num<N>::zero();
 #pragma unroll
     for (int a = 0; a < NB; ++a) {
-      cv[a] = double(c[t * NB + a]);
-      cx = fma(cv[a], xc[a], cx);
+      cv[a] = c[t * NB + a];
+      cx = cx + xc[a] * cv[a];
     }
     if (rh) {
-      const double gres = -p.wg2 * cx;  // beta replaced by the explicit right-hand side
+      const N gres = -(wg2 * cx);   // beta replaced by the explicit right-hand side
 #pragma unroll
-      for (int a = 0; a < NB; ++a) r[a] = fma(gres, cv[a], double(rh[t * NB + a])) + carry[a];
+      for (int a = 0; a < NB; ++a) r[a] = (gres * cv[a] + rh[t * NB + a]) + carry[a];
     } else {
-      const double gres = p.wg2 * (double(d[t]) - cx);  // w_g^2 c_t (d_t - c_t . x_t)
+      const N gres = wg2 * (cx - d[t]);  // -w_g^2 (d_t - c_t . x_t)
 #pragma unroll
-      for (int a = 0; a < NB; ++a) r[a] = fma(gres, cv[a], carry[a]);
+      for (int a = 0; a < NB; ++a) r[a] = carry[a] - gres * cv[a];
     }
     if (t < p.T_init) {
 #pragma unroll
       for (int a = 0; a < NB; ++a)
-        if (a <= p.R_init)
-          r[a] += p.wi2 * ((rh ? 0.0 : double(u[t * (p.R_init + 1) + a])) - xc[a]);
+        if (a <= p.R_init) {  // w_i^2 (u - x), u replaced by 0 for an explicit rhs
+          const N dv = rh ? -xc[a] : -(xc[a] - u[t * (p.R_init + 1) + a]);
+          r[a] = r[a] + wi2 * dv;
+        }
     }
     if (t + 1 < T) {
-      double xn[NB], ra[NB];
+      N xn[NB], ra[NB];
+      load(t + 1, xn);
+      smooth_pair_residual<N, NB>(s[t], ws2, xc, xn, ra, carry);
 #pragma unroll
-      for (int a = 0; a < NB; ++a) xn[a] = double(xs[(t + 1) * NB + a]);
-      smooth_pair_residual<NB>(double(s[t]), p.ws2, xc, xn, ra, carry);
-#pragma unroll
-      for (int a = 0; a < NB; ++a) { r[a] += ra[a]; xc[a] = xn[a]; }
+      for (int a = 0; a < NB; ++a) { r[a] = r[a] + ra[a]; xc[a] = xn[a]; }
     }
 #pragma unroll
-    for (int a = 0; a < NB; ++a) ro[t * NB + a] = float(r[a]);
+    for (int a = 0; a < NB; ++a) ro[t * NB + a] = Num<N>::to_f(r[a]);
   }
 }
 
@@ -393,44 +431,52 @@ struct GradTables {
   int D;
 };
 
+template <class N> __device__ __forceinline__ N ld_n(float v) { return Num<N>::from_f(v); }
+template <class N> __device__ __forceinline__ N ld_n(double v) { return Num<N>::from_d(v); }
+template <class N> __device__ __forceinline__ N ld_pair(const float* hi, const float* lo, int64_t k) {
+  return Num<N>::pair(hi[k], lo ? lo[k] : 0.f);
+}
+template <class N> __device__ __forceinline__ N ld_pair(const double* hi, const float*, int64_t k) {
+  return Num<N>::from_d(hi[k]);
+}
+template <class Tr, class N> __device__ __forceinline__ Tr st_n(N v);
+template <> __device__ __forceinline__ float st_n<float, double>(double v) { return float(v); }
+template <> __device__ __forceinline__ float st_n<float, ff>(ff v) { return Num<ff>::to_f(v); }
+template <> __device__ __forceinline__ double st_n<double, double>(double v) { return v; }
+
 // -w_s^2 d/ds sum_r s^{2r} (f+_r e+_r + f-_r e-_r) for the pair (t, t+1), g and y held fixed.
-template <int NB>
-__device__ __forceinline__ double smooth_pair_grad(double s, double ws2, const double (&ya)[NB],
-                                                   const double (&yb)[NB], const double (&ga)[NB],
-                                                   const double (&gb)[NB]) {
-  double cp[NB], cm[NB];
-  cp[0] = 1.0; cm[0] = 1.0;
-  double pk = 1.0;
-#pragma unroll
-  for (int k = 1; k < NB; ++k) {
-    pk *= s;
-    cp[k] = pk * inv_fact(k);
-    cm[k] = (k & 1) ? -cp[k] : cp[k];
-  }
-  double pya[NB], pga[NB], qyb[NB], qgb[NB];
-  taylor_fw<NB>(cp, ya, pya);
-  taylor_fw<NB>(cp, ga, pga);
-  taylor_fw<NB>(cm, yb, qyb);
-  taylor_fw<NB>(cm, gb, qgb);
-  double acc = 0.0;
-  double s2r = 1.0;     // s^{2r}
-  double ds2r = 0.0;    // d/ds s^{2r} = 2r s^{2r-1}
+template <class N, int NB>
+__device__ __forceinline__ N smooth_pair_grad(float s, N ws2, const N (&ya)[NB], const N (&yb)[NB],
+                                              const N (&ga)[NB], const N (&gb)[NB]) {
+  N cp[NB], cm[NB];
+  taylor_coefs<N, NB>(s, cp, cm);
+  N pya[NB], pga[NB], qyb[NB], qgb[NB];
+  taylor_fw<N, NB>(cp, ya, pya);
+  taylor_fw<N, NB>(cp, ga, pga);
+  taylor_fw<N, NB>(cm, yb, qyb);
+  taylor_fw<N, NB>(cm, gb, qgb);
+  const N s2 = Num<N>::from_f(s) * s;
+  N acc = Num<N>::zero();
+  N s2r = Num<N>::from_f(1.f);   // s^{2r}
+  N ds2r = Num<N>::zero();       // d/ds s^{2r} = 2r s^{2r-1}
 #pragma unroll
   for (int r = 0; r < NB; ++r) {
-    const double ep = pya[r] - yb[r], fp = pga[r] - gb[r];
-    const double em = qyb[r] - ya[r], fm = qgb[r] - ga[r];
-    // d/ds exp(+-sN) v = +-N exp(+-sN) v: component r takes component r+1
-    const double dep = r + 1 < NB ? pya[r + 1] : 0.0, dfp = r + 1 < NB ? pga[r + 1] : 0.0;
-    const double dem = r + 1 < NB ? -qyb[r + 1] : 0.0, dfm = r + 1 < NB ? -qgb[r + 1] : 0.0;
-    acc += ds2r * (fp * ep + fm * em) + s2r * (dfp * ep + fp * dep + dfm * em + fm * dem);
-    ds2r = (2.0 * r + 2.0) * s2r * s;
-    s2r *= s * s;
+    const N ep = pya[r] - yb[r], fp = pga[r] - gb[r];
+    const N em = qyb[r] - ya[r], fm = qgb[r] - ga[r];
+    N inner = Num<N>::zero();
+    if (r + 1 < NB) {  // d/ds exp(+-sN) v = +-N exp(+-sN) v: component r takes component r+1
+      inner = (pga[r + 1] * ep + fp * pya[r + 1]) - (qgb[r + 1] * em + fm * qyb[r + 1]);
+    }
+    acc = acc + ds2r * (fp * ep + fm * em) + s2r * inner;
+    ds2r = s2r * s * float(2 * r + 2);
+    s2r = s2r * s2;
   }
-  return -ws2 * acc;
+  return -(ws2 * acc);
 }
 
-template <class Tr, int NB>
-__global__ void __launch_bounds__(kThreads) k_grad(GradTables gt, Problem0 p, const Tr* y, const Tr* gv,
+template <class Tr, class N, int NB>
+__global__ void __launch_bounds__(kThreads) k_grad(GradTables gt, Problem0 p, const Tr* y_hi,
+                                                   const float* y_lo, const Tr* g_hi, const float* g_lo,
                                                    const int32_t* info, Tr* gc, Tr* gd, Tr* gs, Tr* gu) {
   const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (q >= gt.Q) return;
@@ -443,50 +489,51 @@ __global__ void __launch_bounds__(kThreads) k_grad(GradTables gt, Problem0 p, co
   const Tr* s = static_cast<const Tr*>(p.s) + gt.seq_soff[b];
   Tr* gso = gs + gt.seq_soff[b];
   const int nu = p.T_init * (p.R_init + 1);
+  const N wg2 = Num<N>::from_d(p.wg2), wi2 = Num<N>::from_d(p.wi2), ws2 = Num<N>::from_d(p.ws2);
   bool any_fail = false;
   for (int dd = 0; dd < gt.D; ++dd) any_fail = any_fail || info[i0 + dd] > 0;
   for (int64_t t = first; t <= last; ++t) {
-    double gsum = 0.0;
+    N gsum = Num<N>::zero();
     const bool pair = t + 1 < T;
-    const double st = pair ? double(s[t]) : 0.0;
+    const float st = pair ? float(s[t]) : 0.f;
     for (int dd = 0; dd < gt.D; ++dd) {
       const int64_t i = i0 + dd;
       const int64_t base = gt.sys_base[i];
       const Tr* c = static_cast<const Tr*>(p.c) + base * NB;
       const Tr* d = static_cast<const Tr*>(p.d) + base;
-      const Tr* ys = y + base * NB;
-      const Tr* gs_ = gv + base * NB;
       const bool failed = info[i] > 0;
-      double ya[NB], ga[NB], cv[NB];
-      double cy = 0.0, cg = 0.0;
+      N ya[NB], ga[NB];
+      N cy = Num<N>::zero(), cg = Num<N>::zero();
 #pragma unroll
       for (int a = 0; a < NB; ++a) {
-        ya[a] = double(ys[t * NB + a]);
-        ga[a] = double(gs_[t * NB + a]);
-        cv[a] = double(c[t * NB + a]);
-        cy = fma(cv[a], ya[a], cy);
-        cg = fma(cv[a], ga[a], cg);
+        const int64_t at = (base + t) * NB + a;
+        ya[a] = ld_pair<N>(y_hi, y_lo, at);
+        ga[a] = ld_pair<N>(g_hi, g_lo, at);
+        const N cv = ld_n<N>(c[t * NB + a]);
+        cy = cy + cv * ya[a];
+        cg = cg + cv * ga[a];
       }
-      const double e = double(d[t]) - cy;
+      const N e = ld_n<N>(d[t]) - cy;
 #pragma unroll
       for (int a = 0; a < NB; ++a)
-        gc[(base + t) * NB + a] = failed ? nan_t<Tr>() : Tr(p.wg2 * (e * ga[a] - cg * ya[a]));
-      gd[base + t] = failed ? nan_t<Tr>() : Tr(p.wg2 * cg);
+        gc[(base + t) * NB + a] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * (e * ga[a] - cg * ya[a]));
+      gd[base + t] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * cg);
       if (t < p.T_init) {
         for (int a = 0; a <= p.R_init; ++a)
-          gu[i * nu + t * (p.R_init + 1) + a] = failed ? nan_t<Tr>() : Tr(p.wi2 * ga[a]);
+          gu[i * nu + t * (p.R_init + 1) + a] = failed ? nan_t<Tr>() : st_n<Tr, N>(wi2 * ga[a]);
       }
       if (pair) {
-        double yb[NB], gb[NB];
+        N yb[NB], gb[NB];
 #pragma unroll
         for (int a = 0; a < NB; ++a) {
-          yb[a] = double(ys[(t + 1) * NB + a]);
-          gb[a] = double(gs_[(t + 1) * NB + a]);
+          const int64_t at = (base + t + 1) * NB + a;
+          yb[a] = ld_pair<N>(y_hi, y_lo, at);
+          gb[a] = ld_pair<N>(g_hi, g_lo, at);
         }
-        gsum += smooth_pair_grad<NB>(st, p.ws2, ya, yb, ga, gb);
+        gsum = gsum + smooth_pair_grad<N, NB>(st, ws2, ya, yb, ga, gb);
       }
     }
-    gso[t] = any_fail ? nan_t<Tr>() : Tr(gsum);
+    gso[t] = any_fail ? nan_t<Tr>() : st_n<Tr, N>(gsum);
   }
 }
 
@@ -553,6 +600,7 @@ struct smnn_plan_s {
   std::vector<Level> lv;
   size_t factor_bytes = 0, solve_bytes = 0;
   size_t o_r = 0, o_g = 0, o_nrm = 0;  // solve region (bytes)
+  size_t o_yh = 0, o_yl = 0, o_gh = 0, o_gl = 0;
   void* tables = nullptr;              // one device allocation for every index table
 };
 
@@ -640,6 +688,12 @@ smnn_status build_plan(smnn_plan_s* pl) {
   }
   pl->o_r = s;   s += align_up(size_t(pl->N0) * NB * es);
   pl->o_g = s;   s += align_up(size_t(pl->N0) * NB * es);
+  if (es == 4) {  // float-float accumulators of the FP32 paths
+    pl->o_yh = s; s += align_up(size_t(pl->N0) * NB * 4);
+    pl->o_yl = s; s += align_up(size_t(pl->N0) * NB * 4);
+    pl->o_gh = s; s += align_up(size_t(pl->N0) * NB * 4);
+    pl->o_gl = s; s += align_up(size_t(pl->N0) * NB * 4);
+  }
   pl->o_nrm = s; s += align_up(size_t(S) * 2 * sizeof(double));
   pl->factor_bytes = f;
   pl->solve_bytes = s;
@@ -730,11 +784,11 @@ Problem0 problem0(const smnn_plan_s* pl, const void* c, const void* d, const voi
   return p;
 }
 
-// One pass of the chunked solve: eliminate level by level (factor or replay), then back
-// substitute into x (level-0 unknowns, y layout), optionally accumulating.
+// One pass of the chunked solve: eliminate level by level (factor, or replay the stored
+// factor on a new right-hand side), then back substitute; level-0 output per `out`.
 template <class Tr, int NB>
 smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, bool factor,
-                       char* fac, char* sol, Tr* x, bool accum, int32_t* info, double* nrm,
+                       char* fac, char* sol, const Level0Out<Tr>& out, int mode, int32_t* info,
                        cudaStream_t st) {
   const int nl = int(pl->lv.size());
   for (int l = 0; l < nl; ++l) {
@@ -763,8 +817,92 @@ smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, 
   }
   const Level& L0 = pl->lv[0];
   const LevelBufs<Tr, NB> lb0 = bufs_of<Tr, NB>(L0, fac, sol);
-  if (accum) SMNN_LAUNCH((k_backsub0<Tr, NB, true>), L0.G, st, tables_of(L0), lb0, p, x, info, nrm);
-  else SMNN_LAUNCH((k_backsub0<Tr, NB, false>), L0.G, st, tables_of(L0), lb0, p, x, info, nrm);
+  if (mode == 0) SMNN_LAUNCH((k_backsub0<Tr, NB, 0>), L0.G, st, tables_of(L0), lb0, p, out, info);
+  else if constexpr (std::is_same<Tr, float>::value)
+    SMNN_LAUNCH((k_backsub0<Tr, NB, 1>), L0.G, st, tables_of(L0), lb0, p, out, info);
+  return SMNN_OK;
+}
+
+struct RefineBufs {  // FP32 refinement scratch in the solve region
+  float* r;               // residual [N0][NB]
+  float* y_hi; float* y_lo;  // float-float accumulator of y
+  float* g_hi; float* g_lo;  // float-float accumulator of g (adjoint)
+  double* nrm;            // [S][2]
+};
+
+RefineBufs refine_bufs(const smnn_plan_s* pl, char* sol) {
+  RefineBufs b;
+  b.r = reinterpret_cast<float*>(sol + pl->o_r);
+  b.y_hi = reinterpret_cast<float*>(sol + pl->o_yh);
+  b.y_lo = reinterpret_cast<float*>(sol + pl->o_yl);
+  b.g_hi = reinterpret_cast<float*>(sol + pl->o_gh);
+  b.g_lo = reinterpret_cast<float*>(sol + pl->o_gl);
+  b.nrm = reinterpret_cast<double*>(sol + pl->o_nrm);
+  return b;
+}
+
+template <class N, int NB>
+smnn_status residual(const smnn_plan_s* pl, const Problem0& p, const float* xh, const float* xl,
+                     const float* rhs, float* r, cudaStream_t st) {
+  SMNN_LAUNCH((k_residual<N, NB>), pl->lv[0].G, st, tables_of(pl->lv[0]), p, xh, xl, rhs, r);
+  return SMNN_OK;
+}
+
+// Forward solve with refinement in number type N (double: FP64 residual; ff: float-float).
+template <class N, int NB>
+smnn_status refine_forward(const smnn_plan_s* pl, const Problem0& p, char* fac, char* sol,
+                           float* y, int32_t* info, cudaStream_t st) {
+  const RefineBufs rb = refine_bufs(pl, sol);
+  const int K = pl->desc.max_refine;
+  const bool check = pl->desc.refine_tol > 0;
+  Level0Out<float> o{K == 0 ? y : nullptr, rb.y_hi, rb.y_lo, nullptr, nullptr, nullptr};
+  smnn_status rc = solve_pass<float, NB>(pl, p, nullptr, true, fac, sol, o, 1, info, st);
+  for (int it = 0; it < K && rc == SMNN_OK; ++it) {
+    const bool last = it + 1 == K;
+    if (check && last) SMNN_LAUNCH(k_fill_f64, 2 * pl->S, st, rb.nrm, 2 * pl->S, 0.0);
+    rc = residual<N, NB>(pl, p, rb.y_hi, rb.y_lo, nullptr, rb.r, st);
+    if (rc != SMNN_OK) return rc;
+    Level0Out<float> oa{last ? y : nullptr, rb.y_hi, rb.y_lo, rb.y_hi, rb.y_lo,
+                        check && last ? rb.nrm : nullptr};
+    rc = solve_pass<float, NB>(pl, p, rb.r, false, fac, sol, oa, 1, info, st);
+  }
+  if (rc == SMNN_OK && check && K > 0)
+    SMNN_LAUNCH(k_refine_check, pl->S, st, rb.nrm, pl->S, pl->desc.refine_tol, info);
+  return rc;
+}
+
+// Adjoint: g = M^{-1} gy refined KA times, y re-refined once from the caller's FP32 y (both
+// kept as float-float), then the fused gradients in number type N.
+template <class N, int NB>
+smnn_status refine_backward(const smnn_plan_s* pl, const Problem0& p, char* fac, char* sol,
+                            bool factor, const float* y, const float* gy, float* gc, float* gd,
+                            float* gs, float* gu, int32_t* info, cudaStream_t st) {
+  const RefineBufs rb = refine_bufs(pl, sol);
+  const int KA = pl->desc.precision == SMNN_F32 ? 0 : pl->desc.adjoint_refine;
+  Level0Out<float> og{nullptr, rb.g_hi, rb.g_lo, nullptr, nullptr, nullptr};
+  smnn_status rc = solve_pass<float, NB>(pl, p, gy, factor, fac, sol, og, 1, info, st);
+  if (rc != SMNN_OK) return rc;
+  const float* yh = y;
+  const float* yl = nullptr;
+  if (KA > 0) {
+    rc = residual<N, NB>(pl, p, y, nullptr, nullptr, rb.r, st);
+    if (rc != SMNN_OK) return rc;
+    Level0Out<float> oy{nullptr, rb.y_hi, rb.y_lo, y, nullptr, nullptr};
+    rc = solve_pass<float, NB>(pl, p, rb.r, false, fac, sol, oy, 1, info, st);
+    if (rc != SMNN_OK) return rc;
+    yh = rb.y_hi;
+    yl = rb.y_lo;
+  }
+  for (int it = 0; it < KA; ++it) {
+    rc = residual<N, NB>(pl, p, rb.g_hi, rb.g_lo, gy, rb.r, st);
+    if (rc != SMNN_OK) return rc;
+    Level0Out<float> oa{nullptr, rb.g_hi, rb.g_lo, rb.g_hi, rb.g_lo, nullptr};
+    rc = solve_pass<float, NB>(pl, p, rb.r, false, fac, sol, oa, 1, info, st);
+    if (rc != SMNN_OK) return rc;
+  }
+  GradTables gt{pl->d_sq_b, pl->d_sq_k, pl->d_sys_off, pl->d_sys_T, pl->d_seq_soff, pl->Q,
+                pl->lv[0].L, int(pl->D)};
+  SMNN_LAUNCH((k_grad<float, N, NB>), pl->Q, st, gt, p, yh, yl, rb.g_hi, rb.g_lo, info, gc, gd, gs, gu);
   return SMNN_OK;
 }
 
@@ -775,28 +913,15 @@ smnn_status factor_solve_t(const smnn_plan_s* pl, const void* c, const void* d, 
   const Problem0 p = problem0(pl, c, d, s, u);
   char* fac = factor ? static_cast<char*>(factor) : static_cast<char*>(ws);
   char* sol = static_cast<char*>(ws) + pl->factor_bytes;
-  Tr* yy = static_cast<Tr*>(y);
   SMNN_LAUNCH(k_fill_i32, pl->S, st, info, pl->S, 0);
-  smnn_status rc = solve_pass<Tr, NB>(pl, p, nullptr, true, fac, sol, yy, false, info, nullptr, st);
-  if (rc != SMNN_OK) return rc;
   if constexpr (std::is_same<Tr, float>::value) {
-    if (pl->desc.precision == SMNN_F32_REFINED) {
-      float* r = reinterpret_cast<float*>(sol + pl->o_r);
-      double* nrm = reinterpret_cast<double*>(sol + pl->o_nrm);
-      const bool check = pl->desc.refine_tol > 0;
-      for (int it = 0; it < pl->desc.max_refine; ++it) {
-        const bool last = it + 1 == pl->desc.max_refine;
-        if (check && last) SMNN_LAUNCH(k_fill_f64, 2 * pl->S, st, nrm, 2 * pl->S, 0.0);
-        SMNN_LAUNCH((k_residual<NB>), pl->lv[0].G, st, tables_of(pl->lv[0]), p, yy, nullptr, r);
-        rc = solve_pass<Tr, NB>(pl, p, r, false, fac, sol, yy, true, info,
-                                check && last ? nrm : nullptr, st);
-        if (rc != SMNN_OK) return rc;
-      }
-      if (check && pl->desc.max_refine > 0)
-        SMNN_LAUNCH(k_refine_check, pl->S, st, nrm, pl->S, pl->desc.refine_tol, info);
-    }
+    if (pl->desc.precision == SMNN_F32_REFINED)
+      return refine_forward<double, NB>(pl, p, fac, sol, static_cast<float*>(y), info, st);
+    if (pl->desc.precision == SMNN_F32_REFINED_DF)
+      return refine_forward<ff, NB>(pl, p, fac, sol, static_cast<float*>(y), info, st);
   }
-  return SMNN_OK;
+  Level0Out<Tr> o{static_cast<Tr*>(y), nullptr, nullptr, nullptr, nullptr, nullptr};
+  return solve_pass<Tr, NB>(pl, p, nullptr, true, fac, sol, o, 0, info, st);
 }
 
 template <class Tr, int NB>
@@ -806,26 +931,31 @@ smnn_status backward_t(const smnn_plan_s* pl, const void* c, const void* d, cons
   const Problem0 p = problem0(pl, c, d, s, u);
   char* fac = factor ? static_cast<char*>(const_cast<void*>(factor)) : static_cast<char*>(ws);
   char* sol = static_cast<char*>(ws) + pl->factor_bytes;
-  Tr* g = reinterpret_cast<Tr*>(sol + pl->o_g);
-  const Tr* rhs = static_cast<const Tr*>(gy);
   SMNN_LAUNCH(k_fill_i32, pl->S, st, info, pl->S, 0);
-  smnn_status rc = solve_pass<Tr, NB>(pl, p, rhs, factor == nullptr, fac, sol, g, false, info, nullptr, st);
-  if (rc != SMNN_OK) return rc;
   if constexpr (std::is_same<Tr, float>::value) {
-    if (pl->desc.precision == SMNN_F32_REFINED) {
-      float* r = reinterpret_cast<float*>(sol + pl->o_r);
-      for (int it = 0; it < pl->desc.max_refine; ++it) {
-        SMNN_LAUNCH((k_residual<NB>), pl->lv[0].G, st, tables_of(pl->lv[0]), p, g, rhs, r);
-        rc = solve_pass<Tr, NB>(pl, p, r, false, fac, sol, g, true, info, nullptr, st);
-        if (rc != SMNN_OK) return rc;
-      }
-    }
+    auto* y32 = static_cast<const float*>(y);
+    auto* gy32 = static_cast<const float*>(gy);
+    auto* o = reinterpret_cast<float*>(gc);
+    if (pl->desc.precision == SMNN_F32_REFINED_DF)
+      return refine_backward<ff, NB>(pl, p, fac, sol, factor == nullptr, y32, gy32, o,
+                                     static_cast<float*>(gd), static_cast<float*>(gs),
+                                     static_cast<float*>(gu), info, st);
+    return refine_backward<double, NB>(pl, p, fac, sol, factor == nullptr, y32, gy32, o,
+                                       static_cast<float*>(gd), static_cast<float*>(gs),
+                                       static_cast<float*>(gu), info, st);
+  } else {
+    Tr* g = reinterpret_cast<Tr*>(sol + pl->o_g);
+    Level0Out<Tr> o{g, nullptr, nullptr, nullptr, nullptr, nullptr};
+    smnn_status rc = solve_pass<Tr, NB>(pl, p, static_cast<const Tr*>(gy), factor == nullptr, fac,
+                                        sol, o, 0, info, st);
+    if (rc != SMNN_OK) return rc;
+    GradTables gt{pl->d_sq_b, pl->d_sq_k, pl->d_sys_off, pl->d_sys_T, pl->d_seq_soff, pl->Q,
+                  pl->lv[0].L, int(pl->D)};
+    SMNN_LAUNCH((k_grad<Tr, double, NB>), pl->Q, st, gt, p, static_cast<const Tr*>(y), nullptr, g,
+                nullptr, info, static_cast<Tr*>(gc), static_cast<Tr*>(gd), static_cast<Tr*>(gs),
+                static_cast<Tr*>(gu));
+    return SMNN_OK;
   }
-  GradTables gt{pl->d_sq_b, pl->d_sq_k, pl->d_sys_off, pl->d_sys_T, pl->d_seq_soff, pl->Q,
-                pl->lv[0].L, int(pl->D)};
-  SMNN_LAUNCH((k_grad<Tr, NB>), pl->Q, st, gt, p, static_cast<const Tr*>(y), g, info,
-              static_cast<Tr*>(gc), static_cast<Tr*>(gd), static_cast<Tr*>(gs), static_cast<Tr*>(gu));
-  return SMNN_OK;
 }
 
 template <class Tr, int NB>
@@ -875,9 +1005,10 @@ smnn_status smnn_plan_create(const smnn_desc* desc, smnn_plan* plan) {
   *plan = nullptr;
   const smnn_desc& d = *desc;
   if (d.R < 1 || d.R > SMNN_MAX_R || d.R_init < 0 || d.R_init > d.R || d.T_init < 1) return SMNN_ERR_INVALID_ARG;
-  if (d.precision < SMNN_F32_REFINED || d.precision > SMNN_F64) return SMNN_ERR_INVALID_ARG;
+  if (d.precision < SMNN_F32_REFINED || d.precision > SMNN_F32_REFINED_DF) return SMNN_ERR_INVALID_ARG;
   if (d.algo < SMNN_ALGO_AUTO || d.algo > SMNN_ALGO_CR) return SMNN_ERR_INVALID_ARG;
-  if (d.max_refine < 0 || d.max_refine > 16 || d.chunk < 0 || d.chunk == 1 || d.reserved0 != 0)
+  if (d.max_refine < 0 || d.max_refine > 16 || d.adjoint_refine < 0 || d.adjoint_refine > 16 ||
+      d.chunk < 0 || d.chunk == 1)
     return SMNN_ERR_INVALID_ARG;
   if (d.num_seq < 1 || d.dims_per_seq < 1) return SMNN_ERR_INVALID_ARG;
   if (!(d.w_gov >= 0) || !(d.w_init >= 0) || !(d.w_smooth >= 0) || !(d.refine_tol >= 0))

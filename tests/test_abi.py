@@ -34,7 +34,8 @@ def test_status_strings_and_counter():
 
 @pytest.mark.parametrize("field,value", [("R", 0), ("R", 4), ("R_init", 3), ("T_init", 0),
                                          ("precision", 7), ("algo", 5), ("max_refine", -1),
-                                         ("chunk", 1), ("reserved0", 1), ("num_seq", 0),
+                                         ("chunk", 1), ("adjoint_refine", -1), ("adjoint_refine", 17),
+                                         ("precision", 4), ("num_seq", 0),
                                          ("w_gov", -1.0), ("T", 0)])
 def test_plan_create_rejects_invalid_descriptors(field, value):
     from paper_2410_06074_b300 import binding as B

@@ -47,12 +47,16 @@ def test_config1_fp64_matches_dense_oracle(algo, chunk):
         assert np.abs(g - r).max() <= TOL_F64 * np.abs(r).max()
 
 
+REFINED = ["F32_REFINED", "F32_REFINED_DF"]
+
+
+@pytest.mark.parametrize("prec", REFINED)
 @pytest.mark.parametrize("T,algo,chunk", [(1000, "CR", 0), (1000, "CR", 8), (4099, "CR", 64),
                                           (4099, "SEQ", 0), (333, "CR", 2), (64, "CR", 0)])
-def test_refined_fp32_forward(T, algo, chunk):
+def test_refined_fp32_forward(T, algo, chunk, prec):
     pk = P()
     prob = random_problem(7, 3, 2, T, 2)
-    y, info = gpu_solve(prob, pk.F32_REFINED, algo=getattr(pk, "ALGO_" + algo), chunk=chunk)
+    y, info = gpu_solve(prob, getattr(pk, prec), algo=getattr(pk, "ALGO_" + algo), chunk=chunk)
     yo, _ = oracle_solve(rounded(prob, pk.F32_REFINED))
     assert (info == 0).all()
     assert rel_err_per_system(y, yo, prob).max() <= TOL_REF
@@ -79,11 +83,12 @@ def test_unrefined_fp32_error_band():
     assert e1.max() < e.max() * 0.05      # one sweep contracts the error by > 20x
 
 
+@pytest.mark.parametrize("prec", REFINED)
 @pytest.mark.parametrize("R", [1, 3])
-def test_other_orders(R):
+def test_other_orders(R, prec):
     pk = P()
     prob = random_problem(10, 2, 2, 1500, R, s_lo=0.1, s_hi=0.5)
-    y, info = gpu_solve(prob, pk.F32_REFINED)
+    y, info = gpu_solve(prob, getattr(pk, prec))
     yo, _ = oracle_solve(rounded(prob, pk.F32_REFINED))
     assert (info == 0).all()
     assert rel_err_per_system(y, yo, prob).max() <= TOL_REF
@@ -190,24 +195,26 @@ def test_gradients_fp64_match_oracle(store_factor):
         assert rel_err(a, b) <= 1e-8, rel_err(a, b)
 
 
+@pytest.mark.parametrize("prec", REFINED)
 @pytest.mark.parametrize("T,chunk", [(1024, 0), (777, 16)])
-def test_gradients_refined_fp32_match_oracle(T, chunk):
+def test_gradients_refined_fp32_match_oracle(T, chunk, prec):
     pk = P()
     prob = random_problem(17, 2, 4, T, 2)
     gy = upstream_gradient(prob)
     r = rounded(prob, pk.F32_REFINED)
-    y, gc, gd, gs, gu, info, info2 = gpu_grad(prob, gy.astype(np.float32), pk.F32_REFINED, chunk=chunk)
+    y, gc, gd, gs, gu, info, info2 = gpu_grad(prob, gy.astype(np.float32), getattr(pk, prec), chunk=chunk)
     yo, gco, gdo, gso, guo, _ = oracle_grad(r, gy.astype(np.float32).astype(np.float64))
     for name, a, b in (("y", y, yo), ("gc", gc, gco), ("gd", gd, gdo), ("gs", gs, gso), ("gu", gu, guo)):
         assert rel_err(a, b) <= TOL_REF, (name, rel_err(a, b))
 
 
-def test_saved_and_recomputed_factor_give_identical_gradients():
+@pytest.mark.parametrize("prec", REFINED)
+def test_saved_and_recomputed_factor_give_identical_gradients(prec):
     pk = P()
     prob = random_problem(18, 2, 2, 900, 2)
     gy = upstream_gradient(prob).astype(np.float32)
-    a = gpu_grad(prob, gy, pk.F32_REFINED, store_factor=True)
-    b = gpu_grad(prob, gy, pk.F32_REFINED, store_factor=False)
+    a = gpu_grad(prob, gy, getattr(pk, prec), store_factor=True)
+    b = gpu_grad(prob, gy, getattr(pk, prec), store_factor=False)
     for x, z in zip(a[:5], b[:5]):
         np.testing.assert_array_equal(x, z)
 
@@ -221,4 +228,6 @@ def test_gradcheck_config2_slice():
     c, d, s, u = (torch.from_numpy(a).cuda().requires_grad_(True) for a in (prob.c, prob.d, prob.s, prob.u))
     cfg = pk.SolveConfig(R_init=1, T_init=1, precision=pk.F64)
     f = lambda c, d, s, u: pk.smnn_layer(c, d, s, u, cfg)[0]
-    assert torch.autograd.gradcheck(f, (c, d, s, u), eps=1e-6, atol=1e-6, rtol=1e-4)
+    # kappa(M) ~ 2e5 here: eps = 1e-6 would leave ~1e-5 finite-difference noise from FP64
+    # rounding of the solve itself; eps = 1e-4 keeps both noise and truncation below 1e-7
+    assert torch.autograd.gradcheck(f, (c, d, s, u), eps=1e-4, atol=1e-6, rtol=1e-4)
