@@ -134,10 +134,11 @@ smnn_status smnn_workspace_size(smnn_plan plan, size_t* workspace_bytes, size_t*
 /* App. A.2: materialise M_t (lower triangle packed row by row: M_00, M_10, M_11,
  * M_20, ..., (R+1)(R+2)/2 values), N_t (block (t+1,t), (R+1)^2 values row-major,
  * zero for the last step of a system) and beta_t (R+1 values) for every step, laid
- * out per step like y.  Testing and inspection aid; the solver forms these blocks
- * in registers. */
+ * out per step like y.  workspace: as for smnn_factor_solve.  Testing and inspection
+ * aid; the solver forms these blocks in registers. */
 smnn_status smnn_assemble(smnn_plan plan, const void* c, const void* d, const void* s,
-                          const void* u, void* M, void* N, void* beta, void* stream);
+                          const void* u, void* M, void* N, void* beta, void* workspace,
+                          void* stream);
 
 /* Forward pass (Alg. 1: Decompose, Alg. 3, then Substitute, Alg. 4, in the chunked
  * cyclic-reduction order of the plan), fused with the assembly of App. A.2, plus

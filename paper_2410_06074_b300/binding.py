@@ -59,7 +59,7 @@ SYMBOLS = {
     "smnn_plan_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(PlanStats)]),
     "smnn_workspace_size": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t),
                                            ctypes.POINTER(ctypes.c_size_t)]),
-    "smnn_assemble": (ctypes.c_int, [_VP] + [_VP] * 7 + [_VP]),
+    "smnn_assemble": (ctypes.c_int, [_VP] + [_VP] * 8 + [_VP]),
     "smnn_factor_solve": (ctypes.c_int, [_VP] + [_VP] * 8 + [_VP]),
     "smnn_backward": (ctypes.c_int, [_VP] + [_VP] * 13 + [_VP]),
     "smnn_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -199,10 +199,11 @@ class Plan:
                 if not t.is_cuda or not t.is_contiguous():
                     raise ValueError("smnn: every array must be a contiguous CUDA tensor")
 
-    def assemble(self, c, d, s, u, M, N, beta, stream=None):
-        self._args_ok(c, d, s, u, M, N, beta)
+    def assemble(self, c, d, s, u, M, N, beta, workspace=None, stream=None):
+        workspace = self.workspace(c.device) if workspace is None else workspace
+        self._args_ok(c, d, s, u, M, N, beta, workspace)
         _check(lib.smnn_assemble(self.handle, _p(c), _p(d), _p(s), _p(u), _p(M), _p(N), _p(beta),
-                                 _stream(stream)), "smnn_assemble")
+                                 _p(workspace), _stream(stream)), "smnn_assemble")
 
     def factor_solve(self, c, d, s, u, y, info, workspace, factor=None, stream=None):
         self._args_ok(c, d, s, u, y, info, workspace, factor)

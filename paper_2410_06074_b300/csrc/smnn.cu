@@ -97,16 +97,31 @@ struct Problem0 {  // level-0 inputs
   int T_init, R_init;
 };
 
+// Level-0 interleaved arrays: element e of in-chunk position j of level-0 chunk g at
+// [(e*L + j)*G + g] (the layout of the factor), so that the consecutive chunks handled by a
+// warp's threads touch consecutive addresses.  Positions past a short last chunk are holes.
+template <class Tr>
+struct L0In {
+  const Tr* c;    // [NB][L][G]
+  const Tr* d;    // [L][G]
+  const Tr* s;    // [L][G]
+};
+
 template <class Tr, int NB>
-__device__ __forceinline__ CoefSource<Tr, NB> make_coef(const Problem0& p, const Tr* rhs, int64_t i,
-                                                        int64_t base, int64_t T) {
+__device__ __forceinline__ CoefSource<Tr, NB> make_coef(const Problem0& p, const L0In<Tr>& in,
+                                                        const Tr* rhs, int64_t i, int64_t g,
+                                                        int64_t first, int64_t T, int L, int64_t G) {
   CoefSource<Tr, NB> src;
-  src.c = static_cast<const Tr*>(p.c) + base * NB;
-  src.d = static_cast<const Tr*>(p.d) + base;
-  src.s = static_cast<const Tr*>(p.s) + p.soff[i];
+  src.c = in.c;
+  src.d = in.d;
+  src.s = in.s;
   src.u = static_cast<const Tr*>(p.u) + i * int64_t(p.T_init) * (p.R_init + 1);
-  src.rhs = rhs ? rhs + base * NB : nullptr;
+  src.rhs = rhs;
   src.T = T;
+  src.first = first;
+  src.g = g;
+  src.G = G;
+  src.L = L;
   src.wg2 = Tr(p.wg2);
   src.wi2 = Tr(p.wi2);
   src.ws2 = Tr(p.ws2);
@@ -129,6 +144,20 @@ __device__ __forceinline__ ReducedSource<Tr, NB> make_reduced(const ChunkOut<Tr,
   return src;
 }
 
+// chunk g of a level: system, first and last step
+struct ChunkPos {
+  int64_t i, k, T, first, last;
+};
+__device__ __forceinline__ ChunkPos chunk_pos(const LevelTables& lt, int64_t g) {
+  ChunkPos c;
+  c.i = lt.csys[g];
+  c.k = g - lt.coff[c.i];
+  c.T = lt.P[c.i];
+  c.first = c.k * lt.L;
+  c.last = min(c.first + lt.L, c.T) - 1;
+  return c;
+}
+
 // ----------------------------------------------------------------------------- kernels
 
 __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
@@ -141,22 +170,71 @@ __global__ void k_fill_f64(double* p, int64_t n, double v) {
   if (i < n) p[i] = v;
 }
 
+// User layout -> level-0 interleaved layout.  One thread per (position j, chunk g); the
+// writes of a warp are contiguous.  vec: optional per-step vector of NB values (y or
+// dl/dy) gathered into vec_out (float-float pairs: vec_lo, if given, is zeroed).
+template <class Tr, int NB>
+__global__ void __launch_bounds__(kThreads) k_gather0(LevelTables lt, Problem0 p, Tr* c, Tr* d, Tr* s,
+                                                      const Tr* vec, Tr* vec_out, float* vec_lo) {
+  const int64_t n = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (n >= lt.G * lt.L) return;
+  const int64_t g = n % lt.G;
+  const int j = int(n / lt.G);
+  const int64_t es = int64_t(lt.L) * lt.G;
+  const ChunkPos cp = chunk_pos(lt, g);
+  const int64_t t = cp.first + j;
+  if (t > cp.last) return;
+  const int64_t at = lt.base[cp.i] + t;
+  if (c) {
+#pragma unroll
+    for (int e = 0; e < NB; ++e) c[e * es + n] = static_cast<const Tr*>(p.c)[at * NB + e];
+    d[n] = static_cast<const Tr*>(p.d)[at];
+    s[n] = static_cast<const Tr*>(p.s)[p.soff[cp.i] + t];
+  }
+  if (vec) {
+#pragma unroll
+    for (int e = 0; e < NB; ++e) {
+      vec_out[e * es + n] = vec[at * NB + e];
+      if (vec_lo) vec_lo[e * es + n] = 0.f;
+    }
+  }
+}
+
+// Level-0 interleaved -> user layout for NB-vectors (x = hi + lo, lo optional) and for a
+// per-step scalar (sc).
+template <class Tr, class Ti, int NB>
+__global__ void __launch_bounds__(kThreads) k_scatter0(LevelTables lt, const Ti* hi, const float* lo,
+                                                       Tr* out, const Tr* sc, Tr* sc_out) {
+  const int64_t n = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (n >= lt.G * lt.L) return;
+  const int64_t g = n % lt.G;
+  const int j = int(n / lt.G);
+  const int64_t es = int64_t(lt.L) * lt.G;
+  const ChunkPos cp = chunk_pos(lt, g);
+  const int64_t t = cp.first + j;
+  if (t > cp.last) return;
+  const int64_t at = lt.base[cp.i] + t;
+#pragma unroll
+  for (int e = 0; e < NB; ++e) {
+    Tr v = Tr(hi[e * es + n]);
+    if (lo) v = Tr(__fadd_rn(float(hi[e * es + n]), lo[e * es + n]));
+    out[at * NB + e] = v;
+  }
+  if (sc) sc_out[at] = sc[n];
+}
+
 template <class Tr, int NB, bool kFactor, bool kTop>
 __global__ void __launch_bounds__(kThreads) k_elim0(LevelTables lt, LevelBufs<Tr, NB> lb, Problem0 p,
-                                                    const Tr* rhs, int32_t* info) {
+                                                    L0In<Tr> in, const Tr* rhs, int32_t* info) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  const int64_t i = lt.csys[g];
-  const int64_t k = g - lt.coff[i];
-  const int64_t T = lt.P[i];
-  const int64_t first = k * lt.L;
-  const int64_t last = min(first + lt.L, T) - 1;
-  const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, rhs, i, lt.base[i], T);
-  int64_t fail = elim_chunk<Tr, NB, kFactor>(src, first, last, k > 0, lb.fac, g, lb.out);
+  const ChunkPos cp = chunk_pos(lt, g);
+  const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, in, rhs, cp.i, g, cp.first, cp.T, lt.L, lt.G);
+  int64_t fail = elim_chunk<Tr, NB, kFactor>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
   if (kTop) {
-    if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = last + 1;
+    if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = cp.last + 1;
   }
-  if (kFactor && fail) record_fail(info + i, int32_t(fail));
+  if (kFactor && fail) record_fail(info + cp.i, int32_t(fail));
 }
 
 template <class Tr, int NB, bool kFactor, bool kTop>
@@ -165,19 +243,15 @@ __global__ void __launch_bounds__(kThreads) k_elimN(LevelTables lt, LevelBufs<Tr
                                                     int32_t* info) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  const int64_t i = lt.csys[g];
-  const int64_t k = g - lt.coff[i];
-  const int64_t P = lt.P[i];
-  const int64_t first = k * lt.L;
-  const int64_t last = min(first + lt.L, P) - 1;
-  const ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[i], P);
-  int64_t fail = elim_chunk<Tr, NB, kFactor>(src, first, last, k > 0, lb.fac, g, lb.out);
+  const ChunkPos cp = chunk_pos(lt, g);
+  const ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[cp.i], cp.T);
+  int64_t fail = elim_chunk<Tr, NB, kFactor>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
   if (kTop) {
-    if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = last + 1;
+    if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = cp.last + 1;
   }
   if (kFactor && fail) {  // report the level-0 step of the failing separator
-    const int64_t step0 = min(fail * lt.stride0, T0[i]);
-    record_fail(info + i, int32_t(step0));
+    const int64_t step0 = min(fail * lt.stride0, T0[cp.i]);
+    record_fail(info + cp.i, int32_t(step0));
   }
 }
 
@@ -196,52 +270,44 @@ __global__ void __launch_bounds__(kThreads) k_backsubN(LevelTables lt, LevelBufs
                                                        ChunkOut<Tr, NB> prev, Tr* x_prev) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  const int64_t i = lt.csys[g];
-  const int64_t k = g - lt.coff[i];
-  const int64_t P = lt.P[i];
-  const int64_t first = k * lt.L;
-  const int64_t last = min(first + lt.L, P) - 1;
-  const ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[i], P);
-  EmitX<Tr, NB> emit{x_prev + lt.base[i] * NB};
-  backsub_chunk<Tr, NB>(src, first, last, k > 0, lb.fac, g, lb.xsep + g * NB,
-                        k > 0 ? lb.xsep + (g - 1) * NB : nullptr, emit);
+  const ChunkPos cp = chunk_pos(lt, g);
+  const ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[cp.i], cp.T);
+  EmitX<Tr, NB> emit{x_prev + lt.base[cp.i] * NB};
+  backsub_chunk<Tr, NB>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.xsep + g * NB,
+                        cp.k > 0 ? lb.xsep + (g - 1) * NB : nullptr, emit);
 }
 
-// Level-0 output of a solve pass.  mode 0: y = x (the plain FP32/FP64 result).  mode 1
-// (FP32 refinement): a float-float accumulator acc = base + x, where base is the previous
-// accumulator (in-place sweep), the caller's FP32 y (first sweep of the adjoint's
-// re-refinement of y), or zero (initial solve); optionally also writes the caller's y as
-// the rounded accumulator, and the squared norms of x and acc for the stop test.
+// Level-0 output of a solve pass, interleaved.  mode 0: x = v.  mode 1 (FP32 refinement):
+// float-float accumulator acc = v.  mode 2: acc += v, optionally with the squared norms of
+// v and acc for the refinement stop test.
 template <class Tr>
 struct Level0Out {
-  Tr* y;
+  Tr* x;
   float* acc_hi;
   float* acc_lo;
-  const Tr* base_hi;
-  const float* base_lo;
   double* nrm;
 };
 
 template <class Tr, int NB, int kMode>
 struct EmitY {
   Level0Out<Tr> o;
-  int64_t base;  // first step of this system
+  int64_t g, G, first;
+  int L;
   bool failed;
   double dd, yy;
   __device__ void operator()(int64_t t, const Tr (&v)[NB]) {
-    const int64_t at = (base + t) * NB;
+    const int64_t es = int64_t(L) * G;
+    const int64_t n = (t - first) * G + g;
 #pragma unroll
     for (int a = 0; a < NB; ++a) {
       if (kMode == 0) {
-        o.y[at + a] = failed ? nan_t<Tr>() : v[a];
+        o.x[a * es + n] = failed ? nan_t<Tr>() : v[a];
       } else {
-        ff acc = o.base_hi ? ff{float(o.base_hi[at + a]), o.base_lo ? o.base_lo[at + a] : 0.f}
-                           : ff{0.f, 0.f};
+        ff acc = kMode == 2 ? ff{o.acc_hi[a * es + n], o.acc_lo[a * es + n]} : ff{0.f, 0.f};
         acc = acc + float(v[a]);
         if (failed) acc = ff{nan_t<float>(), nan_t<float>()};
-        o.acc_hi[at + a] = acc.hi;
-        o.acc_lo[at + a] = acc.lo;
-        if (o.y) o.y[at + a] = Tr(acc.hi);
+        o.acc_hi[a * es + n] = acc.hi;
+        o.acc_lo[a * es + n] = acc.lo;
         dd += double(v[a]) * double(v[a]);
         yy += double(acc.hi) * double(acc.hi);
       }
@@ -251,22 +317,18 @@ struct EmitY {
 
 template <class Tr, int NB, int kMode>
 __global__ void __launch_bounds__(kThreads) k_backsub0(LevelTables lt, LevelBufs<Tr, NB> lb,
-                                                       Problem0 p, Level0Out<Tr> o,
+                                                       Problem0 p, L0In<Tr> in, Level0Out<Tr> o,
                                                        const int32_t* info) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  const int64_t i = lt.csys[g];
-  const int64_t k = g - lt.coff[i];
-  const int64_t T = lt.P[i];
-  const int64_t first = k * lt.L;
-  const int64_t last = min(first + lt.L, T) - 1;
-  const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, nullptr, i, lt.base[i], T);
-  EmitY<Tr, NB, kMode> emit{o, lt.base[i], info[i] > 0, 0.0, 0.0};
-  backsub_chunk<Tr, NB>(src, first, last, k > 0, lb.fac, g, lb.xsep + g * NB,
-                        k > 0 ? lb.xsep + (g - 1) * NB : nullptr, emit);
-  if (kMode == 1 && o.nrm) {
-    atomicAdd(o.nrm + 2 * i, emit.dd);
-    atomicAdd(o.nrm + 2 * i + 1, emit.yy);
+  const ChunkPos cp = chunk_pos(lt, g);
+  const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, in, nullptr, cp.i, g, cp.first, cp.T, lt.L, lt.G);
+  EmitY<Tr, NB, kMode> emit{o, g, lt.G, cp.first, lt.L, info[cp.i] > 0, 0.0, 0.0};
+  backsub_chunk<Tr, NB>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.xsep + g * NB,
+                        cp.k > 0 ? lb.xsep + (g - 1) * NB : nullptr, emit);
+  if (kMode == 2 && o.nrm) {
+    atomicAdd(o.nrm + 2 * cp.i, emit.dd);
+    atomicAdd(o.nrm + 2 * cp.i + 1, emit.yy);
   }
 }
 
@@ -278,6 +340,9 @@ __global__ void k_refine_check(const double* nrm, int64_t S, double tol, int32_t
 }
 
 // ---- refinement residual, in FP64 or float-float ------------------------------------
+template <class N> __device__ __forceinline__ N ld_n(float v) { return Num<N>::from_f(v); }
+template <class N> __device__ __forceinline__ N ld_n(double v) { return Num<N>::from_d(v); }
+
 // cf[k] = (+-s)^k / k!;  (P v)_r = sum_k cf[k] v_{r+k},  (P^T v)_r = sum_k cf[k] v_{r-k}
 template <class N, int NB>
 __device__ __forceinline__ void taylor_fw(const N (&cf)[NB], const N (&v)[NB], N (&o)[NB]) {
@@ -301,8 +366,8 @@ __device__ __forceinline__ void taylor_tr(const N (&cf)[NB], const N (&v)[NB], N
 }
 
 // exp(+-sN) Taylor coefficients for one step size
-template <class N, int NB>
-__device__ __forceinline__ void taylor_coefs(float s, N (&cp)[NB], N (&cm)[NB]) {
+template <class N, int NB, class Ts>
+__device__ __forceinline__ void taylor_coefs(Ts s, N (&cp)[NB], N (&cm)[NB]) {
   cp[0] = Num<N>::from_f(1.f);
   cm[0] = cp[0];
   N pk = cp[0];
@@ -322,7 +387,7 @@ template <class N, int NB>
 __device__ __forceinline__ void smooth_pair_residual(float s, N ws2, const N (&xa)[NB],
                                                      const N (&xb)[NB], N (&ra)[NB], N (&rb)[NB]) {
   N cp[NB], cm[NB], w[NB];
-  taylor_coefs<N, NB>(s, cp, cm);
+  taylor_coefs<N, NB, float>(s, cp, cm);
   w[0] = ws2;
   const N s2 = Num<N>::from_f(s) * s;
 #pragma unroll
@@ -344,58 +409,53 @@ __device__ __forceinline__ void smooth_pair_residual(float s, N ws2, const N (&x
   }
 }
 
-// r = rhs - M x for one chunk of steps, rhs = beta (assembled, rhs == nullptr) or an explicit
-// vector; x given as float-float parts (x_lo may be null).  Result rounded to FP32.
+// r = rhs - M x over one level-0 chunk, rhs = beta (assembled, rhs == nullptr) or an explicit
+// vector; x given as float-float parts (x_lo may be null).  Interleaved in and out; the
+// neighbours x_{first-1}, x_{last+1} come from the adjacent chunks.  Rounded to FP32.
 template <class N, int NB>
-__global__ void __launch_bounds__(kThreads) k_residual(LevelTables lt, Problem0 p, const float* x_hi,
-                                                       const float* x_lo, const float* rhs,
-                                                       float* r_out) {
+__global__ void __launch_bounds__(kThreads) k_residual(LevelTables lt, Problem0 p, L0In<float> in,
+                                                       const float* x_hi, const float* x_lo,
+                                                       const float* rhs, float* r_out) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  const int64_t i = lt.csys[g];
-  const int64_t k = g - lt.coff[i];
-  const int64_t T = lt.P[i];
-  const int64_t first = k * lt.L;
-  const int64_t last = min(first + lt.L, T) - 1;
-  const int64_t base = lt.base[i];
-  const float* c = static_cast<const float*>(p.c) + base * NB;
-  const float* d = static_cast<const float*>(p.d) + base;
-  const float* s = static_cast<const float*>(p.s) + p.soff[i];
-  const float* u = static_cast<const float*>(p.u) + i * int64_t(p.T_init) * (p.R_init + 1);
-  const float* xh = x_hi + base * NB;
-  const float* xl = x_lo ? x_lo + base * NB : nullptr;
-  const float* rh = rhs ? rhs + base * NB : nullptr;
-  float* ro = r_out + base * NB;
+  const ChunkPos cp = chunk_pos(lt, g);
+  const int64_t G = lt.G, es = int64_t(lt.L) * lt.G;
+  const float* u = static_cast<const float*>(p.u) + cp.i * int64_t(p.T_init) * (p.R_init + 1);
   const N wg2 = Num<N>::from_d(p.wg2), wi2 = Num<N>::from_d(p.wi2), ws2 = Num<N>::from_d(p.ws2);
+  auto idx = [&](int64_t t) -> int64_t {   // t in [first-1, last+1]
+    return t < cp.first ? int64_t(lt.L - 1) * G + (g - 1) : (t > cp.last ? g + 1 : (t - cp.first) * G + g);
+  };
   auto load = [&](int64_t t, N (&v)[NB]) {
+    const int64_t k = idx(t);
 #pragma unroll
-    for (int a = 0; a < NB; ++a) v[a] = Num<N>::pair(xh[t * NB + a], xl ? xl[t * NB + a] : 0.f);
+    for (int a = 0; a < NB; ++a) v[a] = Num<N>::pair(x_hi[a * es + k], x_lo ? x_lo[a * es + k] : 0.f);
   };
 
   N xc[NB], carry[NB];
-  load(first, xc);
+  load(cp.first, xc);
 #pragma unroll
   for (int a = 0; a < NB; ++a) carry[a] = Num<N>::zero();
-  if (first > 0) {
+  if (cp.first > 0) {
     N xp[NB], dummy[NB];
-    load(first - 1, xp);
-    smooth_pair_residual<N, NB>(s[first - 1], ws2, xp, xc, dummy, carry);
+    load(cp.first - 1, xp);
+    smooth_pair_residual<N, NB>(in.s[idx(cp.first - 1)], ws2, xp, xc, dummy, carry);
   }
-  for (int64_t t = first; t <= last; ++t) {
+  for (int64_t t = cp.first; t <= cp.last; ++t) {
+    const int64_t k = (t - cp.first) * G + g;
     N r[NB];
     float cv[NB];
     N cx = Num<N>::zero();
 #pragma unroll
     for (int a = 0; a < NB; ++a) {
-      cv[a] = c[t * NB + a];
+      cv[a] = in.c[a * es + k];
       cx = cx + xc[a] * cv[a];
     }
-    if (rh) {
+    if (rhs) {
       const N gres = -(wg2 * cx);   // beta replaced by the explicit right-hand side
 #pragma unroll
-      for (int a = 0; a < NB; ++a) r[a] = (gres * cv[a] + rh[t * NB + a]) + carry[a];
+      for (int a = 0; a < NB; ++a) r[a] = (gres * cv[a] + rhs[a * es + k]) + carry[a];
     } else {
-      const N gres = wg2 * (cx - d[t]);  // -w_g^2 (d_t - c_t . x_t)
+      const N gres = wg2 * (cx - in.d[k]);  // -w_g^2 (d_t - c_t . x_t)
 #pragma unroll
       for (int a = 0; a < NB; ++a) r[a] = carry[a] - gres * cv[a];
     }
@@ -403,19 +463,19 @@ __global__ void __launch_bounds__(kThreads) k_residual(LevelTables lt, Problem0 
 #pragma unroll
       for (int a = 0; a < NB; ++a)
         if (a <= p.R_init) {  // w_i^2 (u - x), u replaced by 0 for an explicit rhs
-          const N dv = rh ? -xc[a] : -(xc[a] - u[t * (p.R_init + 1) + a]);
+          const N dv = rhs ? -xc[a] : -(xc[a] - u[t * (p.R_init + 1) + a]);
           r[a] = r[a] + wi2 * dv;
         }
     }
-    if (t + 1 < T) {
+    if (t + 1 < cp.T) {
       N xn[NB], ra[NB];
       load(t + 1, xn);
-      smooth_pair_residual<N, NB>(s[t], ws2, xc, xn, ra, carry);
+      smooth_pair_residual<N, NB>(in.s[k], ws2, xc, xn, ra, carry);
 #pragma unroll
       for (int a = 0; a < NB; ++a) { r[a] = r[a] + ra[a]; xc[a] = xn[a]; }
     }
 #pragma unroll
-    for (int a = 0; a < NB; ++a) ro[t * NB + a] = Num<N>::to_f(r[a]);
+    for (int a = 0; a < NB; ++a) r_out[a * es + k] = Num<N>::to_f(r[a]);
   }
 }
 
@@ -423,16 +483,13 @@ __global__ void __launch_bounds__(kThreads) k_residual(LevelTables lt, Problem0 
 struct GradTables {
   const int32_t* sq_b;      // [Q] sequence of each sequence-chunk
   const int32_t* sq_k;      // [Q] chunk index within the sequence
-  const int64_t* sys_base;  // [S] level-0 step base of each system
+  const int64_t* coff0;     // [S+1] first level-0 chunk of each system
   const int64_t* sys_T;     // [S]
-  const int64_t* seq_soff;  // [B] offset of each sequence's step sizes
-  int64_t Q;
+  int64_t Q, G;             // sequence-chunks, level-0 chunks
   int L;
   int D;
 };
 
-template <class N> __device__ __forceinline__ N ld_n(float v) { return Num<N>::from_f(v); }
-template <class N> __device__ __forceinline__ N ld_n(double v) { return Num<N>::from_d(v); }
 template <class N> __device__ __forceinline__ N ld_pair(const float* hi, const float* lo, int64_t k) {
   return Num<N>::pair(hi[k], lo ? lo[k] : 0.f);
 }
@@ -445,17 +502,17 @@ template <> __device__ __forceinline__ float st_n<float, ff>(ff v) { return Num<
 template <> __device__ __forceinline__ double st_n<double, double>(double v) { return v; }
 
 // -w_s^2 d/ds sum_r s^{2r} (f+_r e+_r + f-_r e-_r) for the pair (t, t+1), g and y held fixed.
-template <class N, int NB>
-__device__ __forceinline__ N smooth_pair_grad(float s, N ws2, const N (&ya)[NB], const N (&yb)[NB],
+template <class N, int NB, class Ts>
+__device__ __forceinline__ N smooth_pair_grad(Ts s, N ws2, const N (&ya)[NB], const N (&yb)[NB],
                                               const N (&ga)[NB], const N (&gb)[NB]) {
   N cp[NB], cm[NB];
-  taylor_coefs<N, NB>(s, cp, cm);
+  taylor_coefs<N, NB, Ts>(s, cp, cm);
   N pya[NB], pga[NB], qyb[NB], qgb[NB];
   taylor_fw<N, NB>(cp, ya, pya);
   taylor_fw<N, NB>(cp, ga, pga);
   taylor_fw<N, NB>(cm, yb, qyb);
   taylor_fw<N, NB>(cm, gb, qgb);
-  const N s2 = Num<N>::from_f(s) * s;
+  const N s2 = ld_n<N>(s) * s;
   N acc = Num<N>::zero();
   N s2r = Num<N>::from_f(1.f);   // s^{2r}
   N ds2r = Num<N>::zero();       // d/ds s^{2r} = 2r s^{2r-1}
@@ -474,10 +531,14 @@ __device__ __forceinline__ N smooth_pair_grad(float s, N ws2, const N (&ya)[NB],
   return -(ws2 * acc);
 }
 
+// One thread per (sequence, level-0 chunk index): loops over the D systems of the sequence
+// (their chunk k sits at coff0[b*D + dd] + k), writes gc, gd (interleaved by system chunk),
+// gs (interleaved by sequence chunk, summed over D) and gu (user layout).
 template <class Tr, class N, int NB>
-__global__ void __launch_bounds__(kThreads) k_grad(GradTables gt, Problem0 p, const Tr* y_hi,
-                                                   const float* y_lo, const Tr* g_hi, const float* g_lo,
-                                                   const int32_t* info, Tr* gc, Tr* gd, Tr* gs, Tr* gu) {
+__global__ void __launch_bounds__(kThreads) k_grad(GradTables gt, Problem0 p, L0In<Tr> in,
+                                                   const Tr* y_hi, const float* y_lo, const Tr* g_hi,
+                                                   const float* g_lo, const int32_t* info, Tr* gc,
+                                                   Tr* gd, Tr* gs, Tr* gu) {
   const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (q >= gt.Q) return;
   const int64_t b = gt.sq_b[q];
@@ -486,8 +547,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(GradTables gt, Problem0 p, co
   const int64_t T = gt.sys_T[i0];
   const int64_t first = kc * gt.L;
   const int64_t last = min(first + gt.L, T) - 1;
-  const Tr* s = static_cast<const Tr*>(p.s) + gt.seq_soff[b];
-  Tr* gso = gs + gt.seq_soff[b];
+  const int64_t G = gt.G, es = int64_t(gt.L) * G;
   const int nu = p.T_init * (p.R_init + 1);
   const N wg2 = Num<N>::from_d(p.wg2), wi2 = Num<N>::from_d(p.wi2), ws2 = Num<N>::from_d(p.ws2);
   bool any_fail = false;
@@ -495,29 +555,28 @@ __global__ void __launch_bounds__(kThreads) k_grad(GradTables gt, Problem0 p, co
   for (int64_t t = first; t <= last; ++t) {
     N gsum = Num<N>::zero();
     const bool pair = t + 1 < T;
-    const float st = pair ? float(s[t]) : 0.f;
+    const int j = int(t - first);
     for (int dd = 0; dd < gt.D; ++dd) {
       const int64_t i = i0 + dd;
-      const int64_t base = gt.sys_base[i];
-      const Tr* c = static_cast<const Tr*>(p.c) + base * NB;
-      const Tr* d = static_cast<const Tr*>(p.d) + base;
+      const int64_t g = gt.coff0[i] + kc;
+      const int64_t k = int64_t(j) * G + g;
+      const int64_t kn = t + 1 <= last ? k + G : g + 1;   // step t+1: next position or next chunk
       const bool failed = info[i] > 0;
       N ya[NB], ga[NB];
       N cy = Num<N>::zero(), cg = Num<N>::zero();
 #pragma unroll
       for (int a = 0; a < NB; ++a) {
-        const int64_t at = (base + t) * NB + a;
-        ya[a] = ld_pair<N>(y_hi, y_lo, at);
-        ga[a] = ld_pair<N>(g_hi, g_lo, at);
-        const N cv = ld_n<N>(c[t * NB + a]);
+        ya[a] = ld_pair<N>(y_hi, y_lo, a * es + k);
+        ga[a] = ld_pair<N>(g_hi, g_lo, a * es + k);
+        const N cv = ld_n<N>(in.c[a * es + k]);
         cy = cy + cv * ya[a];
         cg = cg + cv * ga[a];
       }
-      const N e = ld_n<N>(d[t]) - cy;
+      const N e = ld_n<N>(in.d[k]) - cy;
 #pragma unroll
       for (int a = 0; a < NB; ++a)
-        gc[(base + t) * NB + a] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * (e * ga[a] - cg * ya[a]));
-      gd[base + t] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * cg);
+        gc[a * es + k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * (e * ga[a] - cg * ya[a]));
+      gd[k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * cg);
       if (t < p.T_init) {
         for (int a = 0; a <= p.R_init; ++a)
           gu[i * nu + t * (p.R_init + 1) + a] = failed ? nan_t<Tr>() : st_n<Tr, N>(wi2 * ga[a]);
@@ -526,42 +585,52 @@ __global__ void __launch_bounds__(kThreads) k_grad(GradTables gt, Problem0 p, co
         N yb[NB], gb[NB];
 #pragma unroll
         for (int a = 0; a < NB; ++a) {
-          const int64_t at = (base + t + 1) * NB + a;
-          yb[a] = ld_pair<N>(y_hi, y_lo, at);
-          gb[a] = ld_pair<N>(g_hi, g_lo, at);
+          yb[a] = ld_pair<N>(y_hi, y_lo, a * es + kn);
+          gb[a] = ld_pair<N>(g_hi, g_lo, a * es + kn);
         }
-        gsum = gsum + smooth_pair_grad<N, NB>(st, ws2, ya, yb, ga, gb);
+        gsum = gsum + smooth_pair_grad<N, NB, Tr>(in.s[k], ws2, ya, yb, ga, gb);
       }
     }
-    gso[t] = any_fail ? nan_t<Tr>() : st_n<Tr, N>(gsum);
+    gs[int64_t(j) * gt.Q + q] = any_fail ? nan_t<Tr>() : st_n<Tr, N>(gsum);
   }
+}
+
+// gs: sequence-chunk interleaved -> user layout of s
+template <class Tr>
+__global__ void k_scatter_gs(GradTables gt, const int64_t* seq_soff, const int64_t* seq_T,
+                             const Tr* gsI, Tr* gs) {
+  const int64_t n = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (n >= gt.Q * gt.L) return;
+  const int64_t q = n % gt.Q;
+  const int j = int(n / gt.Q);
+  const int64_t b = gt.sq_b[q];
+  const int64_t t = int64_t(gt.sq_k[q]) * gt.L + j;
+  if (t >= seq_T[b]) return;
+  gs[seq_soff[b] + t] = gsI[n];
 }
 
 // ---- materialised assembly (App. A.2) ---------------------------------------------------
 template <class Tr, int NB>
-__global__ void __launch_bounds__(kThreads) k_assemble(LevelTables lt, Problem0 p, Tr* M, Tr* N, Tr* beta) {
+__global__ void __launch_bounds__(kThreads) k_assemble(LevelTables lt, Problem0 p, L0In<Tr> in, Tr* M,
+                                                       Tr* N, Tr* beta) {
   constexpr int NT = NB * (NB + 1) / 2;
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  const int64_t i = lt.csys[g];
-  const int64_t k = g - lt.coff[i];
-  const int64_t T = lt.P[i];
-  const int64_t first = k * lt.L;
-  const int64_t last = min(first + lt.L, T) - 1;
-  const int64_t base = lt.base[i];
-  const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, nullptr, i, base, T);
-  for (int64_t t = first; t <= last; ++t) {
+  const ChunkPos cp = chunk_pos(lt, g);
+  const int64_t base = lt.base[cp.i];
+  const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, in, nullptr, cp.i, g, cp.first, cp.T, lt.L, lt.G);
+  for (int64_t t = cp.first; t <= cp.last; ++t) {
     Tr a[NB][NB], e[NB][NB], v[NB];
     src.A(t, a);
     src.b(t, v);
-    if (t + 1 < T) src.E(t, e);
+    if (t + 1 < cp.T) src.E(t, e);
 #pragma unroll
     for (int r = 0; r < NB; ++r) {
       beta[(base + t) * NB + r] = v[r];
 #pragma unroll
       for (int q = 0; q <= r; ++q) M[(base + t) * NT + tri(r, q)] = a[r][q];
 #pragma unroll
-      for (int q = 0; q < NB; ++q) N[(base + t) * NB * NB + r * NB + q] = t + 1 < T ? e[r][q] : Tr(0);
+      for (int q = 0; q < NB; ++q) N[(base + t) * NB * NB + r * NB + q] = t + 1 < cp.T ? e[r][q] : Tr(0);
     }
   }
 }
@@ -594,13 +663,18 @@ struct smnn_plan_s {
   int64_t* d_sys_T = nullptr;
   int64_t* d_sys_off = nullptr;
   int64_t* d_seq_soff = nullptr;
+  int64_t* d_seq_T = nullptr;
   int32_t* d_sq_b = nullptr;
   int32_t* d_sq_k = nullptr;
   int64_t Q = 0;
   std::vector<Level> lv;
   size_t factor_bytes = 0, solve_bytes = 0;
-  size_t o_r = 0, o_g = 0, o_nrm = 0;  // solve region (bytes)
-  size_t o_yh = 0, o_yl = 0, o_gh = 0, o_gl = 0;
+  size_t o_nrm = 0;                    // solve region (bytes), and the level-0 interleaved arrays:
+  size_t o_c = 0, o_d = 0, o_s = 0;    //   staged inputs
+  size_t o_r = 0, o_gy = 0;            //   residual / explicit rhs, staged dl/dy
+  size_t o_x = 0, o_g = 0;             //   plain solutions (FP64 and FP32 paths)
+  size_t o_yh = 0, o_yl = 0, o_gh = 0, o_gl = 0;  // float-float accumulators (FP32 paths)
+  size_t o_gc = 0, o_gd = 0, o_gs = 0; //   gradients before the scatter
   void* tables = nullptr;              // one device allocation for every index table
 };
 
@@ -686,17 +760,28 @@ smnn_status build_plan(smnn_plan_s* pl) {
     L.o_bl = s; s += align_up(size_t(L.G) * NB * es);
     L.o_xs = s; s += align_up(size_t(L.G) * NB * es);
   }
-  pl->o_r = s;   s += align_up(size_t(pl->N0) * NB * es);
-  pl->o_g = s;   s += align_up(size_t(pl->N0) * NB * es);
-  if (es == 4) {  // float-float accumulators of the FP32 paths
-    pl->o_yh = s; s += align_up(size_t(pl->N0) * NB * 4);
-    pl->o_yl = s; s += align_up(size_t(pl->N0) * NB * 4);
-    pl->o_gh = s; s += align_up(size_t(pl->N0) * NB * 4);
-    pl->o_gl = s; s += align_up(size_t(pl->N0) * NB * 4);
+  {
+    const Level& L0 = pl->lv[0];
+    const size_t GL = size_t(L0.G) * size_t(L0.L);
+    auto take = [&](size_t bytes) { const size_t o = s; s += align_up(bytes); return o; };
+    pl->o_c = take(GL * NB * es);
+    pl->o_d = take(GL * es);
+    pl->o_s = take(GL * es);
+    pl->o_r = take(GL * NB * es);
+    pl->o_gy = take(GL * NB * es);
+    pl->o_x = take(GL * NB * es);
+    pl->o_g = take(GL * NB * es);
+    if (es == 4) {
+      pl->o_yh = take(GL * NB * 4);
+      pl->o_yl = take(GL * NB * 4);
+      pl->o_gh = take(GL * NB * 4);
+      pl->o_gl = take(GL * NB * 4);
+    }
+    pl->o_gc = take(GL * NB * es);
+    pl->o_gd = take(GL * es);
+    pl->o_nrm = take(size_t(S) * 2 * sizeof(double));
   }
-  pl->o_nrm = s; s += align_up(size_t(S) * 2 * sizeof(double));
   pl->factor_bytes = f;
-  pl->solve_bytes = s;
 
   // sequence chunks for the gradient kernel (level-0 chunk length)
   std::vector<int32_t> sq_b, sq_k;
@@ -706,10 +791,13 @@ smnn_status build_plan(smnn_plan_s* pl) {
     for (int64_t k = 0; k < K; ++k) { sq_b.push_back(int32_t(b)); sq_k.push_back(int32_t(k)); }
   }
   pl->Q = int64_t(sq_b.size());
+  pl->o_gs = s;
+  s += align_up(size_t(pl->Q) * size_t(L0) * es);
+  pl->solve_bytes = s;
 
   size_t tb = 0;  // one device allocation for every table
   for (auto& L : pl->lv) tb += align_up(L.G * 4) + align_up((S + 1) * 8) + 2 * align_up(S * 8);
-  tb += 3 * align_up(S * 8) + align_up(pl->B * 8) + 2 * align_up(pl->Q * 4);
+  tb += 3 * align_up(S * 8) + 2 * align_up(pl->B * 8) + 2 * align_up(pl->Q * 4);
   if (cudaMalloc(&pl->tables, tb) != cudaSuccess) { pl->tables = nullptr; return SMNN_ERR_CUDA; }
   std::vector<char> host(tb, 0);
   char* hp = host.data();
@@ -730,6 +818,7 @@ smnn_status build_plan(smnn_plan_s* pl) {
   put(pl->sys_T.data(), S * 8, &pl->d_sys_T);
   put(pl->sys_off.data(), S * 8, &pl->d_sys_off);
   put(pl->seq_soff.data(), pl->B * 8, &pl->d_seq_soff);
+  put(pl->seq_T.data(), pl->B * 8, &pl->d_seq_T);
   put(sq_b.data(), pl->Q * 4, &pl->d_sq_b);
   put(sq_k.data(), pl->Q * 4, &pl->d_sq_k);
   if (cudaMemcpy(pl->tables, host.data(), tb, cudaMemcpyHostToDevice) != cudaSuccess) return SMNN_ERR_CUDA;
@@ -784,23 +873,30 @@ Problem0 problem0(const smnn_plan_s* pl, const void* c, const void* d, const voi
   return p;
 }
 
+template <class Tr>
+L0In<Tr> l0_in(const smnn_plan_s* pl, char* sol) {
+  return L0In<Tr>{reinterpret_cast<const Tr*>(sol + pl->o_c), reinterpret_cast<const Tr*>(sol + pl->o_d),
+                  reinterpret_cast<const Tr*>(sol + pl->o_s)};
+}
+
 // One pass of the chunked solve: eliminate level by level (factor, or replay the stored
-// factor on a new right-hand side), then back substitute; level-0 output per `out`.
+// factor on a new right-hand side), then back substitute; level-0 output per `out`/`mode`.
 template <class Tr, int NB>
 smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, bool factor,
                        char* fac, char* sol, const Level0Out<Tr>& out, int mode, int32_t* info,
                        cudaStream_t st) {
   const int nl = int(pl->lv.size());
+  const L0In<Tr> in = l0_in<Tr>(pl, sol);
   for (int l = 0; l < nl; ++l) {
     const Level& L = pl->lv[l];
     const LevelTables lt = tables_of(L);
     const LevelBufs<Tr, NB> lb = bufs_of<Tr, NB>(L, fac, sol);
     const bool top = l == nl - 1;
     if (l == 0) {
-      if (factor && top) SMNN_LAUNCH((k_elim0<Tr, NB, true, true>), L.G, st, lt, lb, p, rhs, info);
-      else if (factor) SMNN_LAUNCH((k_elim0<Tr, NB, true, false>), L.G, st, lt, lb, p, rhs, info);
-      else if (top) SMNN_LAUNCH((k_elim0<Tr, NB, false, true>), L.G, st, lt, lb, p, rhs, info);
-      else SMNN_LAUNCH((k_elim0<Tr, NB, false, false>), L.G, st, lt, lb, p, rhs, info);
+      if (factor && top) SMNN_LAUNCH((k_elim0<Tr, NB, true, true>), L.G, st, lt, lb, p, in, rhs, info);
+      else if (factor) SMNN_LAUNCH((k_elim0<Tr, NB, true, false>), L.G, st, lt, lb, p, in, rhs, info);
+      else if (top) SMNN_LAUNCH((k_elim0<Tr, NB, false, true>), L.G, st, lt, lb, p, in, rhs, info);
+      else SMNN_LAUNCH((k_elim0<Tr, NB, false, false>), L.G, st, lt, lb, p, in, rhs, info);
     } else {
       const ChunkOut<Tr, NB> prev = bufs_of<Tr, NB>(pl->lv[l - 1], fac, sol).out;
       if (factor && top) SMNN_LAUNCH((k_elimN<Tr, NB, true, true>), L.G, st, lt, lb, prev, pl->d_sys_T, info);
@@ -817,92 +913,105 @@ smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, 
   }
   const Level& L0 = pl->lv[0];
   const LevelBufs<Tr, NB> lb0 = bufs_of<Tr, NB>(L0, fac, sol);
-  if (mode == 0) SMNN_LAUNCH((k_backsub0<Tr, NB, 0>), L0.G, st, tables_of(L0), lb0, p, out, info);
-  else if constexpr (std::is_same<Tr, float>::value)
-    SMNN_LAUNCH((k_backsub0<Tr, NB, 1>), L0.G, st, tables_of(L0), lb0, p, out, info);
+  if (mode == 0) {
+    SMNN_LAUNCH((k_backsub0<Tr, NB, 0>), L0.G, st, tables_of(L0), lb0, p, in, out, info);
+  } else if constexpr (std::is_same<Tr, float>::value) {
+    if (mode == 1) SMNN_LAUNCH((k_backsub0<Tr, NB, 1>), L0.G, st, tables_of(L0), lb0, p, in, out, info);
+    else SMNN_LAUNCH((k_backsub0<Tr, NB, 2>), L0.G, st, tables_of(L0), lb0, p, in, out, info);
+  }
   return SMNN_OK;
 }
 
-struct RefineBufs {  // FP32 refinement scratch in the solve region
-  float* r;               // residual [N0][NB]
-  float* y_hi; float* y_lo;  // float-float accumulator of y
-  float* g_hi; float* g_lo;  // float-float accumulator of g (adjoint)
-  double* nrm;            // [S][2]
+template <class Tr>
+struct L0Bufs {  // level-0 interleaved scratch of one call
+  Tr* c; Tr* d; Tr* s; Tr* r; Tr* gy; Tr* x; Tr* g;
+  float* yh; float* yl; float* gh; float* gl;
+  Tr* gc; Tr* gd; Tr* gs;
+  double* nrm;
 };
 
-RefineBufs refine_bufs(const smnn_plan_s* pl, char* sol) {
-  RefineBufs b;
-  b.r = reinterpret_cast<float*>(sol + pl->o_r);
-  b.y_hi = reinterpret_cast<float*>(sol + pl->o_yh);
-  b.y_lo = reinterpret_cast<float*>(sol + pl->o_yl);
-  b.g_hi = reinterpret_cast<float*>(sol + pl->o_gh);
-  b.g_lo = reinterpret_cast<float*>(sol + pl->o_gl);
-  b.nrm = reinterpret_cast<double*>(sol + pl->o_nrm);
-  return b;
+template <class Tr>
+L0Bufs<Tr> l0_bufs(const smnn_plan_s* pl, char* sol) {
+  auto P = [&](size_t o) { return reinterpret_cast<Tr*>(sol + o); };
+  auto F = [&](size_t o) { return reinterpret_cast<float*>(sol + o); };
+  return L0Bufs<Tr>{P(pl->o_c), P(pl->o_d), P(pl->o_s), P(pl->o_r), P(pl->o_gy), P(pl->o_x),
+                    P(pl->o_g), F(pl->o_yh), F(pl->o_yl), F(pl->o_gh), F(pl->o_gl), P(pl->o_gc),
+                    P(pl->o_gd), P(pl->o_gs), reinterpret_cast<double*>(sol + pl->o_nrm)};
+}
+
+inline int64_t l0_elems(const smnn_plan_s* pl) { return pl->lv[0].G * int64_t(pl->lv[0].L); }
+
+template <class Tr, int NB>
+smnn_status gather_inputs(const smnn_plan_s* pl, const Problem0& p, const L0Bufs<Tr>& b,
+                          const Tr* vec, Tr* vec_out, float* vec_lo, bool coefs, cudaStream_t st) {
+  SMNN_LAUNCH((k_gather0<Tr, NB>), l0_elems(pl), st, tables_of(pl->lv[0]), p,
+              coefs ? b.c : nullptr, b.d, b.s, vec, vec_out, vec_lo);
+  return SMNN_OK;
 }
 
 template <class N, int NB>
-smnn_status residual(const smnn_plan_s* pl, const Problem0& p, const float* xh, const float* xl,
-                     const float* rhs, float* r, cudaStream_t st) {
-  SMNN_LAUNCH((k_residual<N, NB>), pl->lv[0].G, st, tables_of(pl->lv[0]), p, xh, xl, rhs, r);
+smnn_status residual(const smnn_plan_s* pl, const Problem0& p, const L0Bufs<float>& b,
+                     const float* xh, const float* xl, const float* rhs, cudaStream_t st) {
+  const L0In<float> in{b.c, b.d, b.s};
+  SMNN_LAUNCH((k_residual<N, NB>), pl->lv[0].G, st, tables_of(pl->lv[0]), p, in, xh, xl, rhs, b.r);
   return SMNN_OK;
 }
+
+#define SMNN_TRY(x) do { const smnn_status rc_ = (x); if (rc_ != SMNN_OK) return rc_; } while (0)
 
 // Forward solve with refinement in number type N (double: FP64 residual; ff: float-float).
 template <class N, int NB>
 smnn_status refine_forward(const smnn_plan_s* pl, const Problem0& p, char* fac, char* sol,
-                           float* y, int32_t* info, cudaStream_t st) {
-  const RefineBufs rb = refine_bufs(pl, sol);
+                           int32_t* info, cudaStream_t st) {
+  const L0Bufs<float> b = l0_bufs<float>(pl, sol);
   const int K = pl->desc.max_refine;
   const bool check = pl->desc.refine_tol > 0;
-  Level0Out<float> o{K == 0 ? y : nullptr, rb.y_hi, rb.y_lo, nullptr, nullptr, nullptr};
-  smnn_status rc = solve_pass<float, NB>(pl, p, nullptr, true, fac, sol, o, 1, info, st);
-  for (int it = 0; it < K && rc == SMNN_OK; ++it) {
+  Level0Out<float> o{nullptr, b.yh, b.yl, nullptr};
+  SMNN_TRY((solve_pass<float, NB>(pl, p, nullptr, true, fac, sol, o, 1, info, st)));
+  for (int it = 0; it < K; ++it) {
     const bool last = it + 1 == K;
-    if (check && last) SMNN_LAUNCH(k_fill_f64, 2 * pl->S, st, rb.nrm, 2 * pl->S, 0.0);
-    rc = residual<N, NB>(pl, p, rb.y_hi, rb.y_lo, nullptr, rb.r, st);
-    if (rc != SMNN_OK) return rc;
-    Level0Out<float> oa{last ? y : nullptr, rb.y_hi, rb.y_lo, rb.y_hi, rb.y_lo,
-                        check && last ? rb.nrm : nullptr};
-    rc = solve_pass<float, NB>(pl, p, rb.r, false, fac, sol, oa, 1, info, st);
+    if (check && last) SMNN_LAUNCH(k_fill_f64, 2 * pl->S, st, b.nrm, 2 * pl->S, 0.0);
+    SMNN_TRY((residual<N, NB>(pl, p, b, b.yh, b.yl, nullptr, st)));
+    Level0Out<float> oa{nullptr, b.yh, b.yl, check && last ? b.nrm : nullptr};
+    SMNN_TRY((solve_pass<float, NB>(pl, p, b.r, false, fac, sol, oa, 2, info, st)));
   }
-  if (rc == SMNN_OK && check && K > 0)
-    SMNN_LAUNCH(k_refine_check, pl->S, st, rb.nrm, pl->S, pl->desc.refine_tol, info);
-  return rc;
+  if (check && K > 0) SMNN_LAUNCH(k_refine_check, pl->S, st, b.nrm, pl->S, pl->desc.refine_tol, info);
+  return SMNN_OK;
 }
 
 // Adjoint: g = M^{-1} gy refined KA times, y re-refined once from the caller's FP32 y (both
 // kept as float-float), then the fused gradients in number type N.
 template <class N, int NB>
 smnn_status refine_backward(const smnn_plan_s* pl, const Problem0& p, char* fac, char* sol,
-                            bool factor, const float* y, const float* gy, float* gc, float* gd,
-                            float* gs, float* gu, int32_t* info, cudaStream_t st) {
-  const RefineBufs rb = refine_bufs(pl, sol);
+                            bool factor, const float* y, int32_t* info, cudaStream_t st) {
+  const L0Bufs<float> b = l0_bufs<float>(pl, sol);
   const int KA = pl->desc.precision == SMNN_F32 ? 0 : pl->desc.adjoint_refine;
-  Level0Out<float> og{nullptr, rb.g_hi, rb.g_lo, nullptr, nullptr, nullptr};
-  smnn_status rc = solve_pass<float, NB>(pl, p, gy, factor, fac, sol, og, 1, info, st);
-  if (rc != SMNN_OK) return rc;
-  const float* yh = y;
-  const float* yl = nullptr;
+  Level0Out<float> og{nullptr, b.gh, b.gl, nullptr};
+  SMNN_TRY((solve_pass<float, NB>(pl, p, b.gy, factor, fac, sol, og, 1, info, st)));
+  SMNN_TRY((gather_inputs<float, NB>(pl, p, b, y, b.yh, b.yl, false, st)));
   if (KA > 0) {
-    rc = residual<N, NB>(pl, p, y, nullptr, nullptr, rb.r, st);
-    if (rc != SMNN_OK) return rc;
-    Level0Out<float> oy{nullptr, rb.y_hi, rb.y_lo, y, nullptr, nullptr};
-    rc = solve_pass<float, NB>(pl, p, rb.r, false, fac, sol, oy, 1, info, st);
-    if (rc != SMNN_OK) return rc;
-    yh = rb.y_hi;
-    yl = rb.y_lo;
+    SMNN_TRY((residual<N, NB>(pl, p, b, b.yh, nullptr, nullptr, st)));
+    Level0Out<float> oy{nullptr, b.yh, b.yl, nullptr};
+    SMNN_TRY((solve_pass<float, NB>(pl, p, b.r, false, fac, sol, oy, 2, info, st)));
   }
   for (int it = 0; it < KA; ++it) {
-    rc = residual<N, NB>(pl, p, rb.g_hi, rb.g_lo, gy, rb.r, st);
-    if (rc != SMNN_OK) return rc;
-    Level0Out<float> oa{nullptr, rb.g_hi, rb.g_lo, rb.g_hi, rb.g_lo, nullptr};
-    rc = solve_pass<float, NB>(pl, p, rb.r, false, fac, sol, oa, 1, info, st);
-    if (rc != SMNN_OK) return rc;
+    SMNN_TRY((residual<N, NB>(pl, p, b, b.gh, b.gl, b.gy, st)));
+    Level0Out<float> oa{nullptr, b.gh, b.gl, nullptr};
+    SMNN_TRY((solve_pass<float, NB>(pl, p, b.r, false, fac, sol, oa, 2, info, st)));
   }
-  GradTables gt{pl->d_sq_b, pl->d_sq_k, pl->d_sys_off, pl->d_sys_T, pl->d_seq_soff, pl->Q,
-                pl->lv[0].L, int(pl->D)};
-  SMNN_LAUNCH((k_grad<float, N, NB>), pl->Q, st, gt, p, yh, yl, rb.g_hi, rb.g_lo, info, gc, gd, gs, gu);
+  return SMNN_OK;
+}
+
+template <class Tr, class N, int NB>
+smnn_status gradients_out(const smnn_plan_s* pl, const Problem0& p, const L0Bufs<Tr>& b,
+                          const Tr* yh, const float* yl, const Tr* gh, const float* gl,
+                          int32_t* info, Tr* gc, Tr* gd, Tr* gs, Tr* gu, cudaStream_t st) {
+  const Level& L0 = pl->lv[0];
+  GradTables gt{pl->d_sq_b, pl->d_sq_k, L0.d_coff, pl->d_sys_T, pl->Q, L0.G, L0.L, int(pl->D)};
+  const L0In<Tr> in{b.c, b.d, b.s};
+  SMNN_LAUNCH((k_grad<Tr, N, NB>), pl->Q, st, gt, p, in, yh, yl, gh, gl, info, b.gc, b.gd, b.gs, gu);
+  SMNN_LAUNCH((k_scatter0<Tr, Tr, NB>), l0_elems(pl), st, tables_of(L0), b.gc, nullptr, gc, b.gd, gd);
+  SMNN_LAUNCH(k_scatter_gs<Tr>, pl->Q * int64_t(L0.L), st, gt, pl->d_seq_soff, pl->d_seq_T, b.gs, gs);
   return SMNN_OK;
 }
 
@@ -913,15 +1022,24 @@ smnn_status factor_solve_t(const smnn_plan_s* pl, const void* c, const void* d, 
   const Problem0 p = problem0(pl, c, d, s, u);
   char* fac = factor ? static_cast<char*>(factor) : static_cast<char*>(ws);
   char* sol = static_cast<char*>(ws) + pl->factor_bytes;
+  const L0Bufs<Tr> b = l0_bufs<Tr>(pl, sol);
+  const LevelTables lt0 = tables_of(pl->lv[0]);
   SMNN_LAUNCH(k_fill_i32, pl->S, st, info, pl->S, 0);
+  SMNN_TRY((gather_inputs<Tr, NB>(pl, p, b, nullptr, nullptr, nullptr, true, st)));
   if constexpr (std::is_same<Tr, float>::value) {
-    if (pl->desc.precision == SMNN_F32_REFINED)
-      return refine_forward<double, NB>(pl, p, fac, sol, static_cast<float*>(y), info, st);
-    if (pl->desc.precision == SMNN_F32_REFINED_DF)
-      return refine_forward<ff, NB>(pl, p, fac, sol, static_cast<float*>(y), info, st);
+    if (pl->desc.precision == SMNN_F32_REFINED || pl->desc.precision == SMNN_F32_REFINED_DF) {
+      if (pl->desc.precision == SMNN_F32_REFINED) SMNN_TRY((refine_forward<double, NB>(pl, p, fac, sol, info, st)));
+      else SMNN_TRY((refine_forward<ff, NB>(pl, p, fac, sol, info, st)));
+      SMNN_LAUNCH((k_scatter0<float, float, NB>), l0_elems(pl), st, lt0, b.yh, b.yl,
+                  static_cast<float*>(y), nullptr, nullptr);
+      return SMNN_OK;
+    }
   }
-  Level0Out<Tr> o{static_cast<Tr*>(y), nullptr, nullptr, nullptr, nullptr, nullptr};
-  return solve_pass<Tr, NB>(pl, p, nullptr, true, fac, sol, o, 0, info, st);
+  Level0Out<Tr> o{b.x, nullptr, nullptr, nullptr};
+  SMNN_TRY((solve_pass<Tr, NB>(pl, p, nullptr, true, fac, sol, o, 0, info, st)));
+  SMNN_LAUNCH((k_scatter0<Tr, Tr, NB>), l0_elems(pl), st, lt0, b.x, nullptr, static_cast<Tr*>(y),
+              nullptr, nullptr);
+  return SMNN_OK;
 }
 
 template <class Tr, int NB>
@@ -931,38 +1049,38 @@ smnn_status backward_t(const smnn_plan_s* pl, const void* c, const void* d, cons
   const Problem0 p = problem0(pl, c, d, s, u);
   char* fac = factor ? static_cast<char*>(const_cast<void*>(factor)) : static_cast<char*>(ws);
   char* sol = static_cast<char*>(ws) + pl->factor_bytes;
+  const L0Bufs<Tr> b = l0_bufs<Tr>(pl, sol);
   SMNN_LAUNCH(k_fill_i32, pl->S, st, info, pl->S, 0);
+  SMNN_TRY((gather_inputs<Tr, NB>(pl, p, b, static_cast<const Tr*>(gy), b.gy, nullptr, true, st)));
+  Tr* gco = static_cast<Tr*>(gc);
+  Tr* gdo = static_cast<Tr*>(gd);
+  Tr* gso = static_cast<Tr*>(gs);
+  Tr* guo = static_cast<Tr*>(gu);
   if constexpr (std::is_same<Tr, float>::value) {
-    auto* y32 = static_cast<const float*>(y);
-    auto* gy32 = static_cast<const float*>(gy);
-    auto* o = reinterpret_cast<float*>(gc);
-    if (pl->desc.precision == SMNN_F32_REFINED_DF)
-      return refine_backward<ff, NB>(pl, p, fac, sol, factor == nullptr, y32, gy32, o,
-                                     static_cast<float*>(gd), static_cast<float*>(gs),
-                                     static_cast<float*>(gu), info, st);
-    return refine_backward<double, NB>(pl, p, fac, sol, factor == nullptr, y32, gy32, o,
-                                       static_cast<float*>(gd), static_cast<float*>(gs),
-                                       static_cast<float*>(gu), info, st);
+    const float* y32 = static_cast<const float*>(y);
+    if (pl->desc.precision == SMNN_F32_REFINED_DF) {
+      SMNN_TRY((refine_backward<ff, NB>(pl, p, fac, sol, factor == nullptr, y32, info, st)));
+      return gradients_out<float, ff, NB>(pl, p, b, b.yh, b.yl, b.gh, b.gl, info, gco, gdo, gso, guo, st);
+    }
+    SMNN_TRY((refine_backward<double, NB>(pl, p, fac, sol, factor == nullptr, y32, info, st)));
+    return gradients_out<float, double, NB>(pl, p, b, b.yh, b.yl, b.gh, b.gl, info, gco, gdo, gso, guo, st);
   } else {
-    Tr* g = reinterpret_cast<Tr*>(sol + pl->o_g);
-    Level0Out<Tr> o{g, nullptr, nullptr, nullptr, nullptr, nullptr};
-    smnn_status rc = solve_pass<Tr, NB>(pl, p, static_cast<const Tr*>(gy), factor == nullptr, fac,
-                                        sol, o, 0, info, st);
-    if (rc != SMNN_OK) return rc;
-    GradTables gt{pl->d_sq_b, pl->d_sq_k, pl->d_sys_off, pl->d_sys_T, pl->d_seq_soff, pl->Q,
-                  pl->lv[0].L, int(pl->D)};
-    SMNN_LAUNCH((k_grad<Tr, double, NB>), pl->Q, st, gt, p, static_cast<const Tr*>(y), nullptr, g,
-                nullptr, info, static_cast<Tr*>(gc), static_cast<Tr*>(gd), static_cast<Tr*>(gs),
-                static_cast<Tr*>(gu));
-    return SMNN_OK;
+    Level0Out<Tr> o{b.g, nullptr, nullptr, nullptr};
+    SMNN_TRY((solve_pass<Tr, NB>(pl, p, b.gy, factor == nullptr, fac, sol, o, 0, info, st)));
+    SMNN_TRY((gather_inputs<Tr, NB>(pl, p, b, static_cast<const Tr*>(y), b.x, nullptr, false, st)));
+    return gradients_out<Tr, double, NB>(pl, p, b, b.x, nullptr, b.g, nullptr, info, gco, gdo, gso, guo, st);
   }
 }
 
 template <class Tr, int NB>
 smnn_status assemble_t(const smnn_plan_s* pl, const void* c, const void* d, const void* s,
-                       const void* u, void* M, void* N, void* beta, cudaStream_t st) {
+                       const void* u, void* M, void* N, void* beta, void* ws, cudaStream_t st) {
   const Problem0 p = problem0(pl, c, d, s, u);
-  SMNN_LAUNCH((k_assemble<Tr, NB>), pl->lv[0].G, st, tables_of(pl->lv[0]), p, static_cast<Tr*>(M),
+  char* sol = static_cast<char*>(ws) + pl->factor_bytes;
+  const L0Bufs<Tr> b = l0_bufs<Tr>(pl, sol);
+  SMNN_TRY((gather_inputs<Tr, NB>(pl, p, b, nullptr, nullptr, nullptr, true, st)));
+  const L0In<Tr> in{b.c, b.d, b.s};
+  SMNN_LAUNCH((k_assemble<Tr, NB>), pl->lv[0].G, st, tables_of(pl->lv[0]), p, in, static_cast<Tr*>(M),
               static_cast<Tr*>(N), static_cast<Tr*>(beta));
   return SMNN_OK;
 }
@@ -1088,11 +1206,13 @@ smnn_status smnn_workspace_size(smnn_plan plan, size_t* workspace_bytes, size_t*
 }
 
 smnn_status smnn_assemble(smnn_plan plan, const void* c, const void* d, const void* s, const void* u,
-                          void* M, void* N, void* beta, void* stream) {
+                          void* M, void* N, void* beta, void* workspace, void* stream) {
   if (!plan || !c || !d || !s || !u || !M || !N || !beta) return SMNN_ERR_INVALID_ARG;
+  if (!workspace || !aligned(workspace)) return SMNN_ERR_WORKSPACE;
   DeviceGuard dg(plan->device);
   if (!dg.ok) return SMNN_ERR_CUDA;
-  SMNN_DISPATCH(plan, assemble_t, plan, c, d, s, u, M, N, beta, static_cast<cudaStream_t>(stream));
+  SMNN_DISPATCH(plan, assemble_t, plan, c, d, s, u, M, N, beta, workspace,
+                static_cast<cudaStream_t>(stream));
 }
 
 smnn_status smnn_factor_solve(smnn_plan plan, const void* c, const void* d, const void* s,

@@ -224,22 +224,31 @@ struct ChunkOut {
 // ----------------------------------------------------------------------------- sources
 
 // Level-0 blocks, assembled in registers from the paper's representation {c, d, u, s}
-// (App. A.2).  Pointers are already offset to the system.
+// (App. A.2).  The per-step inputs sit in the chunk-interleaved layout of the factor:
+// element e of in-chunk position j of chunk g at [(e*L + j)*G + g]; steps of the previous
+// chunk (g-1, position L-1) are reached for t = first-1.
 template <class Tr, int NB>
 struct CoefSource {
-  const Tr* c;     // [T][NB]
-  const Tr* d;     // [T]
-  const Tr* s;     // [T]
-  const Tr* u;     // [T_init][R_init+1]
-  const Tr* rhs;   // explicit right-hand side [T][NB], or nullptr for beta_t
-  int64_t T;
+  const Tr* c;     // [NB][L][G]
+  const Tr* d;     // [L][G]
+  const Tr* s;     // [L][G]
+  const Tr* u;     // this system's initial values [T_init][R_init+1]
+  const Tr* rhs;   // explicit right-hand side [NB][L][G], or nullptr for beta_t
+  int64_t T, first, g, G;
+  int L;
   Tr wg2, wi2, ws2;
   int T_init, R_init;
 
+  SMNN_HD int64_t at(int64_t t) const {
+    return t >= first ? (t - first) * G + g : int64_t(L - 1) * G + (g - 1);
+  }
+  SMNN_HD int64_t es() const { return int64_t(L) * G; }
+
   SMNN_HD void A(int64_t t, Tr (&a)[NB][NB]) const {
+    const int64_t k = at(t);
     Tr cv[NB];
 #pragma unroll
-    for (int r = 0; r < NB; ++r) cv[r] = c[t * NB + r];
+    for (int r = 0; r < NB; ++r) cv[r] = c[r * es() + k];
 #pragma unroll
     for (int i = 0; i < NB; ++i)
 #pragma unroll
@@ -249,8 +258,8 @@ struct CoefSource {
       for (int r = 0; r < NB; ++r)
         if (r <= R_init) a[r][r] += wi2;
     }
-    if (t + 1 < T) add_smooth<false>(s[t], a);
-    if (t > 0) add_smooth<true>(s[t - 1], a);
+    if (t + 1 < T) add_smooth<false>(s[k], a);
+    if (t > 0) add_smooth<true>(s[at(t - 1)], a);
   }
 
   // w_s^2 ((S+- F^T F S+-) + S2) of the pair (t, t+1), seen from t (kMinus = false) or
@@ -273,14 +282,15 @@ struct CoefSource {
   }
 
   SMNN_HD void b(int64_t t, Tr (&v)[NB]) const {
+    const int64_t k = at(t);
     if (rhs) {
 #pragma unroll
-      for (int r = 0; r < NB; ++r) v[r] = rhs[t * NB + r];
+      for (int r = 0; r < NB; ++r) v[r] = rhs[r * es() + k];
       return;
     }
-    const Tr dt = d[t];
+    const Tr dt = d[k];
 #pragma unroll
-    for (int r = 0; r < NB; ++r) v[r] = wg2 * c[t * NB + r] * dt;
+    for (int r = 0; r < NB; ++r) v[r] = wg2 * c[r * es() + k] * dt;
     if (t < T_init) {
 #pragma unroll
       for (int r = 0; r < NB; ++r)
@@ -290,7 +300,7 @@ struct CoefSource {
 
   // E_t = N_t = block (t+1, t), t < T-1
   SMNN_HD void E(int64_t t, Tr (&e)[NB][NB]) const {
-    const Tr st = s[t];
+    const Tr st = s[at(t)];
     Tr pw[2 * NB - 1];
     pw[0] = Tr(1);
 #pragma unroll
