@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
+    ap.add_argument("--chunk", type=int, default=0, help="level-0 chunk length (0: plan's table)")
+    ap.add_argument("--only", default="", help="comma-separated variants to time (default: all)")
     return ap.parse_args()
 
 
@@ -186,11 +188,11 @@ def algorithmic_units(name: str, NB: int, D: int):
 class Variant:
     """One precision mode of the library on the benchmark workload: its plan and buffers."""
 
-    def __init__(self, pk, prob, precision, dev, inputs, factor=True):
+    def __init__(self, pk, prob, precision, dev, inputs, factor=True, chunk=0):
         import torch
         self.precision = precision
         cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=precision,
-                             max_refine=2, adjoint_refine=3)
+                             max_refine=2, adjoint_refine=3, chunk=chunk)
         self.plan = pk.get_plan((prob.R, prob.B, prob.D, prob.T), cfg)
         dt = self.plan.dtype
         self.c, self.d, self.s, self.u = (t.to(dt) for t in inputs)
@@ -247,8 +249,10 @@ def run_ours(args, ws, rank, local):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    variants = {"F32_REFINED_DF": Variant(pk, prob, pk.F32_REFINED_DF, dev, inputs),
-                "F32_REFINED": Variant(pk, prob, pk.F32_REFINED, dev, inputs)}
+    only = set(x for x in args.only.split(",") if x)
+    variants = {"F32_REFINED_DF": Variant(pk, prob, pk.F32_REFINED_DF, dev, inputs, chunk=args.chunk)}
+    if not only or "F32_REFINED" in only:
+        variants["F32_REFINED"] = Variant(pk, prob, pk.F32_REFINED, dev, inputs, chunk=args.chunk)
     # dl/dy of config 2's loss, mean over S*T of (y^(0) - tau)^2, at this workload's y
     v0 = variants["F32_REFINED_DF"]
     v0.forward()
@@ -257,8 +261,8 @@ def run_ours(args, ws, rank, local):
     gy[..., 0] = 2.0 * (v0.y[..., 0] - tau) / float(steps_per_pass)
     for v in variants.values():
         v.gy = gy
-    if not args.no_fp64:
-        v64 = Variant(pk, prob, pk.F64, dev, inputs)
+    if not args.no_fp64 and (not only or "F64" in only):
+        v64 = Variant(pk, prob, pk.F64, dev, inputs, chunk=args.chunk)
         v64.gy = gy.double()
         variants["F64"] = v64
     torch.cuda.synchronize()

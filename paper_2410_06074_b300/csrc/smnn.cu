@@ -531,71 +531,64 @@ __device__ __forceinline__ N smooth_pair_grad(Ts s, N ws2, const N (&ya)[NB], co
   return -(ws2 * acc);
 }
 
-// One thread per (sequence, level-0 chunk index): loops over the D systems of the sequence
-// (their chunk k sits at coff0[b*D + dd] + k), writes gc, gd (interleaved by system chunk),
-// gs (interleaved by sequence chunk, summed over D) and gu (user layout).
+// One thread per level-0 chunk of one system: gc, gd (interleaved), this system's share of
+// gs (interleaved; the D systems of a sequence are summed in k_scatter_gs) and gu.
 template <class Tr, class N, int NB>
-__global__ void __launch_bounds__(kThreads) k_grad(GradTables gt, Problem0 p, L0In<Tr> in,
+__global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L0In<Tr> in,
                                                    const Tr* y_hi, const float* y_lo, const Tr* g_hi,
                                                    const float* g_lo, const int32_t* info, Tr* gc,
                                                    Tr* gd, Tr* gs, Tr* gu) {
-  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (q >= gt.Q) return;
-  const int64_t b = gt.sq_b[q];
-  const int64_t kc = gt.sq_k[q];
-  const int64_t i0 = b * gt.D;
-  const int64_t T = gt.sys_T[i0];
-  const int64_t first = kc * gt.L;
-  const int64_t last = min(first + gt.L, T) - 1;
-  const int64_t G = gt.G, es = int64_t(gt.L) * G;
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= lt.G) return;
+  const ChunkPos cp = chunk_pos(lt, g);
+  const int64_t G = lt.G, es = int64_t(lt.L) * G;
   const int nu = p.T_init * (p.R_init + 1);
   const N wg2 = Num<N>::from_d(p.wg2), wi2 = Num<N>::from_d(p.wi2), ws2 = Num<N>::from_d(p.ws2);
-  bool any_fail = false;
-  for (int dd = 0; dd < gt.D; ++dd) any_fail = any_fail || info[i0 + dd] > 0;
-  for (int64_t t = first; t <= last; ++t) {
+  const bool failed = info[cp.i] > 0;
+  N ya[NB], ga[NB];
+  int64_t k = g;
+#pragma unroll
+  for (int a = 0; a < NB; ++a) {
+    ya[a] = ld_pair<N>(y_hi, y_lo, a * es + k);
+    ga[a] = ld_pair<N>(g_hi, g_lo, a * es + k);
+  }
+  for (int64_t t = cp.first; t <= cp.last; ++t) {
+    N cy = Num<N>::zero(), cg = Num<N>::zero();
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      const N cv = ld_n<N>(in.c[a * es + k]);
+      cy = cy + cv * ya[a];
+      cg = cg + cv * ga[a];
+    }
+    const N e = ld_n<N>(in.d[k]) - cy;
+#pragma unroll
+    for (int a = 0; a < NB; ++a)
+      gc[a * es + k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * (e * ga[a] - cg * ya[a]));
+    gd[k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * cg);
+    if (t < p.T_init) {
+      for (int a = 0; a <= p.R_init; ++a)
+        gu[cp.i * nu + t * (p.R_init + 1) + a] = failed ? nan_t<Tr>() : st_n<Tr, N>(wi2 * ga[a]);
+    }
     N gsum = Num<N>::zero();
-    const bool pair = t + 1 < T;
-    const int j = int(t - first);
-    for (int dd = 0; dd < gt.D; ++dd) {
-      const int64_t i = i0 + dd;
-      const int64_t g = gt.coff0[i] + kc;
-      const int64_t k = int64_t(j) * G + g;
-      const int64_t kn = t + 1 <= last ? k + G : g + 1;   // step t+1: next position or next chunk
-      const bool failed = info[i] > 0;
-      N ya[NB], ga[NB];
-      N cy = Num<N>::zero(), cg = Num<N>::zero();
+    const int64_t kn = t < cp.last ? k + G : g + 1;   // step t+1: next position or next chunk
+    if (t + 1 < cp.T) {
+      N yb[NB], gb[NB];
 #pragma unroll
       for (int a = 0; a < NB; ++a) {
-        ya[a] = ld_pair<N>(y_hi, y_lo, a * es + k);
-        ga[a] = ld_pair<N>(g_hi, g_lo, a * es + k);
-        const N cv = ld_n<N>(in.c[a * es + k]);
-        cy = cy + cv * ya[a];
-        cg = cg + cv * ga[a];
+        yb[a] = ld_pair<N>(y_hi, y_lo, a * es + kn);
+        gb[a] = ld_pair<N>(g_hi, g_lo, a * es + kn);
       }
-      const N e = ld_n<N>(in.d[k]) - cy;
+      gsum = smooth_pair_grad<N, NB, Tr>(in.s[k], ws2, ya, yb, ga, gb);
 #pragma unroll
-      for (int a = 0; a < NB; ++a)
-        gc[a * es + k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * (e * ga[a] - cg * ya[a]));
-      gd[k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * cg);
-      if (t < p.T_init) {
-        for (int a = 0; a <= p.R_init; ++a)
-          gu[i * nu + t * (p.R_init + 1) + a] = failed ? nan_t<Tr>() : st_n<Tr, N>(wi2 * ga[a]);
-      }
-      if (pair) {
-        N yb[NB], gb[NB];
-#pragma unroll
-        for (int a = 0; a < NB; ++a) {
-          yb[a] = ld_pair<N>(y_hi, y_lo, a * es + kn);
-          gb[a] = ld_pair<N>(g_hi, g_lo, a * es + kn);
-        }
-        gsum = gsum + smooth_pair_grad<N, NB, Tr>(in.s[k], ws2, ya, yb, ga, gb);
-      }
+      for (int a = 0; a < NB; ++a) { ya[a] = yb[a]; ga[a] = gb[a]; }
     }
-    gs[int64_t(j) * gt.Q + q] = any_fail ? nan_t<Tr>() : st_n<Tr, N>(gsum);
+    gs[k] = failed ? nan_t<Tr>() : st_n<Tr, N>(gsum);
+    k += G;
   }
 }
 
-// gs: sequence-chunk interleaved -> user layout of s
+// gs: sum of the D systems' shares (system-chunk interleaved) -> user layout of s.  One
+// thread per (sequence chunk q, position j); the sum runs over dd in order.
 template <class Tr>
 __global__ void k_scatter_gs(GradTables gt, const int64_t* seq_soff, const int64_t* seq_T,
                              const Tr* gsI, Tr* gs) {
@@ -604,9 +597,12 @@ __global__ void k_scatter_gs(GradTables gt, const int64_t* seq_soff, const int64
   const int64_t q = n % gt.Q;
   const int j = int(n / gt.Q);
   const int64_t b = gt.sq_b[q];
-  const int64_t t = int64_t(gt.sq_k[q]) * gt.L + j;
+  const int64_t kc = gt.sq_k[q];
+  const int64_t t = kc * gt.L + j;
   if (t >= seq_T[b]) return;
-  gs[seq_soff[b] + t] = gsI[n];
+  Tr acc = Tr(0);
+  for (int dd = 0; dd < gt.D; ++dd) acc += gsI[int64_t(j) * gt.G + gt.coff0[b * gt.D + dd] + kc];
+  gs[seq_soff[b] + t] = acc;
 }
 
 // ---- materialised assembly (App. A.2) ---------------------------------------------------
@@ -792,7 +788,7 @@ smnn_status build_plan(smnn_plan_s* pl) {
   }
   pl->Q = int64_t(sq_b.size());
   pl->o_gs = s;
-  s += align_up(size_t(pl->Q) * size_t(L0) * es);
+  s += align_up(size_t(pl->lv[0].G) * size_t(L0) * es);
   pl->solve_bytes = s;
 
   size_t tb = 0;  // one device allocation for every table
@@ -1009,7 +1005,8 @@ smnn_status gradients_out(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
   const Level& L0 = pl->lv[0];
   GradTables gt{pl->d_sq_b, pl->d_sq_k, L0.d_coff, pl->d_sys_T, pl->Q, L0.G, L0.L, int(pl->D)};
   const L0In<Tr> in{b.c, b.d, b.s};
-  SMNN_LAUNCH((k_grad<Tr, N, NB>), pl->Q, st, gt, p, in, yh, yl, gh, gl, info, b.gc, b.gd, b.gs, gu);
+  SMNN_LAUNCH((k_grad<Tr, N, NB>), L0.G, st, tables_of(L0), p, in, yh, yl, gh, gl, info, b.gc, b.gd,
+              b.gs, gu);
   SMNN_LAUNCH((k_scatter0<Tr, Tr, NB>), l0_elems(pl), st, tables_of(L0), b.gc, nullptr, gc, b.gd, gd);
   SMNN_LAUNCH(k_scatter_gs<Tr>, pl->Q * int64_t(L0.L), st, gt, pl->d_seq_soff, pl->d_seq_T, b.gs, gs);
   return SMNN_OK;
