@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 from smnn_workloads import config2, mse_target  # noqa: E402
 
-WORKLOAD = "config2: B=512 D=8 T=1024 R=2, FP32 factor + 2 FP64-residual refinement sweeps, fwd+adjoint"
+WORKLOAD = "config2: B=512 D=8 T=1024 R=2, FP32 factor + refinement (3 forward, 3 adjoint sweeps), fwd+adjoint"
 METRIC = "time-steps solved/s fwd+bwd (FP32-refined, <=1e-6 vs FP64 oracle)"
 UNIT = "time-steps/s"
 
@@ -192,7 +192,7 @@ class Variant:
         import torch
         self.precision = precision
         cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=precision,
-                             max_refine=2, adjoint_refine=3, chunk=chunk)
+                             max_refine=3, adjoint_refine=3, chunk=chunk)
         self.plan = pk.get_plan((prob.R, prob.B, prob.D, prob.T), cfg)
         dt = self.plan.dtype
         self.c, self.d, self.s, self.u = (t.to(dt) for t in inputs)
@@ -440,7 +440,7 @@ def main():
         "data": "synthetic (seeded config-2 generators: c~N(0,1), c2=1+|N|, d~N(0,1), s~U[0.01,0.1], u~N(0,1))",
         "config": {"workload": WORKLOAD, "B": prob.B, "D": prob.D, "T": prob.T, "R": prob.R,
                    "time_steps_per_pass": prob.steps, "precision": "SMNN_" + head,
-                   "solver": prec_txt, "max_refine": 2, "adjoint_refine": 3,
+                   "solver": prec_txt, "max_refine": 3, "adjoint_refine": 3,
                    "factor": "stored in forward, reused in backward",
                    "l2": "256 MiB write between timed steps (outside the events)",
                    "parallelism": f"replicas x{ws} (independent systems, no collective)"},

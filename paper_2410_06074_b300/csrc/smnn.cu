@@ -6,7 +6,8 @@
 //               chunked order), or replay a stored factor on a new right-hand side
 //   k_elimN     level >= 1: the same on the separators' Schur complement
 //   k_backsubN  levels >= 1, then k_backsub0: back substitution (Alg. 4), writing y
-//   k_residual  refinement residual r = beta - M y (or gy - M g), evaluated in FP64
+//   k_elim0_res refinement sweep: level-0 replay whose right-hand side is the residual
+//               r = beta - M y (or gy - M g), evaluated on the fly in FP64 or float-float
 //               row by row (governing, initial and smoothness rows of Eq. 4-7)
 //   k_grad      parameter gradients from y and g = M^{-1} dl/dy (Eq. 14 chained through
 //               App. A.2), FP64 internally, summed over the D systems sharing s
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) k_elim0(LevelTables lt, LevelBufs<Tr
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
   const ChunkPos cp = chunk_pos(lt, g);
-  const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, in, rhs, cp.i, g, cp.first, cp.T, lt.L, lt.G);
+  CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, in, rhs, cp.i, g, cp.first, cp.T, lt.L, lt.G);
   int64_t fail = elim_chunk<Tr, NB, kFactor>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
   if (kTop) {
     if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = cp.last + 1;
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(kThreads) k_elimN(LevelTables lt, LevelBufs<Tr
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
   const ChunkPos cp = chunk_pos(lt, g);
-  const ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[cp.i], cp.T);
+  ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[cp.i], cp.T);
   int64_t fail = elim_chunk<Tr, NB, kFactor>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
   if (kTop) {
     if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = cp.last + 1;
@@ -409,74 +410,101 @@ __device__ __forceinline__ void smooth_pair_residual(float s, N ws2, const N (&x
   }
 }
 
-// r = rhs - M x over one level-0 chunk, rhs = beta (assembled, rhs == nullptr) or an explicit
-// vector; x given as float-float parts (x_lo may be null).  Interleaved in and out; the
-// neighbours x_{first-1}, x_{last+1} come from the adjacent chunks.  Rounded to FP32.
+// Level-0 source of a refinement sweep: blocks as CoefSource, right-hand side = the residual
+// r_t = rhs_t - (M x)_t evaluated on the fly in number type N (FP64 or float-float), so that
+// the residual never goes through memory.  b(t) must be called for consecutive t.
 template <class N, int NB>
-__global__ void __launch_bounds__(kThreads) k_residual(LevelTables lt, Problem0 p, L0In<float> in,
-                                                       const float* x_hi, const float* x_lo,
-                                                       const float* rhs, float* r_out) {
-  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (g >= lt.G) return;
-  const ChunkPos cp = chunk_pos(lt, g);
-  const int64_t G = lt.G, es = int64_t(lt.L) * lt.G;
-  const float* u = static_cast<const float*>(p.u) + cp.i * int64_t(p.T_init) * (p.R_init + 1);
-  const N wg2 = Num<N>::from_d(p.wg2), wi2 = Num<N>::from_d(p.wi2), ws2 = Num<N>::from_d(p.ws2);
-  auto idx = [&](int64_t t) -> int64_t {   // t in [first-1, last+1]
-    return t < cp.first ? int64_t(lt.L - 1) * G + (g - 1) : (t > cp.last ? g + 1 : (t - cp.first) * G + g);
-  };
-  auto load = [&](int64_t t, N (&v)[NB]) {
-    const int64_t k = idx(t);
-#pragma unroll
-    for (int a = 0; a < NB; ++a) v[a] = Num<N>::pair(x_hi[a * es + k], x_lo ? x_lo[a * es + k] : 0.f);
-  };
-
+struct ResidualSource {
+  CoefSource<float, NB> cs;
+  const float* xh;
+  const float* xl;
+  const float* rhs;     // explicit right-hand side (interleaved) or nullptr for beta
+  const float* u;
+  N wg2, wi2, ws2;
+  int64_t last;
   N xc[NB], carry[NB];
-  load(cp.first, xc);
-#pragma unroll
-  for (int a = 0; a < NB; ++a) carry[a] = Num<N>::zero();
-  if (cp.first > 0) {
-    N xp[NB], dummy[NB];
-    load(cp.first - 1, xp);
-    smooth_pair_residual<N, NB>(in.s[idx(cp.first - 1)], ws2, xp, xc, dummy, carry);
+
+  __device__ int64_t idx(int64_t t) const {
+    return t < cs.first ? int64_t(cs.L - 1) * cs.G + (cs.g - 1)
+                        : (t > last ? cs.g + 1 : (t - cs.first) * cs.G + cs.g);
   }
-  for (int64_t t = cp.first; t <= cp.last; ++t) {
-    const int64_t k = (t - cp.first) * G + g;
+  __device__ void load(int64_t t, N (&v)[NB]) const {
+    const int64_t k = idx(t), es = cs.es();
+#pragma unroll
+    for (int a = 0; a < NB; ++a) v[a] = Num<N>::pair(xh[a * es + k], xl ? xl[a * es + k] : 0.f);
+  }
+  __device__ void init() {
+    load(cs.first, xc);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) carry[a] = Num<N>::zero();
+    if (cs.first > 0) {
+      N xp[NB], dummy[NB];
+      load(cs.first - 1, xp);
+      smooth_pair_residual<N, NB>(cs.s[idx(cs.first - 1)], ws2, xp, xc, dummy, carry);
+    }
+  }
+  __device__ void A(int64_t t, float (&a)[NB][NB]) const { cs.A(t, a); }
+  __device__ void E(int64_t t, float (&e)[NB][NB]) const { cs.E(t, e); }
+  __device__ void b(int64_t t, float (&v)[NB]) {
+    const int64_t k = (t - cs.first) * cs.G + cs.g, es = cs.es();
     N r[NB];
     float cv[NB];
     N cx = Num<N>::zero();
 #pragma unroll
     for (int a = 0; a < NB; ++a) {
-      cv[a] = in.c[a * es + k];
+      cv[a] = cs.c[a * es + k];
       cx = cx + xc[a] * cv[a];
     }
     if (rhs) {
-      const N gres = -(wg2 * cx);   // beta replaced by the explicit right-hand side
+      const N gres = -(wg2 * cx);
 #pragma unroll
       for (int a = 0; a < NB; ++a) r[a] = (gres * cv[a] + rhs[a * es + k]) + carry[a];
     } else {
-      const N gres = wg2 * (cx - in.d[k]);  // -w_g^2 (d_t - c_t . x_t)
+      const N gres = wg2 * (cx - cs.d[k]);
 #pragma unroll
       for (int a = 0; a < NB; ++a) r[a] = carry[a] - gres * cv[a];
     }
-    if (t < p.T_init) {
+    if (t < cs.T_init) {
 #pragma unroll
       for (int a = 0; a < NB; ++a)
-        if (a <= p.R_init) {  // w_i^2 (u - x), u replaced by 0 for an explicit rhs
-          const N dv = rhs ? -xc[a] : -(xc[a] - u[t * (p.R_init + 1) + a]);
+        if (a <= cs.R_init) {
+          const N dv = rhs ? -xc[a] : -(xc[a] - u[t * (cs.R_init + 1) + a]);
           r[a] = r[a] + wi2 * dv;
         }
     }
-    if (t + 1 < cp.T) {
+    if (t + 1 < cs.T) {
       N xn[NB], ra[NB];
       load(t + 1, xn);
-      smooth_pair_residual<N, NB>(in.s[k], ws2, xc, xn, ra, carry);
+      smooth_pair_residual<N, NB>(cs.s[k], ws2, xc, xn, ra, carry);
 #pragma unroll
       for (int a = 0; a < NB; ++a) { r[a] = r[a] + ra[a]; xc[a] = xn[a]; }
     }
 #pragma unroll
-    for (int a = 0; a < NB; ++a) r_out[a * es + k] = Num<N>::to_f(r[a]);
+    for (int a = 0; a < NB; ++a) v[a] = Num<N>::to_f(r[a]);
   }
+};
+
+// Level-0 replay of the stored FP32 factor on the refinement residual (fused, see above).
+template <class N, int NB, bool kTop>
+__global__ void __launch_bounds__(kThreads) k_elim0_res(LevelTables lt, LevelBufs<float, NB> lb,
+                                                        Problem0 p, L0In<float> in, const float* x_hi,
+                                                        const float* x_lo, const float* rhs) {
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= lt.G) return;
+  const ChunkPos cp = chunk_pos(lt, g);
+  ResidualSource<N, NB> src;
+  src.cs = make_coef<float, NB>(p, in, nullptr, cp.i, g, cp.first, cp.T, lt.L, lt.G);
+  src.xh = x_hi;
+  src.xl = x_lo;
+  src.rhs = rhs;
+  src.u = src.cs.u;
+  src.wg2 = Num<N>::from_d(p.wg2);
+  src.wi2 = Num<N>::from_d(p.wi2);
+  src.ws2 = Num<N>::from_d(p.ws2);
+  src.last = cp.last;
+  src.init();
+  elim_chunk<float, NB, false>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
+  if (kTop) solve_top<float, NB>(lb.out, g, lb.xsep + g * NB);
 }
 
 // ---- parameter gradients ----------------------------------------------------------------
@@ -665,6 +693,7 @@ struct smnn_plan_s {
   int64_t Q = 0;
   std::vector<Level> lv;
   size_t factor_bytes = 0, solve_bytes = 0;
+  size_t o_fyl = 0;                    // factor region: low part of the refined y (FP32 paths)
   size_t o_nrm = 0;                    // solve region (bytes), and the level-0 interleaved arrays:
   size_t o_c = 0, o_d = 0, o_s = 0;    //   staged inputs
   size_t o_r = 0, o_gy = 0;            //   residual / explicit rhs, staged dl/dy
@@ -759,6 +788,8 @@ smnn_status build_plan(smnn_plan_s* pl) {
   {
     const Level& L0 = pl->lv[0];
     const size_t GL = size_t(L0.G) * size_t(L0.L);
+    pl->o_fyl = f;
+    if (es == 4) f += align_up(GL * NB * 4);
     auto take = [&](size_t bytes) { const size_t o = s; s += align_up(bytes); return o; };
     pl->o_c = take(GL * NB * es);
     pl->o_d = take(GL * es);
@@ -877,10 +908,16 @@ L0In<Tr> l0_in(const smnn_plan_s* pl, char* sol) {
 
 // One pass of the chunked solve: eliminate level by level (factor, or replay the stored
 // factor on a new right-hand side), then back substitute; level-0 output per `out`/`mode`.
-template <class Tr, int NB>
+struct ResIn {  // refinement sweep: residual of x (float-float) against rhs (or beta)
+  const float* xh;
+  const float* xl;
+  const float* rhs;
+};
+
+template <class Tr, int NB, class N = double>
 smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, bool factor,
                        char* fac, char* sol, const Level0Out<Tr>& out, int mode, int32_t* info,
-                       cudaStream_t st) {
+                       cudaStream_t st, const ResIn* res = nullptr) {
   const int nl = int(pl->lv.size());
   const L0In<Tr> in = l0_in<Tr>(pl, sol);
   for (int l = 0; l < nl; ++l) {
@@ -888,6 +925,13 @@ smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, 
     const LevelTables lt = tables_of(L);
     const LevelBufs<Tr, NB> lb = bufs_of<Tr, NB>(L, fac, sol);
     const bool top = l == nl - 1;
+    if constexpr (std::is_same<Tr, float>::value) {
+      if (l == 0 && res) {
+        if (top) SMNN_LAUNCH((k_elim0_res<N, NB, true>), L.G, st, lt, lb, p, in, res->xh, res->xl, res->rhs);
+        else SMNN_LAUNCH((k_elim0_res<N, NB, false>), L.G, st, lt, lb, p, in, res->xh, res->xl, res->rhs);
+        continue;
+      }
+    }
     if (l == 0) {
       if (factor && top) SMNN_LAUNCH((k_elim0<Tr, NB, true, true>), L.G, st, lt, lb, p, in, rhs, info);
       else if (factor) SMNN_LAUNCH((k_elim0<Tr, NB, true, false>), L.G, st, lt, lb, p, in, rhs, info);
@@ -945,55 +989,58 @@ smnn_status gather_inputs(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
   return SMNN_OK;
 }
 
-template <class N, int NB>
-smnn_status residual(const smnn_plan_s* pl, const Problem0& p, const L0Bufs<float>& b,
-                     const float* xh, const float* xl, const float* rhs, cudaStream_t st) {
-  const L0In<float> in{b.c, b.d, b.s};
-  SMNN_LAUNCH((k_residual<N, NB>), pl->lv[0].G, st, tables_of(pl->lv[0]), p, in, xh, xl, rhs, b.r);
-  return SMNN_OK;
-}
-
 #define SMNN_TRY(x) do { const smnn_status rc_ = (x); if (rc_ != SMNN_OK) return rc_; } while (0)
 
 // Forward solve with refinement in number type N (double: FP64 residual; ff: float-float).
+// The accumulator's low part lives in the factor region so that smnn_backward, given the same
+// factor buffer, starts from the refined y without refining it again.
 template <class N, int NB>
 smnn_status refine_forward(const smnn_plan_s* pl, const Problem0& p, char* fac, char* sol,
                            int32_t* info, cudaStream_t st) {
   const L0Bufs<float> b = l0_bufs<float>(pl, sol);
+  float* yl = reinterpret_cast<float*>(fac + pl->o_fyl);
   const int K = pl->desc.max_refine;
   const bool check = pl->desc.refine_tol > 0;
-  Level0Out<float> o{nullptr, b.yh, b.yl, nullptr};
+  Level0Out<float> o{nullptr, b.yh, yl, nullptr};
   SMNN_TRY((solve_pass<float, NB>(pl, p, nullptr, true, fac, sol, o, 1, info, st)));
   for (int it = 0; it < K; ++it) {
     const bool last = it + 1 == K;
     if (check && last) SMNN_LAUNCH(k_fill_f64, 2 * pl->S, st, b.nrm, 2 * pl->S, 0.0);
-    SMNN_TRY((residual<N, NB>(pl, p, b, b.yh, b.yl, nullptr, st)));
-    Level0Out<float> oa{nullptr, b.yh, b.yl, check && last ? b.nrm : nullptr};
-    SMNN_TRY((solve_pass<float, NB>(pl, p, b.r, false, fac, sol, oa, 2, info, st)));
+    const ResIn ri{b.yh, yl, nullptr};
+    Level0Out<float> oa{nullptr, b.yh, yl, check && last ? b.nrm : nullptr};
+    SMNN_TRY((solve_pass<float, NB, N>(pl, p, nullptr, false, fac, sol, oa, 2, info, st, &ri)));
   }
   if (check && K > 0) SMNN_LAUNCH(k_refine_check, pl->S, st, b.nrm, pl->S, pl->desc.refine_tol, info);
   return SMNN_OK;
 }
 
-// Adjoint: g = M^{-1} gy refined KA times, y re-refined once from the caller's FP32 y (both
-// kept as float-float), then the fused gradients in number type N.
+// Adjoint: g = M^{-1} gy refined KA times (float-float accumulator).  y: with a saved factor
+// the forward's float-float y is reused (its low part was kept in the factor region);
+// otherwise y is refined once from the caller's FP32 y.  Returns the y pair used.
 template <class N, int NB>
 smnn_status refine_backward(const smnn_plan_s* pl, const Problem0& p, char* fac, char* sol,
-                            bool factor, const float* y, int32_t* info, cudaStream_t st) {
+                            bool recompute, const float* y, int32_t* info, cudaStream_t st,
+                            const float** y_lo_used) {
   const L0Bufs<float> b = l0_bufs<float>(pl, sol);
   const int KA = pl->desc.precision == SMNN_F32 ? 0 : pl->desc.adjoint_refine;
   Level0Out<float> og{nullptr, b.gh, b.gl, nullptr};
-  SMNN_TRY((solve_pass<float, NB>(pl, p, b.gy, factor, fac, sol, og, 1, info, st)));
+  SMNN_TRY((solve_pass<float, NB>(pl, p, b.gy, recompute, fac, sol, og, 1, info, st)));
   SMNN_TRY((gather_inputs<float, NB>(pl, p, b, y, b.yh, b.yl, false, st)));
+  *y_lo_used = nullptr;
   if (KA > 0) {
-    SMNN_TRY((residual<N, NB>(pl, p, b, b.yh, nullptr, nullptr, st)));
-    Level0Out<float> oy{nullptr, b.yh, b.yl, nullptr};
-    SMNN_TRY((solve_pass<float, NB>(pl, p, b.r, false, fac, sol, oy, 2, info, st)));
+    if (!recompute && pl->desc.max_refine > 0) {
+      *y_lo_used = reinterpret_cast<const float*>(fac + pl->o_fyl);
+    } else {
+      const ResIn ri{b.yh, nullptr, nullptr};
+      Level0Out<float> oy{nullptr, b.yh, b.yl, nullptr};
+      SMNN_TRY((solve_pass<float, NB, N>(pl, p, nullptr, false, fac, sol, oy, 2, info, st, &ri)));
+      *y_lo_used = b.yl;
+    }
   }
   for (int it = 0; it < KA; ++it) {
-    SMNN_TRY((residual<N, NB>(pl, p, b, b.gh, b.gl, b.gy, st)));
+    const ResIn ri{b.gh, b.gl, b.gy};
     Level0Out<float> oa{nullptr, b.gh, b.gl, nullptr};
-    SMNN_TRY((solve_pass<float, NB>(pl, p, b.r, false, fac, sol, oa, 2, info, st)));
+    SMNN_TRY((solve_pass<float, NB, N>(pl, p, nullptr, false, fac, sol, oa, 2, info, st, &ri)));
   }
   return SMNN_OK;
 }
@@ -1055,12 +1102,13 @@ smnn_status backward_t(const smnn_plan_s* pl, const void* c, const void* d, cons
   Tr* guo = static_cast<Tr*>(gu);
   if constexpr (std::is_same<Tr, float>::value) {
     const float* y32 = static_cast<const float*>(y);
+    const float* yl = nullptr;
     if (pl->desc.precision == SMNN_F32_REFINED_DF) {
-      SMNN_TRY((refine_backward<ff, NB>(pl, p, fac, sol, factor == nullptr, y32, info, st)));
-      return gradients_out<float, ff, NB>(pl, p, b, b.yh, b.yl, b.gh, b.gl, info, gco, gdo, gso, guo, st);
+      SMNN_TRY((refine_backward<ff, NB>(pl, p, fac, sol, factor == nullptr, y32, info, st, &yl)));
+      return gradients_out<float, ff, NB>(pl, p, b, b.yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, st);
     }
-    SMNN_TRY((refine_backward<double, NB>(pl, p, fac, sol, factor == nullptr, y32, info, st)));
-    return gradients_out<float, double, NB>(pl, p, b, b.yh, b.yl, b.gh, b.gl, info, gco, gdo, gso, guo, st);
+    SMNN_TRY((refine_backward<double, NB>(pl, p, fac, sol, factor == nullptr, y32, info, st, &yl)));
+    return gradients_out<float, double, NB>(pl, p, b, b.yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, st);
   } else {
     Level0Out<Tr> o{b.g, nullptr, nullptr, nullptr};
     SMNN_TRY((solve_pass<Tr, NB>(pl, p, b.gy, factor == nullptr, fac, sol, o, 0, info, st)));

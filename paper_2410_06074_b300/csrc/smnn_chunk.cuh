@@ -353,9 +353,10 @@ struct ReducedSource {
 
 // Eliminate the interior of chunk g (steps first..last-1, separator last).  kFactor: compute
 // and store L_t, H_t and the separator's reduced blocks; otherwise read the stored factor and
-// only carry the right-hand side.  Returns 0, or 1 + the step index of the first bad pivot.
+// only carry the right-hand side.  src.b is called for first, first+1, ..., last in order.
+// Returns 0, or 1 + the step index of the first bad pivot.
 template <class Tr, int NB, bool kFactor, class Src>
-SMNN_HD int64_t elim_chunk(const Src& src, int64_t first, int64_t last, bool has_left,
+SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
                            const FactorView<Tr, NB>& fac, int64_t g, const ChunkOut<Tr, NB>& out) {
   constexpr int NT = NB * (NB + 1) / 2;
   int64_t fail = 0;
