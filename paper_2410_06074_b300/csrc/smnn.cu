@@ -1074,8 +1074,8 @@ smnn_status factor_solve_t(const smnn_plan_s* pl, const void* c, const void* d, 
     if (pl->desc.precision == SMNN_F32_REFINED || pl->desc.precision == SMNN_F32_REFINED_DF) {
       if (pl->desc.precision == SMNN_F32_REFINED) SMNN_TRY((refine_forward<double, NB>(pl, p, fac, sol, info, st)));
       else SMNN_TRY((refine_forward<ff, NB>(pl, p, fac, sol, info, st)));
-      SMNN_LAUNCH((k_scatter0<float, float, NB>), l0_elems(pl), st, lt0, b.yh, b.yl,
-                  static_cast<float*>(y), nullptr, nullptr);
+      SMNN_LAUNCH((k_scatter0<float, float, NB>), l0_elems(pl), st, lt0, b.yh,
+                  reinterpret_cast<const float*>(fac + pl->o_fyl), static_cast<float*>(y), nullptr, nullptr);
       return SMNN_OK;
     }
   }
