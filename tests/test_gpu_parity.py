@@ -209,14 +209,18 @@ def test_gradients_refined_fp32_match_oracle(T, chunk, prec):
 
 
 @pytest.mark.parametrize("prec", REFINED)
-def test_saved_and_recomputed_factor_give_identical_gradients(prec):
+def test_saved_and_recomputed_factor_agree(prec):
+    """With the saved factor the backward reuses the forward's refined y; without it the
+    factor is recomputed and y refined again.  Both must meet the refined tolerance."""
     pk = P()
     prob = random_problem(18, 2, 2, 900, 2)
     gy = upstream_gradient(prob).astype(np.float32)
     a = gpu_grad(prob, gy, getattr(pk, prec), store_factor=True)
     b = gpu_grad(prob, gy, getattr(pk, prec), store_factor=False)
-    for x, z in zip(a[:5], b[:5]):
-        np.testing.assert_array_equal(x, z)
+    ref = oracle_grad(rounded(prob, pk.F32_REFINED), gy.astype(np.float64))
+    for x, z, r in zip(a[:5], b[:5], ref[:5]):
+        assert rel_err(x, r) <= TOL_REF and rel_err(z, r) <= TOL_REF
+        assert rel_err(x, z) <= TOL_REF
 
 
 def test_gradcheck_config2_slice():
