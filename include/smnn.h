@@ -56,7 +56,8 @@ typedef enum {
   SMNN_ERR_INVALID_ARG = 1,   /* a pointer, size or parameter is out of range      */
   SMNN_ERR_WORKSPACE = 2,     /* workspace/factor buffer missing or misaligned     */
   SMNN_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed       */
-  SMNN_ERR_UNSUPPORTED = 4    /* valid request the library does not implement     */
+  SMNN_ERR_UNSUPPORTED = 4,   /* valid request the library does not implement     */
+  SMNN_ERR_TOO_LARGE = 5      /* exceeds the static scratch of smnn_factor_solve_noalloc */
 } smnn_status;
 
 typedef enum {
@@ -182,6 +183,34 @@ typedef struct smnn_kernel_time {
 /* Synchronise on the recorded events and aggregate them by kernel name into out[0..n),
  * at most max entries; *n receives the number of distinct kernels. */
 smnn_status smnn_profile_read(smnn_kernel_time* out, int max, int* n);
+
+/* Forward solve without any device allocation.  The paper has no counterpart: this entry
+ * point is for callers that may not allocate device memory at all -- code that runs
+ * under an allocator that owns every device byte (a framework's caching pool, an
+ * embedding application), code on a path where cudaMalloc's implicit synchronisation or
+ * possible failure is not acceptable (latency-critical or real-time loops), and code that
+ * cannot keep a plan alive between calls.  It computes what smnn_plan_create followed by
+ * smnn_factor_solve (with factor = NULL) computes for the same desc and inputs, but takes
+ * no plan and no workspace: the plan's index tables and the workspace are placed in one
+ * library-owned static device array of SMNN_NOALLOC_SCRATCH_BYTES (64 MiB) per device,
+ * held by every GPU that loads the library until the process exits.
+ *   - Requests whose tables plus workspace exceed that size return SMNN_ERR_TOO_LARGE and
+ *     launch nothing (smnn_workspace_size of an equivalent plan tells the need).
+ *   - The call allocates no device memory (no cudaMalloc, cudaFree or allocating library
+ *     routine); it uses host memory for the plan's bookkeeping and copies the index tables
+ *     to the device with cudaMemcpyAsync on `stream`.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (once per device, with that device current); make that first
+ *     call before any stream capture.
+ *   - All calls on a device share the one array, which keeps the previous call's contents;
+ *     everything the solve reads is written earlier in the same call (info is cleared by
+ *     the call itself).  Calls that overlap on the GPU -- on different streams, or from
+ *     different host threads without ordering -- race on the array and give wrong results.
+ * Arguments, layouts and info as smnn_factor_solve; desc as smnn_plan_create. */
+#define SMNN_NOALLOC_SCRATCH_BYTES (64u << 20)
+smnn_status smnn_factor_solve_noalloc(const smnn_desc* desc, const void* c, const void* d,
+                                      const void* s, const void* u, void* y, int32_t* info,
+                                      void* stream);
 
 /* Static string for a status code. */
 const char* smnn_status_string(smnn_status status);

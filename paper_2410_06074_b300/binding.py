@@ -16,7 +16,8 @@ from . import _build
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
-SMNN_OK, SMNN_ERR_INVALID_ARG, SMNN_ERR_WORKSPACE, SMNN_ERR_CUDA, SMNN_ERR_UNSUPPORTED = range(5)
+(SMNN_OK, SMNN_ERR_INVALID_ARG, SMNN_ERR_WORKSPACE, SMNN_ERR_CUDA, SMNN_ERR_UNSUPPORTED,
+ SMNN_ERR_TOO_LARGE) = range(6)
 F32_REFINED, F32, F64, F32_REFINED_DF = 0, 1, 2, 3
 ALGO_AUTO, ALGO_SEQ, ALGO_CR = 0, 1, 2
 SMNN_MAX_R = 3
@@ -67,6 +68,7 @@ SYMBOLS = {
     "smnn_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "smnn_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelTime), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
+    "smnn_factor_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(Desc)] + [_VP] * 7),
 }
 
 

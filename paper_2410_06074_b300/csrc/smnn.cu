@@ -18,6 +18,8 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <mutex>
 #include <new>
 #include <type_traits>
 #include <vector>
@@ -701,6 +703,8 @@ struct smnn_plan_s {
   size_t o_yh = 0, o_yl = 0, o_gh = 0, o_gl = 0;  // float-float accumulators (FP32 paths)
   size_t o_gc = 0, o_gd = 0, o_gs = 0; //   gradients before the scatter
   void* tables = nullptr;              // one device allocation for every index table
+  std::vector<char> table_blob;        // the tables, packed on the host
+  std::vector<std::function<void(char*)>> table_binds;  // set the device pointers for a base
 };
 
 namespace {
@@ -742,7 +746,7 @@ std::vector<int> plan_levels(const smnn_desc& d, const std::vector<int64_t>& T, 
   return Ls;
 }
 
-smnn_status build_plan(smnn_plan_s* pl) {
+smnn_status build_plan_host(smnn_plan_s* pl) {
   const smnn_desc& d = pl->desc;
   const int NB = pl->NB;
   const int NT = NB * (NB + 1) / 2;
@@ -822,18 +826,18 @@ smnn_status build_plan(smnn_plan_s* pl) {
   s += align_up(size_t(pl->lv[0].G) * size_t(L0) * es);
   pl->solve_bytes = s;
 
-  size_t tb = 0;  // one device allocation for every table
+  size_t tb = 0;  // every index table, packed into one blob (one device allocation)
   for (auto& L : pl->lv) tb += align_up(L.G * 4) + align_up((S + 1) * 8) + 2 * align_up(S * 8);
   tb += 3 * align_up(S * 8) + 2 * align_up(pl->B * 8) + 2 * align_up(pl->Q * 4);
-  if (cudaMalloc(&pl->tables, tb) != cudaSuccess) { pl->tables = nullptr; return SMNN_ERR_CUDA; }
-  std::vector<char> host(tb, 0);
-  char* hp = host.data();
-  char* dp = static_cast<char*>(pl->tables);
+  pl->table_blob.assign(tb, 0);
+  pl->table_binds.clear();
+  size_t off = 0;
   auto put = [&](const void* src, size_t n, auto** dst) {
-    if (n) std::memcpy(hp, src, n);
-    *dst = reinterpret_cast<std::remove_pointer_t<decltype(dst)>>(dp);
-    hp += align_up(n);
-    dp += align_up(n);
+    if (n) std::memcpy(pl->table_blob.data() + off, src, n);
+    using Ptr = std::remove_pointer_t<decltype(dst)>;
+    const size_t at = off;
+    pl->table_binds.push_back([dst, at](char* base) { *dst = reinterpret_cast<Ptr>(base + at); });
+    off += align_up(n);
   };
   for (auto& L : pl->lv) {
     put(L.csys.data(), L.G * 4, &L.d_csys);
@@ -848,8 +852,12 @@ smnn_status build_plan(smnn_plan_s* pl) {
   put(pl->seq_T.data(), pl->B * 8, &pl->d_seq_T);
   put(sq_b.data(), pl->Q * 4, &pl->d_sq_b);
   put(sq_k.data(), pl->Q * 4, &pl->d_sq_k);
-  if (cudaMemcpy(pl->tables, host.data(), tb, cudaMemcpyHostToDevice) != cudaSuccess) return SMNN_ERR_CUDA;
   return SMNN_OK;
+}
+
+// Point the plan's device table pointers into `base`, where the blob is (or will be) copied.
+void bind_tables(smnn_plan_s* pl, char* base) {
+  for (auto& b : pl->table_binds) b(base);
 }
 
 // ----------------------------------------------------------------------------- dispatch
@@ -1161,11 +1169,11 @@ struct DeviceGuard {  // run on the plan's device, restore the caller's afterwar
 
 // ----------------------------------------------------------------------------- C ABI
 
-extern "C" {
 
-smnn_status smnn_plan_create(const smnn_desc* desc, smnn_plan* plan) {
-  if (!desc || !plan) return SMNN_ERR_INVALID_ARG;
-  *plan = nullptr;
+namespace {
+// Validate desc and fill a host-side plan (sizes, level structure, table blob); no device work.
+smnn_status plan_init(const smnn_desc* desc, smnn_plan_s* pl) {
+  if (!desc) return SMNN_ERR_INVALID_ARG;
   const smnn_desc& d = *desc;
   if (d.R < 1 || d.R > SMNN_MAX_R || d.R_init < 0 || d.R_init > d.R || d.T_init < 1) return SMNN_ERR_INVALID_ARG;
   if (d.precision < SMNN_F32_REFINED || d.precision > SMNN_F32_REFINED_DF) return SMNN_ERR_INVALID_ARG;
@@ -1178,8 +1186,6 @@ smnn_status smnn_plan_create(const smnn_desc* desc, smnn_plan* plan) {
     return SMNN_ERR_INVALID_ARG;
   if (d.num_seq > INT32_MAX || d.num_seq * d.dims_per_seq > INT32_MAX) return SMNN_ERR_INVALID_ARG;
   if (!d.seq_T && (d.T < 1 || d.T < d.T_init)) return SMNN_ERR_INVALID_ARG;
-  smnn_plan_s* pl = new (std::nothrow) smnn_plan_s();
-  if (!pl) return SMNN_ERR_INVALID_ARG;
   pl->desc = d;
   pl->desc.seq_T = nullptr;
   pl->NB = d.R + 1;
@@ -1189,12 +1195,8 @@ smnn_status smnn_plan_create(const smnn_desc* desc, smnn_plan* plan) {
   pl->S = pl->B * pl->D;
   pl->seq_T.resize(pl->B);
   for (int64_t b = 0; b < pl->B; ++b) pl->seq_T[b] = d.seq_T ? d.seq_T[b] : d.T;
-  for (int64_t b = 0; b < pl->B; ++b) {
-    if (pl->seq_T[b] < 1 || pl->seq_T[b] < d.T_init || pl->seq_T[b] > (int64_t(1) << 31)) {
-      delete pl;
-      return SMNN_ERR_INVALID_ARG;
-    }
-  }
+  for (int64_t b = 0; b < pl->B; ++b)
+    if (pl->seq_T[b] < 1 || pl->seq_T[b] < d.T_init || pl->seq_T[b] > (int64_t(1) << 31)) return SMNN_ERR_INVALID_ARG;
   pl->seq_soff.resize(pl->B);
   int64_t so = 0;
   for (int64_t b = 0; b < pl->B; ++b) { pl->seq_soff[b] = so; so += pl->seq_T[b]; }
@@ -1207,8 +1209,29 @@ smnn_status smnn_plan_create(const smnn_desc* desc, smnn_plan* plan) {
       pl->sys_soff[i] = pl->seq_soff[b];
     }
   pl->N0 = pl->D * so;
-  if (cudaGetDevice(&pl->device) != cudaSuccess) { delete pl; return SMNN_ERR_CUDA; }
-  const smnn_status rc = build_plan(pl);
+  return build_plan_host(pl);
+}
+}  // namespace
+
+extern "C" {
+
+smnn_status smnn_plan_create(const smnn_desc* desc, smnn_plan* plan) {
+  if (!desc || !plan) return SMNN_ERR_INVALID_ARG;
+  *plan = nullptr;
+  smnn_plan_s* pl = new (std::nothrow) smnn_plan_s();
+  if (!pl) return SMNN_ERR_INVALID_ARG;
+  smnn_status rc = plan_init(desc, pl);
+  if (rc == SMNN_OK && cudaGetDevice(&pl->device) != cudaSuccess) rc = SMNN_ERR_CUDA;
+  if (rc == SMNN_OK) {
+    if (cudaMalloc(&pl->tables, pl->table_blob.size()) != cudaSuccess) {
+      pl->tables = nullptr;
+      rc = SMNN_ERR_CUDA;
+    } else {
+      bind_tables(pl, static_cast<char*>(pl->tables));
+      if (cudaMemcpy(pl->tables, pl->table_blob.data(), pl->table_blob.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = SMNN_ERR_CUDA;
+    }
+  }
   if (rc != SMNN_OK) {
     if (pl->tables) cudaFree(pl->tables);
     delete pl;
@@ -1290,6 +1313,8 @@ const char* smnn_status_string(smnn_status status) {
     case SMNN_ERR_WORKSPACE: return "SMNN_ERR_WORKSPACE: workspace missing or misaligned";
     case SMNN_ERR_CUDA: return "SMNN_ERR_CUDA: CUDA runtime error";
     case SMNN_ERR_UNSUPPORTED: return "SMNN_ERR_UNSUPPORTED: unsupported request";
+    case SMNN_ERR_TOO_LARGE:
+      return "SMNN_ERR_TOO_LARGE: the problem needs more than the static scratch of smnn_factor_solve_noalloc";
   }
   return "unknown smnn_status";
 }
@@ -1344,3 +1369,52 @@ smnn_status smnn_profile_read(smnn_kernel_time* out, int max, int* n) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------- no-allocation entry
+
+// Scratch of smnn_factor_solve_noalloc: index tables and workspace of one call.  Every GPU
+// that loads the library holds these SMNN_NOALLOC_SCRATCH_BYTES until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SMNN_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoAllocDevices = 128;
+std::mutex g_noalloc_mu;
+char* g_noalloc_base[kNoAllocDevices] = {};  // device address of g_noalloc_scratch, per device
+
+// Device address of the scratch on the current device.  The host-side name of the array is
+// only a stand-in: the address comes from cudaGetSymbolAddress, once per device, with that
+// device current.
+smnn_status noalloc_base(int dev, char** base) {
+  if (dev < 0 || dev >= kNoAllocDevices) return SMNN_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_base[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return SMNN_ERR_CUDA;
+    g_noalloc_base[dev] = static_cast<char*>(ptr);
+  }
+  *base = g_noalloc_base[dev];
+  return SMNN_OK;
+}
+}  // namespace
+
+extern "C" smnn_status smnn_factor_solve_noalloc(const smnn_desc* desc, const void* c, const void* d,
+                                                 const void* s, const void* u, void* y, int32_t* info,
+                                                 void* stream) {
+  if (!desc || !c || !d || !s || !u || !y || !info) return SMNN_ERR_INVALID_ARG;
+  smnn_plan_s pl;                       // host-side plan; its device tables live in the scratch
+  smnn_status rc = plan_init(desc, &pl);
+  if (rc != SMNN_OK) return rc;
+  const size_t tables = align_up(pl.table_blob.size());
+  if (tables + pl.factor_bytes + pl.solve_bytes > size_t(SMNN_NOALLOC_SCRATCH_BYTES)) return SMNN_ERR_TOO_LARGE;
+  if (cudaGetDevice(&pl.device) != cudaSuccess) return SMNN_ERR_CUDA;
+  char* base = nullptr;
+  rc = noalloc_base(pl.device, &base);
+  if (rc != SMNN_OK) return rc;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  bind_tables(&pl, base);
+  // pageable host -> device: returns once the blob has been staged, so pl may go out of scope
+  if (cudaMemcpyAsync(base, pl.table_blob.data(), pl.table_blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return SMNN_ERR_CUDA;
+  void* ws = base + tables;
+  SMNN_DISPATCH((&pl), factor_solve_t, &pl, c, d, s, u, y, nullptr, info, ws, st);
+}
