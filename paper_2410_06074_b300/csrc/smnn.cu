@@ -262,7 +262,9 @@ __global__ void __launch_bounds__(kThreads) k_elimN(LevelTables lt, LevelBufs<Tr
 template <class Tr, int NB>
 struct EmitX {
   Tr* x;
-  __device__ void operator()(int64_t t, const Tr (&v)[NB]) const {
+  struct Pre {};
+  __device__ Pre fetch(int64_t) const { return Pre{}; }
+  __device__ void operator()(int64_t t, const Tr (&v)[NB], const Pre&) const {
 #pragma unroll
     for (int a = 0; a < NB; ++a) x[t * NB + a] = v[a];
   }
@@ -298,7 +300,23 @@ struct EmitY {
   int L;
   bool failed;
   double dd, yy;
-  __device__ void operator()(int64_t t, const Tr (&v)[NB]) {
+  struct Pre {  // the accumulator of step t (mode 2), loaded ahead of its update
+    float hi[NB], lo[NB];
+  };
+  __device__ Pre fetch(int64_t t) const {
+    Pre p;
+    if (kMode == 2) {
+      const int64_t es = int64_t(L) * G;
+      const int64_t n = (t - first) * G + g;
+#pragma unroll
+      for (int a = 0; a < NB; ++a) {
+        p.hi[a] = o.acc_hi[a * es + n];
+        p.lo[a] = o.acc_lo[a * es + n];
+      }
+    }
+    return p;
+  }
+  __device__ void operator()(int64_t t, const Tr (&v)[NB], const Pre& pre) {
     const int64_t es = int64_t(L) * G;
     const int64_t n = (t - first) * G + g;
 #pragma unroll
@@ -306,7 +324,7 @@ struct EmitY {
       if (kMode == 0) {
         o.x[a * es + n] = failed ? nan_t<Tr>() : v[a];
       } else {
-        ff acc = kMode == 2 ? ff{o.acc_hi[a * es + n], o.acc_lo[a * es + n]} : ff{0.f, 0.f};
+        ff acc = kMode == 2 ? ff{pre.hi[a], pre.lo[a]} : ff{0.f, 0.f};
         acc = acc + float(v[a]);
         if (failed) acc = ff{nan_t<float>(), nan_t<float>()};
         o.acc_hi[a * es + n] = acc.hi;
@@ -435,6 +453,24 @@ struct ResidualSource {
 #pragma unroll
     for (int a = 0; a < NB; ++a) v[a] = Num<N>::pair(xh[a * es + k], xl ? xl[a * es + k] : 0.f);
   }
+  // raw inputs of the next step, loaded one call ahead
+  float pc[NB], prh[NB], pd, ps;
+  N px[NB];
+
+  __device__ void prefetch(int64_t t) {
+    const int64_t k = (t - cs.first) * cs.G + cs.g, es = cs.es();
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      pc[a] = cs.c[a * es + k];
+      prh[a] = rhs ? rhs[a * es + k] : 0.f;
+    }
+    pd = cs.d[k];
+    if (t + 1 < cs.T) {
+      ps = cs.s[k];
+      load(t + 1, px);
+    }
+  }
+
   __device__ void init() {
     load(cs.first, xc);
 #pragma unroll
@@ -444,25 +480,30 @@ struct ResidualSource {
       load(cs.first - 1, xp);
       smooth_pair_residual<N, NB>(cs.s[idx(cs.first - 1)], ws2, xp, xc, dummy, carry);
     }
+    prefetch(cs.first);
   }
+  using ERaw = typename CoefSource<float, NB>::ERaw;
+  __device__ ERaw load_e(int64_t t) const { return cs.load_e(t); }
+  __device__ void e_from(ERaw r, float (&e)[NB][NB]) const { cs.e_from(r, e); }
   __device__ void A(int64_t t, float (&a)[NB][NB]) const { cs.A(t, a); }
   __device__ void E(int64_t t, float (&e)[NB][NB]) const { cs.E(t, e); }
   __device__ void b(int64_t t, float (&v)[NB]) {
-    const int64_t k = (t - cs.first) * cs.G + cs.g, es = cs.es();
+    float cv[NB], rh[NB];
+    N xn[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) { cv[a] = pc[a]; rh[a] = prh[a]; xn[a] = px[a]; }
+    const float dt = pd, st = ps;
+    if (t + 1 <= last) prefetch(t + 1);
     N r[NB];
-    float cv[NB];
     N cx = Num<N>::zero();
 #pragma unroll
-    for (int a = 0; a < NB; ++a) {
-      cv[a] = cs.c[a * es + k];
-      cx = cx + xc[a] * cv[a];
-    }
+    for (int a = 0; a < NB; ++a) cx = cx + xc[a] * cv[a];
     if (rhs) {
       const N gres = -(wg2 * cx);
 #pragma unroll
-      for (int a = 0; a < NB; ++a) r[a] = (gres * cv[a] + rhs[a * es + k]) + carry[a];
+      for (int a = 0; a < NB; ++a) r[a] = (gres * cv[a] + rh[a]) + carry[a];
     } else {
-      const N gres = wg2 * (cx - cs.d[k]);
+      const N gres = wg2 * (cx - dt);
 #pragma unroll
       for (int a = 0; a < NB; ++a) r[a] = carry[a] - gres * cv[a];
     }
@@ -475,9 +516,8 @@ struct ResidualSource {
         }
     }
     if (t + 1 < cs.T) {
-      N xn[NB], ra[NB];
-      load(t + 1, xn);
-      smooth_pair_residual<N, NB>(cs.s[k], ws2, xc, xn, ra, carry);
+      N ra[NB];
+      smooth_pair_residual<N, NB>(st, ws2, xc, xn, ra, carry);
 #pragma unroll
       for (int a = 0; a < NB; ++a) { r[a] = r[a] + ra[a]; xc[a] = xn[a]; }
     }

@@ -207,6 +207,39 @@ struct FactorView {
 #pragma unroll
     for (int a = 0; a < NB; ++a) v[a] = z[at(a, j, g)];
   }
+
+  // Raw stored data of one step, loaded ahead of its use by the pipelined sweeps.
+  struct Raw {
+    Tr l[NB * (NB + 1) / 2];
+    Tr h[NB * NB];
+    Tr z[NB];
+  };
+  SMNN_HD void load_raw(int j, int64_t g, Raw& r, bool with_h, bool with_z) const {
+#pragma unroll
+    for (int e = 0; e < NB * (NB + 1) / 2; ++e) r.l[e] = lf[at(e, j, g)];
+    if (with_h) {
+#pragma unroll
+      for (int e = 0; e < NB * NB; ++e) r.h[e] = h[at(e, j, g)];
+    }
+    if (with_z) {
+#pragma unroll
+      for (int e = 0; e < NB; ++e) r.z[e] = z[at(e, j, g)];
+    }
+  }
+  static SMNN_HD void unpack_l(const Raw& r, Tr (&l)[NB][NB], Tr (&inv)[NB]) {
+#pragma unroll
+    for (int a = 0; a < NB; ++a)
+#pragma unroll
+      for (int b = 0; b <= a; ++b) {
+        if (a == b) inv[a] = r.l[tri(a, b)]; else l[a][b] = r.l[tri(a, b)];
+      }
+  }
+  static SMNN_HD void unpack_h(const Raw& r, Tr (&m)[NB][NB]) {
+#pragma unroll
+    for (int a = 0; a < NB; ++a)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) m[a][b] = r.h[a * NB + b];
+  }
 };
 
 // Separator outputs of one chunk g (array of structs per chunk): the right part of the
@@ -298,9 +331,11 @@ struct CoefSource {
     }
   }
 
-  // E_t = N_t = block (t+1, t), t < T-1
-  SMNN_HD void E(int64_t t, Tr (&e)[NB][NB]) const {
-    const Tr st = s[at(t)];
+  // E_t = N_t = block (t+1, t), t < T-1; its raw data is the step size s_t
+  using ERaw = Tr;
+  SMNN_HD ERaw load_e(int64_t t) const { return s[at(t)]; }
+  SMNN_HD void E(int64_t t, Tr (&e)[NB][NB]) const { e_from(load_e(t), e); }
+  SMNN_HD void e_from(ERaw st, Tr (&e)[NB][NB]) const {
     Tr pw[2 * NB - 1];
     pw[0] = Tr(1);
 #pragma unroll
@@ -341,12 +376,22 @@ struct ReducedSource {
 #pragma unroll
     for (int i = 0; i < NB; ++i) v[i] = b_right[k * NB + i] + (nxt ? b_left[(k + 1) * NB + i] : Tr(0));
   }
-  SMNN_HD void E(int64_t k, Tr (&e)[NB][NB]) const {
+  struct ERaw {
+    Tr v[NB * NB];
+  };
+  SMNN_HD ERaw load_e(int64_t k) const {
+    ERaw r;
+#pragma unroll
+    for (int i = 0; i < NB * NB; ++i) r.v[i] = e_coup[(k + 1) * NB * NB + i];
+    return r;
+  }
+  SMNN_HD void e_from(const ERaw& r, Tr (&e)[NB][NB]) const {
 #pragma unroll
     for (int i = 0; i < NB; ++i)
 #pragma unroll
-      for (int j = 0; j < NB; ++j) e[i][j] = e_coup[(k + 1) * NB * NB + i * NB + j];
+      for (int j = 0; j < NB; ++j) e[i][j] = r.v[i * NB + j];
   }
+  SMNN_HD void E(int64_t k, Tr (&e)[NB][NB]) const { e_from(load_e(k), e); }
 };
 
 // ----------------------------------------------------------------------------- chunk sweeps
@@ -359,6 +404,8 @@ template <class Tr, int NB, bool kFactor, class Src>
 SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
                            const FactorView<Tr, NB>& fac, int64_t g, const ChunkOut<Tr, NB>& out) {
   constexpr int NT = NB * (NB + 1) / 2;
+  using Raw = typename FactorView<Tr, NB>::Raw;
+  using ERaw = typename Src::ERaw;
   int64_t fail = 0;
   Tr D[NB][NB], Gm[NB][NB], r[NB], Sl[NB][NB], bl[NB];
   src.b(first, r);
@@ -372,9 +419,23 @@ SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
     src.A(first, D);
     if (has_left) src.E(first - 1, Gm);
   }
+  // replay: the stored factor and the coupling of step t are loaded one step ahead
+  Raw cur;
+  ERaw ecur;
+  if (!kFactor && first < last) {
+    fac.load_raw(0, g, cur, has_left, false);
+    ecur = src.load_e(first);
+  }
   for (int64_t t = first; t < last; ++t) {
     const int j = int(t - first);
     Tr Lm[NB][NB], inv[NB];
+    Raw nxt;
+    ERaw enxt;
+    const bool more = !kFactor && t + 1 < last;
+    if (more) {
+      fac.load_raw(j + 1, g, nxt, has_left, false);
+      enxt = src.load_e(t + 1);
+    }
     if (kFactor) {
 #pragma unroll
       for (int a = 0; a < NB; ++a)
@@ -383,7 +444,7 @@ SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
       if (!chol<Tr, NB>(Lm, inv) && fail == 0) fail = t + 1;
       fac.store_l(j, g, Lm, inv);
     } else {
-      fac.load_l(j, g, Lm, inv);
+      FactorView<Tr, NB>::unpack_l(cur, Lm, inv);
     }
     Tr z[NB];
 #pragma unroll
@@ -405,7 +466,7 @@ SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
             Sl[a][b] -= acc;
           }
       } else {
-        fac.load_h(j, g, Hm);
+        FactorView<Tr, NB>::unpack_h(cur, Hm);
       }
 #pragma unroll
       for (int a = 0; a < NB; ++a) {
@@ -416,7 +477,8 @@ SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
       }
     }
     Tr E[NB][NB], X[NB][NB];
-    src.E(t, E);
+    if (kFactor) src.E(t, E);
+    else src.e_from(ecur, E);
     trsm_l_bt<Tr, NB>(Lm, inv, E, X);
     src.b(t + 1, r);
 #pragma unroll
@@ -453,6 +515,10 @@ SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
 #pragma unroll
           for (int b = 0; b < NB; ++b) Gm[a][b] = Gn[a][b];
       }
+    }
+    if (more) {
+      cur = nxt;
+      ecur = enxt;
     }
   }
   if (kFactor) {
@@ -499,24 +565,45 @@ SMNN_HD bool solve_top(const ChunkOut<Tr, NB>& out, int64_t g, Tr* x) {
 }
 
 // Back-substitute chunk g given its separators' values (x_left unused without a left
-// separator).  emit(t, x) receives every step of the chunk, separator included.
+// separator).  emit(t, x, emit.fetch(t)) receives every step of the chunk, separator
+// included; the stored data of step t-1 (and emit's prefetch) are loaded while step t is
+// computed.
 template <class Tr, int NB, class Src, class Emit>
 SMNN_HD void backsub_chunk(const Src& src, int64_t first, int64_t last, bool has_left,
                            const FactorView<Tr, NB>& fac, int64_t g, const Tr* x_right,
                            const Tr* x_left, Emit& emit) {
+  using Raw = typename FactorView<Tr, NB>::Raw;
+  using ERaw = typename Src::ERaw;
+  using Pre = typename Emit::Pre;
   Tr xn[NB], xl[NB];
 #pragma unroll
   for (int a = 0; a < NB; ++a) {
     xn[a] = x_right[a];
     xl[a] = has_left ? x_left[a] : Tr(0);
   }
-  emit(last, xn);
+  emit(last, xn, emit.fetch(last));
+  if (last <= first) return;
+  Raw cur;
+  ERaw ecur;
+  Pre pcur;
+  fac.load_raw(int(last - 1 - first), g, cur, has_left, true);
+  ecur = src.load_e(last - 1);
+  pcur = emit.fetch(last - 1);
   for (int64_t t = last - 1; t >= first; --t) {
-    const int j = int(t - first);
+    const bool more = t > first;
+    Raw nxt;
+    ERaw enxt;
+    Pre pnxt;
+    if (more) {
+      fac.load_raw(int(t - 1 - first), g, nxt, has_left, true);
+      enxt = src.load_e(t - 1);
+      pnxt = emit.fetch(t - 1);
+    }
     Tr Lm[NB][NB], inv[NB], v[NB], E[NB][NB], X[NB][NB];
-    fac.load_l(j, g, Lm, inv);
-    fac.load_z(j, g, v);
-    src.E(t, E);
+    FactorView<Tr, NB>::unpack_l(cur, Lm, inv);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) v[a] = cur.z[a];
+    src.e_from(ecur, E);
     trsm_l_bt<Tr, NB>(Lm, inv, E, X);
 #pragma unroll
     for (int a = 0; a < NB; ++a) {
@@ -527,7 +614,7 @@ SMNN_HD void backsub_chunk(const Src& src, int64_t first, int64_t last, bool has
     }
     if (has_left) {
       Tr Hm[NB][NB];
-      fac.load_h(j, g, Hm);
+      FactorView<Tr, NB>::unpack_h(cur, Hm);
 #pragma unroll
       for (int a = 0; a < NB; ++a) {
         Tr acc = Tr(0);
@@ -537,9 +624,14 @@ SMNN_HD void backsub_chunk(const Src& src, int64_t first, int64_t last, bool has
       }
     }
     trsv_lt<Tr, NB>(Lm, inv, v);
-    emit(t, v);
+    emit(t, v, pcur);
 #pragma unroll
     for (int a = 0; a < NB; ++a) xn[a] = v[a];
+    if (more) {
+      cur = nxt;
+      ecur = enxt;
+      pcur = pnxt;
+    }
   }
 }
 
