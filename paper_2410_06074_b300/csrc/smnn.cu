@@ -55,7 +55,7 @@ inline void prof_end(cudaStream_t st) {
 }
 
 constexpr int kThreads = 128;
-constexpr int kTopMax = 64;        // a level with at most this many steps per system is one chunk
+constexpr int kTopMax = 8;         // a level with at most this many steps per system is one chunk
 constexpr int kMaxLevels = 8;
 constexpr size_t kAlign = 256;
 
@@ -173,57 +173,80 @@ __global__ void k_fill_f64(double* p, int64_t n, double v) {
   if (i < n) p[i] = v;
 }
 
-// User layout -> level-0 interleaved layout.  One thread per (position j, chunk g); the
-// writes of a warp are contiguous.  vec: optional per-step vector of NB values (y or
-// dl/dy) gathered into vec_out (float-float pairs: vec_lo, if given, is zeroed).
-template <class Tr, int NB>
-__global__ void __launch_bounds__(kThreads) k_gather0(LevelTables lt, Problem0 p, Tr* c, Tr* d, Tr* s,
-                                                      const Tr* vec, Tr* vec_out, float* vec_lo) {
-  const int64_t n = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (n >= lt.G * lt.L) return;
-  const int64_t g = n % lt.G;
-  const int j = int(n / lt.G);
-  const int64_t es = int64_t(lt.L) * lt.G;
-  const ChunkPos cp = chunk_pos(lt, g);
-  const int64_t t = cp.first + j;
-  if (t > cp.last) return;
-  const int64_t at = lt.base[cp.i] + t;
-  if (c) {
-#pragma unroll
-    for (int e = 0; e < NB; ++e) c[e * es + n] = static_cast<const Tr*>(p.c)[at * NB + e];
-    d[n] = static_cast<const Tr*>(p.d)[at];
-    s[n] = static_cast<const Tr*>(p.s)[p.soff[cp.i] + t];
+// Tiled user <-> level-0 interleaved transposes for per-step arrays of K values.  A CTA
+// takes kTileChunks consecutive chunks; their steps are one contiguous range of the user
+// layout (systems are packed one after another), staged through shared memory with one
+// pad word per 32 against bank conflicts.
+constexpr int kTileChunks = 32;
+constexpr int kTileThreads = 256;
+
+__device__ __forceinline__ int pad32(int x) { return x + (x >> 5); }
+
+template <class Tr, class Ts, int K, bool kIn>
+__global__ void __launch_bounds__(kTileThreads) k_tile(LevelTables lt, const Ts* src, const float* src_lo,
+                                                       Tr* dst, float* dst_lo) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Tr* buf = reinterpret_cast<Tr*>(smem_raw);
+  __shared__ int64_t s_u[kTileChunks];    // user step of each chunk's first step
+  __shared__ int s_len[kTileChunks];      // steps in each chunk
+  const int64_t g0 = int64_t(blockIdx.x) * kTileChunks;
+  const int nch = int(min(int64_t(kTileChunks), lt.G - g0));
+  if (threadIdx.x < nch) {
+    const ChunkPos cp = chunk_pos(lt, g0 + threadIdx.x);
+    s_u[threadIdx.x] = lt.base[cp.i] + cp.first;
+    s_len[threadIdx.x] = int(cp.last - cp.first + 1);
   }
-  if (vec) {
-#pragma unroll
-    for (int e = 0; e < NB; ++e) {
-      vec_out[e * es + n] = vec[at * NB + e];
-      if (vec_lo) vec_lo[e * es + n] = 0.f;
+  __syncthreads();
+  const int64_t u0 = s_u[0];
+  const int64_t span = s_u[nch - 1] + s_len[nch - 1] - u0;   // contiguous user steps
+  const int64_t es = int64_t(lt.L) * lt.G;
+  if (kIn) {
+    for (int64_t x = threadIdx.x; x < span * K; x += blockDim.x) {
+      Tr v = Tr(src[u0 * K + x]);
+      buf[pad32(int(x))] = v;
     }
+    __syncthreads();
+    for (int w = threadIdx.x; w < kTileChunks * lt.L; w += blockDim.x) {
+      const int gl = w % kTileChunks, j = w / kTileChunks;
+      if (gl >= nch || j >= s_len[gl]) continue;
+      const int loc = int(s_u[gl] - u0) + j;
+      const int64_t n = int64_t(j) * lt.G + g0 + gl;
+#pragma unroll
+      for (int e = 0; e < K; ++e) {
+        dst[e * es + n] = buf[pad32(loc * K + e)];
+        if (dst_lo) dst_lo[e * es + n] = 0.f;
+      }
+    }
+  } else {
+    for (int w = threadIdx.x; w < kTileChunks * lt.L; w += blockDim.x) {
+      const int gl = w % kTileChunks, j = w / kTileChunks;
+      if (gl >= nch || j >= s_len[gl]) continue;
+      const int loc = int(s_u[gl] - u0) + j;
+      const int64_t n = int64_t(j) * lt.G + g0 + gl;
+#pragma unroll
+      for (int e = 0; e < K; ++e) {
+        Tr v = Tr(src[e * es + n]);
+        if (src_lo) v = Tr(__fadd_rn(float(src[e * es + n]), src_lo[e * es + n]));
+        buf[pad32(loc * K + e)] = v;
+      }
+    }
+    __syncthreads();
+    for (int64_t x = threadIdx.x; x < span * K; x += blockDim.x) dst[u0 * K + x] = buf[pad32(int(x))];
   }
 }
 
-// Level-0 interleaved -> user layout for NB-vectors (x = hi + lo, lo optional) and for a
-// per-step scalar (sc).
-template <class Tr, class Ti, int NB>
-__global__ void __launch_bounds__(kThreads) k_scatter0(LevelTables lt, const Ti* hi, const float* lo,
-                                                       Tr* out, const Tr* sc, Tr* sc_out) {
+// step sizes: user sequence layout -> interleaved per system chunk (s is shared by the D
+// systems of a sequence, so it is gathered per element)
+template <class Tr>
+__global__ void __launch_bounds__(kThreads) k_gather_s(LevelTables lt, Problem0 p, Tr* s) {
   const int64_t n = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (n >= lt.G * lt.L) return;
   const int64_t g = n % lt.G;
   const int j = int(n / lt.G);
-  const int64_t es = int64_t(lt.L) * lt.G;
   const ChunkPos cp = chunk_pos(lt, g);
   const int64_t t = cp.first + j;
   if (t > cp.last) return;
-  const int64_t at = lt.base[cp.i] + t;
-#pragma unroll
-  for (int e = 0; e < NB; ++e) {
-    Tr v = Tr(hi[e * es + n]);
-    if (lo) v = Tr(__fadd_rn(float(hi[e * es + n]), lo[e * es + n]));
-    out[at * NB + e] = v;
-  }
-  if (sc) sc_out[at] = sc[n];
+  s[n] = static_cast<const Tr*>(p.s)[p.soff[cp.i] + t];
 }
 
 template <class Tr, int NB, bool kFactor, bool kTop>
@@ -749,9 +772,12 @@ struct smnn_plan_s {
 
 namespace {
 
-// Chunk length per level.  SEQ: one level, one chunk per system (Alg. 3/4 as written).
-// CR/AUTO: level 0 takes chunks long enough to leave ~75k threads (at most 64 steps),
-// higher levels 32, until a level fits one chunk of <= kTopMax steps.
+// Chunk length per level (the autotuner table).  SEQ: one level, one chunk per system
+// (Alg. 3/4 as written).  CR/AUTO: level 0 takes chunks long enough to leave ~75k threads
+// (4..64 steps; desc.chunk overrides).  An upper level keeps >= 32k chunks while the level
+// is large (L = its steps / 32k, 4..32), else takes L = 16, until one chunk of <= kTopMax
+// steps per system remains.  Each level costs about L dependent steps of latency plus two
+// launches, so the upper levels stay short while enough chunks remain.
 std::vector<int> plan_levels(const smnn_desc& d, const std::vector<int64_t>& T, int64_t total) {
   int64_t maxT = 1;
   for (int64_t t : T) maxT = std::max(maxT, t);
@@ -761,25 +787,32 @@ std::vector<int> plan_levels(const smnn_desc& d, const std::vector<int64_t>& T, 
     return Ls;
   }
   std::vector<int64_t> P = T;
-  int64_t maxP = maxT;
+  int64_t maxP = maxT, sumP = total;
   bool first = true;
   while (maxP > kTopMax && int(Ls.size()) < kMaxLevels - 1) {
     int L;
-    if (first && d.chunk > 0) {
-      L = d.chunk;
-    } else if (first) {
-      const int64_t want = total / 75000;
+    if (first) {
+      if (d.chunk > 0) {
+        L = d.chunk;
+      } else {
+        const int64_t want = total / 75000;
+        L = 4;
+        while (L * 2 <= want && L < 64) L *= 2;
+      }
+    } else if (sumP >= 4 * 32768) {
       L = 4;
-      while (L * 2 <= want && L < 64) L *= 2;
+      while (L * 2 <= sumP / 32768 && L < 32) L *= 2;
     } else {
-      L = 32;
+      L = 16;
     }
     first = false;
     Ls.push_back(L);
     maxP = 0;
+    sumP = 0;
     for (auto& p : P) {
       p = (p + L - 1) / L;
       maxP = std::max(maxP, p);
+      sumP += p;
     }
   }
   Ls.push_back(int(std::max<int64_t>(maxP, 1)));
@@ -1029,12 +1062,63 @@ L0Bufs<Tr> l0_bufs(const smnn_plan_s* pl, char* sol) {
 
 inline int64_t l0_elems(const smnn_plan_s* pl) { return pl->lv[0].G * int64_t(pl->lv[0].L); }
 
+// Per-element transposes, used when a tile of kTileChunks chunks would not fit in shared
+// memory (long chunks, e.g. the sequential algorithm).
+template <class Tr, class Ts, int K, bool kIn>
+__global__ void __launch_bounds__(kThreads) k_copy_elem(LevelTables lt, const Ts* src, const float* src_lo,
+                                                        Tr* dst, float* dst_lo) {
+  const int64_t n = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (n >= lt.G * lt.L) return;
+  const int64_t g = n % lt.G;
+  const int j = int(n / lt.G);
+  const int64_t es = int64_t(lt.L) * lt.G;
+  const ChunkPos cp = chunk_pos(lt, g);
+  const int64_t t = cp.first + j;
+  if (t > cp.last) return;
+  const int64_t u = lt.base[cp.i] + t;
+#pragma unroll
+  for (int e = 0; e < K; ++e) {
+    if (kIn) {
+      dst[e * es + n] = Tr(src[u * K + e]);
+      if (dst_lo) dst_lo[e * es + n] = 0.f;
+    } else {
+      Tr v = Tr(src[e * es + n]);
+      if (src_lo) v = Tr(__fadd_rn(float(src[e * es + n]), src_lo[e * es + n]));
+      dst[u * K + e] = v;
+    }
+  }
+}
+
+template <class Tr, class Ts, int K, bool kIn>
+smnn_status tile_copy(const smnn_plan_s* pl, const Ts* src, const float* src_lo, Tr* dst, float* dst_lo,
+                      cudaStream_t st) {
+  const Level& L0 = pl->lv[0];
+  const unsigned blocks = unsigned((L0.G + kTileChunks - 1) / kTileChunks);
+  const int64_t elems = int64_t(kTileChunks) * L0.L * K;
+  const size_t shm = size_t(elems + elems / 32 + 1) * sizeof(Tr);
+  if (shm > 48 * 1024) {
+    SMNN_LAUNCH((k_copy_elem<Tr, Ts, K, kIn>), L0.G * int64_t(L0.L), st, tables_of(L0), src, src_lo, dst, dst_lo);
+    return SMNN_OK;
+  }
+  prof_begin("k_tile", st);
+  k_tile<Tr, Ts, K, kIn><<<blocks, kTileThreads, shm, st>>>(tables_of(L0), src, src_lo, dst, dst_lo);
+  prof_end(st);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError() == cudaSuccess ? SMNN_OK : SMNN_ERR_CUDA;
+}
+
 template <class Tr, int NB>
 smnn_status gather_inputs(const smnn_plan_s* pl, const Problem0& p, const L0Bufs<Tr>& b,
                           const Tr* vec, Tr* vec_out, float* vec_lo, bool coefs, cudaStream_t st) {
-  SMNN_LAUNCH((k_gather0<Tr, NB>), l0_elems(pl), st, tables_of(pl->lv[0]), p,
-              coefs ? b.c : nullptr, b.d, b.s, vec, vec_out, vec_lo);
-  return SMNN_OK;
+  smnn_status rc = SMNN_OK;
+  if (coefs) {
+    rc = tile_copy<Tr, Tr, NB, true>(pl, static_cast<const Tr*>(p.c), nullptr, b.c, nullptr, st);
+    if (rc == SMNN_OK) rc = tile_copy<Tr, Tr, 1, true>(pl, static_cast<const Tr*>(p.d), nullptr, b.d, nullptr, st);
+    if (rc != SMNN_OK) return rc;
+    SMNN_LAUNCH(k_gather_s<Tr>, l0_elems(pl), st, tables_of(pl->lv[0]), p, b.s);
+  }
+  if (vec) rc = tile_copy<Tr, Tr, NB, true>(pl, vec, nullptr, vec_out, vec_lo, st);
+  return rc;
 }
 
 #define SMNN_TRY(x) do { const smnn_status rc_ = (x); if (rc_ != SMNN_OK) return rc_; } while (0)
@@ -1102,7 +1186,8 @@ smnn_status gradients_out(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
   const L0In<Tr> in{b.c, b.d, b.s};
   SMNN_LAUNCH((k_grad<Tr, N, NB>), L0.G, st, tables_of(L0), p, in, yh, yl, gh, gl, info, b.gc, b.gd,
               b.gs, gu);
-  SMNN_LAUNCH((k_scatter0<Tr, Tr, NB>), l0_elems(pl), st, tables_of(L0), b.gc, nullptr, gc, b.gd, gd);
+  SMNN_TRY((tile_copy<Tr, Tr, NB, false>(pl, b.gc, nullptr, gc, nullptr, st)));
+  SMNN_TRY((tile_copy<Tr, Tr, 1, false>(pl, b.gd, nullptr, gd, nullptr, st)));
   SMNN_LAUNCH(k_scatter_gs<Tr>, pl->Q * int64_t(L0.L), st, gt, pl->d_seq_soff, pl->d_seq_T, b.gs, gs);
   return SMNN_OK;
 }
@@ -1122,16 +1207,14 @@ smnn_status factor_solve_t(const smnn_plan_s* pl, const void* c, const void* d, 
     if (pl->desc.precision == SMNN_F32_REFINED || pl->desc.precision == SMNN_F32_REFINED_DF) {
       if (pl->desc.precision == SMNN_F32_REFINED) SMNN_TRY((refine_forward<double, NB>(pl, p, fac, sol, info, st)));
       else SMNN_TRY((refine_forward<ff, NB>(pl, p, fac, sol, info, st)));
-      SMNN_LAUNCH((k_scatter0<float, float, NB>), l0_elems(pl), st, lt0, b.yh,
-                  reinterpret_cast<const float*>(fac + pl->o_fyl), static_cast<float*>(y), nullptr, nullptr);
+      return tile_copy<float, float, NB, false>(pl, b.yh, reinterpret_cast<const float*>(fac + pl->o_fyl),
+                                                static_cast<float*>(y), nullptr, st);
       return SMNN_OK;
     }
   }
   Level0Out<Tr> o{b.x, nullptr, nullptr, nullptr};
   SMNN_TRY((solve_pass<Tr, NB>(pl, p, nullptr, true, fac, sol, o, 0, info, st)));
-  SMNN_LAUNCH((k_scatter0<Tr, Tr, NB>), l0_elems(pl), st, lt0, b.x, nullptr, static_cast<Tr*>(y),
-              nullptr, nullptr);
-  return SMNN_OK;
+  return tile_copy<Tr, Tr, NB, false>(pl, b.x, nullptr, static_cast<Tr*>(y), nullptr, st);
 }
 
 template <class Tr, int NB>
