@@ -35,7 +35,8 @@
  * nothing and does not synchronise.  Host return codes report argument, workspace
  * and launch errors only.  Numerical failures go to the device array info[S]
  * (int32): 0 ok; k > 0: a non-positive pivot was met at (1-based) step k of that
- * system, and its outputs are NaN; -1: the refinement stop test
+ * system, and its outputs are NaN (steps eliminated first are reported first: a failure
+ * inside a chunk is reported before the separators it poisons); -1: the refinement stop test
  * (desc.refine_tol > 0) failed after the last sweep.
  */
 #ifndef SMNN_H_

@@ -275,7 +275,10 @@ __global__ void __launch_bounds__(kThreads) k_elimN(LevelTables lt, LevelBufs<Tr
   if (kTop) {
     if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = cp.last + 1;
   }
-  if (kFactor && fail) {  // report the level-0 step of the failing separator
+  // Report the level-0 step of the failing separator, unless a lower level (which finished
+  // before this kernel started) already reported a failure of this system: a bad pivot
+  // there poisons the Schur complement, so the lower level locates the cause.
+  if (kFactor && fail && *reinterpret_cast<volatile int32_t*>(info + cp.i) == 0) {
     const int64_t step0 = min(fail * lt.stride0, T0[cp.i]);
     record_fail(info + cp.i, int32_t(step0));
   }
