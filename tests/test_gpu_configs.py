@@ -1,0 +1,176 @@
+"""Full-size parity of the five workloads, in the launch configuration bench.py times
+(SMNN_F32_REFINED_DF, 3 forward and 3 adjoint refinement sweeps, saved factor), against the
+FP64 oracle on sampled systems (every system of a sampled sequence, so that dl/ds, which
+sums over the D dimensions of a sequence, is checked too).  GPU required."""
+import numpy as np
+import pytest
+
+import oracle as O
+from smnn_workloads import (Problem, config1, config2, config3, config3b, config4, config5,
+                            upstream_gradient)
+from _helpers import oracle_params, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+def run_full(prob, precision_name="F32_REFINED_DF", seed=2, store_factor=True, **kw):
+    import torch
+    import paper_2410_06074_b300 as pk
+    from paper_2410_06074_b300.api import _shape_key
+    prec = getattr(pk, precision_name)
+    dt = np.float64 if prec == pk.F64 else np.float32
+    c, d, s, u = (torch.from_numpy(np.ascontiguousarray(a, dt)).cuda() for a in (prob.c, prob.d, prob.s, prob.u))
+    cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=prec, max_refine=3,
+                         adjoint_refine=3, **kw)
+    seq_T = None if prob.seq_T is None else tuple(int(x) for x in prob.seq_T)
+    plan = pk.get_plan(_shape_key(c, s, prob.D, seq_T), cfg)
+    fac = plan.factor_buffer() if store_factor else None
+    y, info = pk.solve(c, d, s, u, cfg, D=prob.D, seq_T=seq_T, factor=fac)
+    gy_np = upstream_gradient(prob, seed).astype(dt)
+    gy = torch.from_numpy(gy_np).cuda()
+    gc, gd, gs, gu, info_b = pk.gradients(c, d, s, u, y, gy, cfg, D=prob.D, seq_T=seq_T, factor=fac)
+    torch.cuda.synchronize()
+    out = {k: v.double().cpu().numpy() for k, v in dict(y=y, gc=gc, gd=gd, gs=gs, gu=gu).items()}
+    return out, gy_np.astype(np.float64), info.cpu().numpy(), info_b.cpu().numpy()
+
+
+def sub_uniform(prob, seqs):
+    """Sub-problem made of whole sequences (uniform layout)."""
+    r = prob.cast(np.float32).as_f64()
+    return Problem(prob.name, prob.R, prob.R_init, prob.T_init, len(seqs), prob.D, prob.T,
+                   r.c[seqs], r.d[seqs], r.s[seqs], r.u[seqs], w_gov=prob.w_gov,
+                   w_init=prob.w_init, w_smooth=prob.w_smooth)
+
+
+def check_uniform(prob, out, gy, seqs, tol=TOL):
+    sp = sub_uniform(prob, seqs)
+    yo, gco, gdo, gso, guo, info = O.gradient(oracle_params(sp), sp.c, sp.d, sp.s, sp.u, gy[seqs])
+    assert (info == 0).all()
+    y = out["y"][seqs]
+    per = np.linalg.norm((y - yo).reshape(-1, prob.T * (prob.R + 1)), axis=1) / \
+        np.linalg.norm(yo.reshape(-1, prob.T * (prob.R + 1)), axis=1)
+    errs = {"y": float(per.max()), "gc": rel_err(out["gc"][seqs], gco), "gd": rel_err(out["gd"][seqs], gdo),
+            "gs": rel_err(out["gs"][seqs], gso), "gu": rel_err(out["gu"][seqs], guo)}
+    assert max(errs.values()) <= tol, errs
+    return errs
+
+
+def test_config1_fp64_full():
+    prob = config1()
+    out, gy, info, info_b = run_full(prob, "F64")
+    assert (info == 0).all() and (info_b == 0).all()
+    check_uniform(prob, out, gy, list(range(prob.B)), tol=1e-9)
+
+
+def test_config2_full_size_sampled():
+    prob = config2()
+    out, gy, info, info_b = run_full(prob)
+    assert (info == 0).all() and (info_b == 0).all()
+    check_uniform(prob, out, gy, [0, 97, 255, 256, 400, 511])
+
+
+def test_config3b_full_size():
+    """T = 2^20, R = 3, s ~ U[0.1, 0.5]: the refined FP32 chunked-CR path."""
+    prob = config3b()
+    out, gy, info, info_b = run_full(prob)
+    assert (info == 0).all() and (info_b == 0).all()
+    sp = sub_uniform(prob, [0])
+    # one system through the oracle (T = 2^20 rows in memory per system)
+    one = Problem("one", 3, 2, 1, 1, 1, prob.T, sp.c[:, :1], sp.d[:, :1], sp.s, sp.u[:, :1])
+    yo, info_o = O.solve(oracle_params(one), one.c, one.d, one.s, one.u, nthreads=1)
+    assert info_o[0] == 0
+    assert rel_err(out["y"][0, 0], yo[0, 0]) <= TOL
+
+
+def test_config3_as_stated_fp64_and_detected_fp32_breakdown():
+    """T = 2^20, R = 3, s ~ U[0.001, 0.01]: kappa(M) ~ 1e14.  The FP64 path agrees with the
+    FP64 oracle to the accuracy FP64 normal equations allow there (kappa * 1e-16 ~ 1e-2 worst
+    case; observed far better), and the FP32 factorisation reports its breakdown in info
+    instead of returning garbage."""
+    import torch
+    import paper_2410_06074_b300 as pk
+    prob = config3()
+    out, gy, info, info_b = run_full(prob, "F64")
+    assert (info == 0).all()
+    sp = sub_uniform(prob, [0])
+    one = Problem("one", 3, 2, 1, 1, 1, prob.T, sp.c[:, :1], sp.d[:, :1], sp.s, sp.u[:, :1])
+    yo, info_o = O.solve(oracle_params(one), one.c, one.d, one.s, one.u, nthreads=1)
+    assert info_o[0] == 0
+    assert rel_err(out["y"][0, 0], yo[0, 0]) <= 1e-3
+    y32, info32 = pk.solve(*(torch.from_numpy(a.astype(np.float32)).cuda() for a in (prob.c, prob.d, prob.s, prob.u)),
+                           pk.SolveConfig(R_init=2, T_init=1, precision=pk.F32_REFINED_DF))
+    info32 = info32.cpu().numpy()
+    y32 = y32.cpu().numpy()
+    for i in range(prob.D):   # each system either solves to the refined tolerance or reports
+        if info32[i] > 0:
+            assert np.isnan(y32[0, i]).all()
+
+
+def test_config4_ragged_full_size_sampled():
+    prob = config4()
+    out, gy, info, info_b = run_full(prob)
+    assert (info == 0).all() and (info_b == 0).all()
+    seq_T = prob.seq_T
+    off = np.concatenate([[0], np.cumsum(seq_T)])
+    picks = sorted(set([int(np.argmax(seq_T)), int(np.argmin(seq_T)), 0, 1, 2047, 4095]))
+    r = prob.cast(np.float32).as_f64()
+    for b in picks:
+        sl = slice(off[b], off[b + 1])
+        yo, gco, gdo, gso, guo, info_o = O.gradient(
+            oracle_params(prob), r.c[sl][None, None], r.d[sl][None, None], r.s[sl][None],
+            r.u[b][None, None], gy[sl][None, None])
+        errs = {"y": rel_err(out["y"][sl], yo[0, 0]), "gc": rel_err(out["gc"][sl], gco[0, 0]),
+                "gd": rel_err(out["gd"][sl], gdo[0, 0]), "gs": rel_err(out["gs"][sl], gso[0]),
+                "gu": rel_err(out["gu"][b], guo[0, 0])}
+        assert max(errs.values()) <= TOL, (b, int(seq_T[b]), errs)
+
+
+@pytest.mark.parametrize("store_factor", [True, False])
+def test_config5_full_size_sampled(store_factor):
+    """B=256, D=32, T=8192 with MLP-generated coefficients; both the saved-factor and the
+    recompute branch of the backward pass."""
+    prob = config5()
+    out, gy, info, info_b = run_full(prob, store_factor=store_factor)
+    assert (info == 0).all() and (info_b == 0).all()
+    check_uniform(prob, out, gy, [0, 255])
+
+
+def test_cuda_graph_replay_matches_eager():
+    """The forward + backward launch sequence captured in a CUDA graph replays to the same
+    bits as the eager calls."""
+    import torch
+    import paper_2410_06074_b300 as pk
+    from smnn_workloads import random_problem
+    prob = random_problem(41, 16, 4, 2048, 2).cast(np.float32)
+    c, d, s, u = (torch.from_numpy(a).cuda() for a in (prob.c, prob.d, prob.s, prob.u))
+    cfg = pk.SolveConfig(R_init=1, T_init=1, precision=pk.F32_REFINED_DF, max_refine=3, adjoint_refine=3)
+    plan = pk.get_plan((2, 16, 4, 2048), cfg)
+    ws, fac = plan.workspace(), plan.factor_buffer()
+    y = torch.empty_like(c); info = torch.empty(plan.S, dtype=torch.int32, device="cuda")
+    gy = torch.from_numpy(upstream_gradient(prob).astype(np.float32)).cuda()
+    gc, gd, gs, gu = (torch.empty_like(t) for t in (c, d, s, u))
+    info_b = torch.empty_like(info)
+
+    def step():
+        plan.factor_solve(c, d, s, u, y, info, ws, factor=fac)
+        plan.backward(c, d, s, u, y, gy, gc, gd, gs, gu, info_b, ws, factor=fac)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    eager = [t.clone() for t in (y, gc, gd, gs, gu)]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for t in (y, gc, gd, gs, gu):
+        t.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(eager, (y, gc, gd, gs, gu)):
+        assert torch.equal(a, b)
