@@ -426,7 +426,7 @@ def main():
             acc[name] = accuracy(v, ores, p32.S)
     ok = [n for n in ("F32_REFINED_DF", "F32_REFINED")
           if n in acc and max(acc[n].values()) <= 1e-6]
-    pool = ok if ok else ["F32_REFINED"]
+    pool = ok if ok else [n for n in ("F32_REFINED_DF", "F32_REFINED") if n in results]
     head = max(pool, key=lambda n: results[n]["value"])
     r = results[head]
     e2e, roof, whole = e2e_and_roofline(prob, variants[head], r, ws, args, stream, flush)
