@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 from smnn_workloads import config2, mse_target  # noqa: E402
 
-WORKLOAD = "config2: B=512 D=8 T=1024 R=2, FP32 factor + refinement (3 forward, 3 adjoint sweeps), fwd+adjoint"
+WORKLOAD = "config2: B=512 D=8 T=1024 R=2, FP32 factor + float-float/FP64-residual refinement, fwd+adjoint"
 METRIC = "time-steps solved/s fwd+bwd (FP32-refined, <=1e-6 vs FP64 oracle)"
 UNIT = "time-steps/s"
 
@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
     ap.add_argument("--chunk", type=int, default=0, help="level-0 chunk length (0: plan's table)")
     ap.add_argument("--only", default="", help="comma-separated variants to time (default: all)")
+    ap.add_argument("--max-refine", type=int, default=3, help="forward refinement sweeps")
+    ap.add_argument("--adjoint-refine", type=int, default=3, help="adjoint refinement sweeps")
     return ap.parse_args()
 
 
@@ -188,11 +190,12 @@ def algorithmic_units(name: str, NB: int, D: int):
 class Variant:
     """One precision mode of the library on the benchmark workload: its plan and buffers."""
 
-    def __init__(self, pk, prob, precision, dev, inputs, factor=True, chunk=0):
+    def __init__(self, pk, prob, precision, dev, inputs, factor=True, chunk=0, max_refine=3,
+                 adjoint_refine=3):
         import torch
         self.precision = precision
         cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=precision,
-                             max_refine=3, adjoint_refine=3, chunk=chunk)
+                             max_refine=max_refine, adjoint_refine=adjoint_refine, chunk=chunk)
         self.plan = pk.get_plan((prob.R, prob.B, prob.D, prob.T), cfg)
         dt = self.plan.dtype
         self.c, self.d, self.s, self.u = (t.to(dt) for t in inputs)
@@ -250,9 +253,10 @@ def run_ours(args, ws, rank, local):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     only = set(x for x in args.only.split(",") if x)
-    variants = {"F32_REFINED_DF": Variant(pk, prob, pk.F32_REFINED_DF, dev, inputs, chunk=args.chunk)}
+    kw = dict(chunk=args.chunk, max_refine=args.max_refine, adjoint_refine=args.adjoint_refine)
+    variants = {"F32_REFINED_DF": Variant(pk, prob, pk.F32_REFINED_DF, dev, inputs, **kw)}
     if not only or "F32_REFINED" in only:
-        variants["F32_REFINED"] = Variant(pk, prob, pk.F32_REFINED, dev, inputs, chunk=args.chunk)
+        variants["F32_REFINED"] = Variant(pk, prob, pk.F32_REFINED, dev, inputs, **kw)
     # dl/dy of config 2's loss, mean over S*T of (y^(0) - tau)^2, at this workload's y
     v0 = variants["F32_REFINED_DF"]
     v0.forward()
@@ -440,7 +444,8 @@ def main():
         "data": "synthetic (seeded config-2 generators: c~N(0,1), c2=1+|N|, d~N(0,1), s~U[0.01,0.1], u~N(0,1))",
         "config": {"workload": WORKLOAD, "B": prob.B, "D": prob.D, "T": prob.T, "R": prob.R,
                    "time_steps_per_pass": prob.steps, "precision": "SMNN_" + head,
-                   "solver": prec_txt, "max_refine": 3, "adjoint_refine": 3,
+                   "solver": prec_txt, "max_refine": args.max_refine,
+                   "adjoint_refine": args.adjoint_refine,
                    "factor": "stored in forward, reused in backward",
                    "l2": "256 MiB write between timed steps (outside the events)",
                    "parallelism": f"replicas x{ws} (independent systems, no collective)"},

@@ -355,8 +355,10 @@ struct EmitY {
         if (failed) acc = ff{nan_t<float>(), nan_t<float>()};
         o.acc_hi[a * es + n] = acc.hi;
         o.acc_lo[a * es + n] = acc.lo;
-        dd += double(v[a]) * double(v[a]);
-        yy += double(acc.hi) * double(acc.hi);
+        if (o.nrm) {  // only for the refinement stop test (FP64 work on a narrow pipe)
+          dd += double(v[a]) * double(v[a]);
+          yy += double(acc.hi) * double(acc.hi);
+        }
       }
     }
   }
