@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="level-0 chunk length (0: plan's table)")
     ap.add_argument("--only", default="", help="comma-separated variants to time (default: all)")
     ap.add_argument("--max-refine", type=int, default=3, help="forward refinement sweeps")
-    ap.add_argument("--adjoint-refine", type=int, default=3, help="adjoint refinement sweeps")
+    ap.add_argument("--adjoint-refine", type=int, default=2, help="adjoint refinement sweeps")
     return ap.parse_args()
 
 
@@ -191,7 +191,7 @@ class Variant:
     """One precision mode of the library on the benchmark workload: its plan and buffers."""
 
     def __init__(self, pk, prob, precision, dev, inputs, factor=True, chunk=0, max_refine=3,
-                 adjoint_refine=3):
+                 adjoint_refine=2):
         import torch
         self.precision = precision
         cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=precision,

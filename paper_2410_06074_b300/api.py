@@ -26,8 +26,8 @@ class SolveConfig:
     w_smooth: float = 1.0
     precision: int = B.F32_REFINED
     algo: int = B.ALGO_AUTO
-    max_refine: int = 2
-    adjoint_refine: int = 3
+    max_refine: int = 3
+    adjoint_refine: int = 2
     chunk: int = 0
     refine_tol: float = 0.0
     factor_budget_bytes: int = 16 << 30   # store the factor for backward if it fits

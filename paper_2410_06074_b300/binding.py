@@ -136,8 +136,8 @@ class Plan:
     seq_T: tuple | None = None
     precision: int = F32_REFINED
     algo: int = ALGO_AUTO
-    max_refine: int = 2
-    adjoint_refine: int = 3
+    max_refine: int = 3
+    adjoint_refine: int = 2
     chunk: int = 0
     w_gov: float = 1.0
     w_init: float = 1.0

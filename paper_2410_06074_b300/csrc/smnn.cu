@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_s(LevelTables lt, Problem0 
 }
 
 template <class Tr, int NB, bool kFactor, bool kTop>
-__global__ void __launch_bounds__(kThreads) k_elim0(LevelTables lt, LevelBufs<Tr, NB> lb, Problem0 p,
+__global__ void __launch_bounds__(kThreads, kFactor ? 3 : 4) k_elim0(LevelTables lt, LevelBufs<Tr, NB> lb, Problem0 p,
                                                     L0In<Tr> in, const Tr* rhs, int32_t* info) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
@@ -365,7 +365,7 @@ struct EmitY {
 };
 
 template <class Tr, int NB, int kMode>
-__global__ void __launch_bounds__(kThreads) k_backsub0(LevelTables lt, LevelBufs<Tr, NB> lb,
+__global__ void __launch_bounds__(kThreads, 4) k_backsub0(LevelTables lt, LevelBufs<Tr, NB> lb,
                                                        Problem0 p, L0In<Tr> in, Level0Out<Tr> o,
                                                        const int32_t* info) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -556,7 +556,7 @@ struct ResidualSource {
 
 // Level-0 replay of the stored FP32 factor on the refinement residual (fused, see above).
 template <class N, int NB, bool kTop>
-__global__ void __launch_bounds__(kThreads) k_elim0_res(LevelTables lt, LevelBufs<float, NB> lb,
+__global__ void __launch_bounds__(kThreads, 4) k_elim0_res(LevelTables lt, LevelBufs<float, NB> lb,
                                                         Problem0 p, L0In<float> in, const float* x_hi,
                                                         const float* x_lo, const float* rhs) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
