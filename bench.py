@@ -158,30 +158,41 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
-# FP64 peak of this B300, measured with a DFMA-chain microbenchmark (8 independent chains
-# per thread, 148 x 4..8 CTAs of 256 threads): 0.562e12 DFMA/s = 1.125 TFLOP/s at
-# ~1.94 GHz, i.e. ~2 DFMA per SM per clock; FP32 measured 68.7 TFLOP/s the same way.
-FP64_PEAK_TFLOPS = 1.125
+# ALU peaks.  FP32: 148 SMs x 128 FP32 lanes x 2.032 GHz (maximum SM clock; the clock
+# sampled under this benchmark's load) = 38.5e12 FP32 instructions/s, an FMA counted as one
+# instruction (a DFMA-chain and FFMA-chain microbenchmark on this B300 measured 34.4e12
+# FFMA/s and 0.562e12 DFMA/s).  FP64: ~2 DFMA/clock/SM -> 0.60e12 DP instructions/s.
+FP32_PEAK_TOPS = 148 * 128 * 2.032e9 / 1e12
+FP64_PEAK_TOPS = 148 * 2 * 2.032e9 / 1e12
 
 
-def algorithmic_units(name: str, NB: int, D: int):
-    """Per-step algorithmic work of one launch of a kernel: (bound, amount, unit).
-    FP64 arithmetic kernels count FP64 operations per time-step (an FMA counts 2); the
-    memory-bound sweeps count the HBM bytes the method must move per time-step."""
-    if name == "k_residual":
-        # governing row: c.x (NB FMA), w*(d - c.x) (2), NB FMA into r;  pair of smoothness
-        # row blocks: two Taylor products (NB(NB-1)/2 FMA each + NB), 2*NB subs, 2*NB weight
-        # products, two transposed Taylor products (NB(NB-1)/2 FMA each + NB), 2*NB
-        # combinations, NB + 2 power products; NB accumulations
-        tay = NB * (NB - 1) // 2
-        fl = 2 * NB + 2 + 2 * NB + 2 * (2 * tay + NB) + 2 * NB + 2 * NB + 2 * (2 * tay + NB) \
-            + 2 * NB + NB + 2 + NB
-        return "alu", float(fl), "FLOP"
-    if name == "k_grad":
-        tay = NB * (NB - 1) // 2
-        fl = 4 * NB + 2 * NB + 3 + 4 * (2 * tay + NB) + 4 * NB + NB * 16
-        return "alu", float(fl), "FLOP"
-    # elimination / substitution sweeps: c (4 NB) + d (4) + s (4/D) read, y (4 NB) written
+def residual_ops(NB: int, explicit_rhs: bool, df: bool) -> float:
+    """Arithmetic instructions per time-step of the refinement residual r = rhs - M x
+    (governing row, 2(R+1) smoothness rows, accumulation), counted from the formulas in
+    csrc/smnn.cu.  Float-float costs per operation (smnn_num.cuh): ff*float 6, ff*ff 7,
+    ff+float 10, ff+ff 11 FP32 instructions; in FP64 every operation is one instruction."""
+    n = NB
+    mf, mm, af, aa = (6, 7, 10, 11) if df else (1, 1, 1, 1)
+    gov = n * (mf + aa) + (mm + n * (mf + af + aa) if explicit_rhs else (af + mm) + n * (mf + aa))
+    tay = n * (n - 1) // 2 * (mm + aa)                  # one exp(+-sN) product
+    pair = (n - 1) * (mf + mf) + mf + (n - 1) * mm + 4 * tay + 2 * n * (aa + mm) + 2 * n * aa
+    return float(gov + pair + n * aa + n)
+
+
+def replay_ops(NB: int) -> float:
+    """FP32 instructions per time-step of one level-0 replay of the stored factor: z = L^-1 r,
+    the fill contribution H^T z, E_t from s_t, X = L^-1 E^T and r_{t+1} -= X^T z."""
+    n = NB
+    return float(n * n + n * n + (2 * n - 2 + 2 * n * n) + n * n * (n + 1) // 2 + n * n)
+
+
+def algorithmic_units(name: str, NB: int, D: int, df: bool):
+    """Per-step algorithmic work of one launch of a kernel: (bound, amount, unit)."""
+    if name == "k_elim0_res":
+        if df:
+            return "alu", residual_ops(NB, False, True) + replay_ops(NB), "FP32 instr"
+        return "alu", residual_ops(NB, False, False), "FP64 instr"
+    # memory sweeps: the method's forward bytes per time-step (c, d, s read; y written)
     return "hbm", 8.0 * NB + 4.0 + 4.0 / D, "B"
 
 
@@ -320,12 +331,15 @@ def e2e_and_roofline(prob, v, res, ws, args, stream, flush):
     prof = res["profile"]
     name, (nl, tms) = max(prof.items(), key=lambda kv: kv[1][1])
     per_launch_ms = tms / max(nl, 1)
-    bound, per_step, unit = algorithmic_units(name, NB, D)
+    df = v.precision == 3
+    bound, per_step, unit = algorithmic_units(name, NB, D, df)
     if bound == "alu":
+        peak = FP32_PEAK_TOPS if df else FP64_PEAK_TOPS
         achieved = per_step * steps_per_pass / (per_launch_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s (FP64)", "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "measured DFMA microbenchmark on this B300 (not in MEASURED_PEAKS.json)"}
+        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
+                "unit": "T FP32 instr/s" if df else "T FP64 instr/s", "frac": achieved / peak,
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2.032 GHz" if df else
+                               "derived: 148 SMs x 2 FP64 lanes x 2.032 GHz"}
     else:
         achieved = per_step * steps_per_pass / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"],

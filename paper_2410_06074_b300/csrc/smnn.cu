@@ -556,7 +556,7 @@ struct ResidualSource {
 
 // Level-0 replay of the stored FP32 factor on the refinement residual (fused, see above).
 template <class N, int NB, bool kTop>
-__global__ void __launch_bounds__(kThreads, 4) k_elim0_res(LevelTables lt, LevelBufs<float, NB> lb,
+__global__ void __launch_bounds__(kThreads) k_elim0_res(LevelTables lt, LevelBufs<float, NB> lb,
                                                         Problem0 p, L0In<float> in, const float* x_hi,
                                                         const float* x_lo, const float* rhs) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
