@@ -4,9 +4,9 @@
 and the ``SmnnSolve`` autograd.Function.  Importing fails loudly if libsmnn.so cannot be
 built or loaded: there is no CPU path.
 """
-from . import binding
+from . import autotune, binding
 from .api import SmnnSolve, SolveConfig, get_plan, gradients, smnn_layer, solve
 from .binding import ALGO_AUTO, ALGO_CR, ALGO_SEQ, F32, F32_REFINED, F32_REFINED_DF, F64, Plan, SmnnError
 
-__all__ = ["binding", "SmnnSolve", "SolveConfig", "get_plan", "gradients", "smnn_layer", "solve",
+__all__ = ["autotune", "binding", "SmnnSolve", "SolveConfig", "get_plan", "gradients", "smnn_layer", "solve",
            "Plan", "SmnnError", "F32", "F32_REFINED", "F32_REFINED_DF", "F64", "ALGO_AUTO", "ALGO_SEQ", "ALGO_CR"]

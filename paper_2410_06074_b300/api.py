@@ -7,7 +7,7 @@ kernels (binding.py).  Shapes (one system = one (sequence, dimension) pair):
 """
 from __future__ import annotations
 
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 
 import torch
 
@@ -33,8 +33,18 @@ class SolveConfig:
     factor_budget_bytes: int = 16 << 30   # store the factor for backward if it fits
 
 
-def get_plan(shape_key, cfg: SolveConfig) -> B.Plan:
-    """shape_key: (R, B, D, T) for uniform batches or (R, B, D, seq_T tuple) for ragged."""
+def get_plan(shape_key, cfg: SolveConfig, tuned: bool = True) -> B.Plan:
+    """shape_key: (R, B, D, T) for uniform batches or (R, B, D, seq_T tuple) for ragged.
+    With tuned=True, ALGO_AUTO and chunk=0, the autotuner's table may pick the algorithm and
+    the level-0 chunk length for this shape bucket."""
+    if tuned and cfg.algo == B.ALGO_AUTO and cfg.chunk == 0:
+        from . import autotune
+        R, Bn, D, T = shape_key
+        S = Bn * D
+        steps = S * T if not isinstance(T, tuple) else D * sum(T)
+        hit = autotune.lookup(R, S, steps, cfg.precision)
+        if hit is not None:
+            cfg = replace(cfg, algo=hit[0], chunk=hit[1])
     key = (shape_key, cfg)
     plan = _PLANS.get(key)
     if plan is None:

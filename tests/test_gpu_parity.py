@@ -237,3 +237,18 @@ def test_gradcheck_config2_slice():
     # kappa(M) ~ 2e5 here: eps = 1e-6 would leave ~1e-5 finite-difference noise from FP64
     # rounding of the solve itself; eps = 1e-4 keeps both noise and truncation below 1e-7
     assert torch.autograd.gradcheck(f, (c, d, z, u), eps=1e-4, atol=1e-6, rtol=1e-4)
+
+
+def test_autotuner_checks_candidates_and_picks_a_correct_one():
+    import torch
+    import paper_2410_06074_b300 as pk
+    prob = random_problem(51, 4, 4, 2048, 2).cast(np.float32)
+    c, d, s, u = (torch.from_numpy(a).cuda() for a in (prob.c, prob.d, prob.s, prob.u))
+    gy = torch.from_numpy(upstream_gradient(prob).astype(np.float32)).cuda()
+    cfg = pk.SolveConfig(R_init=1, T_init=1, precision=pk.F32_REFINED_DF)
+    best, res = pk.autotune.autotune(c, d, s, u, cfg, gy, save=False)
+    assert any(v is not None for v in res.values())
+    assert (best.algo, best.chunk) in [k for k, v in res.items() if v is not None]
+    y, info = pk.solve(c, d, s, u, best)
+    yo, _ = oracle_solve(prob.as_f64())
+    assert rel_err_per_system(y.double().cpu().numpy(), yo, prob).max() <= TOL_REF
