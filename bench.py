@@ -388,7 +388,7 @@ def run_reference(args, ws, rank):
     from smnn_workloads import upstream_gradient
     gy = np.zeros_like(p32.c, dtype=np.float64)
     gy[..., 0] = upstream_gradient(prob)[..., 0] / prob.steps
-    sample_sys = 256
+    sample_sys = prob.S          # the whole workload per step (~0.3-0.6 s on 8-16 cores)
     import oracle as O
     p64 = p32.as_f64()
     nseq = sample_sys // prob.D
