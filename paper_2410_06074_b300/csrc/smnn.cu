@@ -510,6 +510,8 @@ struct ResidualSource {
     }
     prefetch(cs.first);
   }
+  __device__ void prime(int64_t) {}
+  __device__ void commit(int64_t) {}
   using ERaw = typename CoefSource<float, NB>::ERaw;
   __device__ ERaw load_e(int64_t t) const { return cs.load_e(t); }
   __device__ void e_from(ERaw r, float (&e)[NB][NB]) const { cs.e_from(r, e); }
@@ -763,7 +765,7 @@ struct smnn_plan_s {
   int64_t Q = 0;
   std::vector<Level> lv;
   size_t factor_bytes = 0, solve_bytes = 0;
-  size_t o_fyl = 0;                    // factor region: low part of the refined y (FP32 paths)
+  size_t o_fyh = 0, o_fyl = 0;         // factor region: the refined y, float-float (FP32 paths)
   size_t o_nrm = 0;                    // solve region (bytes), and the level-0 interleaved arrays:
   size_t o_c = 0, o_d = 0, o_s = 0;    //   staged inputs
   size_t o_r = 0, o_gy = 0;            //   residual / explicit rhs, staged dl/dy
@@ -870,12 +872,16 @@ smnn_status build_plan_host(smnn_plan_s* pl) {
   {
     const Level& L0 = pl->lv[0];
     const size_t GL = size_t(L0.G) * size_t(L0.L);
+    // factor region: the staged inputs and the forward's float-float y, so that a backward
+    // pass given the saved factor neither re-stages c, d, s nor re-refines y
+    pl->o_c = f; f += align_up(GL * NB * es);
+    pl->o_d = f; f += align_up(GL * es);
+    pl->o_s = f; f += align_up(GL * es);
+    pl->o_fyh = f;
+    if (es == 4) f += align_up(GL * NB * 4);
     pl->o_fyl = f;
     if (es == 4) f += align_up(GL * NB * 4);
     auto take = [&](size_t bytes) { const size_t o = s; s += align_up(bytes); return o; };
-    pl->o_c = take(GL * NB * es);
-    pl->o_d = take(GL * es);
-    pl->o_s = take(GL * es);
     pl->o_r = take(GL * NB * es);
     pl->o_gy = take(GL * NB * es);
     pl->o_x = take(GL * NB * es);
@@ -987,9 +993,9 @@ Problem0 problem0(const smnn_plan_s* pl, const void* c, const void* d, const voi
 }
 
 template <class Tr>
-L0In<Tr> l0_in(const smnn_plan_s* pl, char* sol) {
-  return L0In<Tr>{reinterpret_cast<const Tr*>(sol + pl->o_c), reinterpret_cast<const Tr*>(sol + pl->o_d),
-                  reinterpret_cast<const Tr*>(sol + pl->o_s)};
+L0In<Tr> l0_in(const smnn_plan_s* pl, char* fac) {
+  return L0In<Tr>{reinterpret_cast<const Tr*>(fac + pl->o_c), reinterpret_cast<const Tr*>(fac + pl->o_d),
+                  reinterpret_cast<const Tr*>(fac + pl->o_s)};
 }
 
 // One pass of the chunked solve: eliminate level by level (factor, or replay the stored
@@ -1005,7 +1011,7 @@ smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, 
                        char* fac, char* sol, const Level0Out<Tr>& out, int mode, int32_t* info,
                        cudaStream_t st, const ResIn* res = nullptr) {
   const int nl = int(pl->lv.size());
-  const L0In<Tr> in = l0_in<Tr>(pl, sol);
+  const L0In<Tr> in = l0_in<Tr>(pl, fac);
   for (int l = 0; l < nl; ++l) {
     const Level& L = pl->lv[l];
     const LevelTables lt = tables_of(L);
@@ -1057,10 +1063,11 @@ struct L0Bufs {  // level-0 interleaved scratch of one call
 };
 
 template <class Tr>
-L0Bufs<Tr> l0_bufs(const smnn_plan_s* pl, char* sol) {
+L0Bufs<Tr> l0_bufs(const smnn_plan_s* pl, char* fac, char* sol) {
   auto P = [&](size_t o) { return reinterpret_cast<Tr*>(sol + o); };
   auto F = [&](size_t o) { return reinterpret_cast<float*>(sol + o); };
-  return L0Bufs<Tr>{P(pl->o_c), P(pl->o_d), P(pl->o_s), P(pl->o_r), P(pl->o_gy), P(pl->o_x),
+  auto PF = [&](size_t o) { return reinterpret_cast<Tr*>(fac + o); };
+  return L0Bufs<Tr>{PF(pl->o_c), PF(pl->o_d), PF(pl->o_s), P(pl->o_r), P(pl->o_gy), P(pl->o_x),
                     P(pl->o_g), F(pl->o_yh), F(pl->o_yl), F(pl->o_gh), F(pl->o_gl), P(pl->o_gc),
                     P(pl->o_gd), P(pl->o_gs), reinterpret_cast<double*>(sol + pl->o_nrm)};
 }
@@ -1134,17 +1141,18 @@ smnn_status gather_inputs(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
 template <class N, int NB>
 smnn_status refine_forward(const smnn_plan_s* pl, const Problem0& p, char* fac, char* sol,
                            int32_t* info, cudaStream_t st) {
-  const L0Bufs<float> b = l0_bufs<float>(pl, sol);
+  const L0Bufs<float> b = l0_bufs<float>(pl, fac, sol);
+  float* yh = reinterpret_cast<float*>(fac + pl->o_fyh);
   float* yl = reinterpret_cast<float*>(fac + pl->o_fyl);
   const int K = pl->desc.max_refine;
   const bool check = pl->desc.refine_tol > 0;
-  Level0Out<float> o{nullptr, b.yh, yl, nullptr};
+  Level0Out<float> o{nullptr, yh, yl, nullptr};
   SMNN_TRY((solve_pass<float, NB>(pl, p, nullptr, true, fac, sol, o, 1, info, st)));
   for (int it = 0; it < K; ++it) {
     const bool last = it + 1 == K;
     if (check && last) SMNN_LAUNCH(k_fill_f64, 2 * pl->S, st, b.nrm, 2 * pl->S, 0.0);
-    const ResIn ri{b.yh, yl, nullptr};
-    Level0Out<float> oa{nullptr, b.yh, yl, check && last ? b.nrm : nullptr};
+    const ResIn ri{yh, yl, nullptr};
+    Level0Out<float> oa{nullptr, yh, yl, check && last ? b.nrm : nullptr};
     SMNN_TRY((solve_pass<float, NB, N>(pl, p, nullptr, false, fac, sol, oa, 2, info, st, &ri)));
   }
   if (check && K > 0) SMNN_LAUNCH(k_refine_check, pl->S, st, b.nrm, pl->S, pl->desc.refine_tol, info);
@@ -1157,15 +1165,18 @@ smnn_status refine_forward(const smnn_plan_s* pl, const Problem0& p, char* fac, 
 template <class N, int NB>
 smnn_status refine_backward(const smnn_plan_s* pl, const Problem0& p, char* fac, char* sol,
                             bool recompute, const float* y, int32_t* info, cudaStream_t st,
-                            const float** y_lo_used) {
-  const L0Bufs<float> b = l0_bufs<float>(pl, sol);
+                            const float** y_hi_used, const float** y_lo_used) {
+  const L0Bufs<float> b = l0_bufs<float>(pl, fac, sol);
   const int KA = pl->desc.precision == SMNN_F32 ? 0 : pl->desc.adjoint_refine;
   Level0Out<float> og{nullptr, b.gh, b.gl, nullptr};
   SMNN_TRY((solve_pass<float, NB>(pl, p, b.gy, recompute, fac, sol, og, 1, info, st)));
-  SMNN_TRY((gather_inputs<float, NB>(pl, p, b, y, b.yh, b.yl, false, st)));
+  *y_hi_used = b.yh;
   *y_lo_used = nullptr;
+  const bool reuse = KA > 0 && !recompute && pl->desc.max_refine > 0;
+  if (!reuse) SMNN_TRY((gather_inputs<float, NB>(pl, p, b, y, b.yh, b.yl, false, st)));
   if (KA > 0) {
-    if (!recompute && pl->desc.max_refine > 0) {
+    if (reuse) {
+      *y_hi_used = reinterpret_cast<const float*>(fac + pl->o_fyh);
       *y_lo_used = reinterpret_cast<const float*>(fac + pl->o_fyl);
     } else {
       const ResIn ri{b.yh, nullptr, nullptr};
@@ -1204,7 +1215,7 @@ smnn_status factor_solve_t(const smnn_plan_s* pl, const void* c, const void* d, 
   const Problem0 p = problem0(pl, c, d, s, u);
   char* fac = factor ? static_cast<char*>(factor) : static_cast<char*>(ws);
   char* sol = static_cast<char*>(ws) + pl->factor_bytes;
-  const L0Bufs<Tr> b = l0_bufs<Tr>(pl, sol);
+  const L0Bufs<Tr> b = l0_bufs<Tr>(pl, fac, sol);
   const LevelTables lt0 = tables_of(pl->lv[0]);
   SMNN_LAUNCH(k_fill_i32, pl->S, st, info, pl->S, 0);
   SMNN_TRY((gather_inputs<Tr, NB>(pl, p, b, nullptr, nullptr, nullptr, true, st)));
@@ -1212,7 +1223,8 @@ smnn_status factor_solve_t(const smnn_plan_s* pl, const void* c, const void* d, 
     if (pl->desc.precision == SMNN_F32_REFINED || pl->desc.precision == SMNN_F32_REFINED_DF) {
       if (pl->desc.precision == SMNN_F32_REFINED) SMNN_TRY((refine_forward<double, NB>(pl, p, fac, sol, info, st)));
       else SMNN_TRY((refine_forward<ff, NB>(pl, p, fac, sol, info, st)));
-      return tile_copy<float, float, NB, false>(pl, b.yh, reinterpret_cast<const float*>(fac + pl->o_fyl),
+      return tile_copy<float, float, NB, false>(pl, reinterpret_cast<const float*>(fac + pl->o_fyh),
+                                                reinterpret_cast<const float*>(fac + pl->o_fyl),
                                                 static_cast<float*>(y), nullptr, st);
       return SMNN_OK;
     }
@@ -1229,22 +1241,24 @@ smnn_status backward_t(const smnn_plan_s* pl, const void* c, const void* d, cons
   const Problem0 p = problem0(pl, c, d, s, u);
   char* fac = factor ? static_cast<char*>(const_cast<void*>(factor)) : static_cast<char*>(ws);
   char* sol = static_cast<char*>(ws) + pl->factor_bytes;
-  const L0Bufs<Tr> b = l0_bufs<Tr>(pl, sol);
+  const L0Bufs<Tr> b = l0_bufs<Tr>(pl, fac, sol);
   SMNN_LAUNCH(k_fill_i32, pl->S, st, info, pl->S, 0);
-  SMNN_TRY((gather_inputs<Tr, NB>(pl, p, b, static_cast<const Tr*>(gy), b.gy, nullptr, true, st)));
+  // with the saved factor, the forward's staged c, d, s are still in the factor region
+  SMNN_TRY((gather_inputs<Tr, NB>(pl, p, b, static_cast<const Tr*>(gy), b.gy, nullptr, factor == nullptr, st)));
   Tr* gco = static_cast<Tr*>(gc);
   Tr* gdo = static_cast<Tr*>(gd);
   Tr* gso = static_cast<Tr*>(gs);
   Tr* guo = static_cast<Tr*>(gu);
   if constexpr (std::is_same<Tr, float>::value) {
     const float* y32 = static_cast<const float*>(y);
+    const float* yh = nullptr;
     const float* yl = nullptr;
     if (pl->desc.precision == SMNN_F32_REFINED_DF) {
-      SMNN_TRY((refine_backward<ff, NB>(pl, p, fac, sol, factor == nullptr, y32, info, st, &yl)));
-      return gradients_out<float, ff, NB>(pl, p, b, b.yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, st);
+      SMNN_TRY((refine_backward<ff, NB>(pl, p, fac, sol, factor == nullptr, y32, info, st, &yh, &yl)));
+      return gradients_out<float, ff, NB>(pl, p, b, yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, st);
     }
-    SMNN_TRY((refine_backward<double, NB>(pl, p, fac, sol, factor == nullptr, y32, info, st, &yl)));
-    return gradients_out<float, double, NB>(pl, p, b, b.yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, st);
+    SMNN_TRY((refine_backward<double, NB>(pl, p, fac, sol, factor == nullptr, y32, info, st, &yh, &yl)));
+    return gradients_out<float, double, NB>(pl, p, b, yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, st);
   } else {
     Level0Out<Tr> o{b.g, nullptr, nullptr, nullptr};
     SMNN_TRY((solve_pass<Tr, NB>(pl, p, b.gy, factor == nullptr, fac, sol, o, 0, info, st)));
@@ -1257,8 +1271,9 @@ template <class Tr, int NB>
 smnn_status assemble_t(const smnn_plan_s* pl, const void* c, const void* d, const void* s,
                        const void* u, void* M, void* N, void* beta, void* ws, cudaStream_t st) {
   const Problem0 p = problem0(pl, c, d, s, u);
+  char* fac = static_cast<char*>(ws);
   char* sol = static_cast<char*>(ws) + pl->factor_bytes;
-  const L0Bufs<Tr> b = l0_bufs<Tr>(pl, sol);
+  const L0Bufs<Tr> b = l0_bufs<Tr>(pl, fac, sol);
   SMNN_TRY((gather_inputs<Tr, NB>(pl, p, b, nullptr, nullptr, nullptr, true, st)));
   const L0In<Tr> in{b.c, b.d, b.s};
   SMNN_LAUNCH((k_assemble<Tr, NB>), pl->lv[0].G, st, tables_of(pl->lv[0]), p, in, static_cast<Tr*>(M),

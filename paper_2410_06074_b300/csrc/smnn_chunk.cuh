@@ -277,11 +277,37 @@ struct CoefSource {
   }
   SMNN_HD int64_t es() const { return int64_t(L) * G; }
 
+  // One-step-ahead staging for the elimination sweeps: prime(t) issues the loads of step t's
+  // inputs, commit(t) makes them the ones A(t) and b(t) use.  Without a commit A and b load
+  // directly.
+  struct Stage {
+    Tr c[NB], rh[NB];
+    Tr d, s, sp;
+  };
+  Stage cur, nxt;
+  int64_t cur_t = -1;
+  SMNN_HD void prime(int64_t t) {
+    const int64_t k = at(t);
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      nxt.c[r] = c[r * es() + k];
+      if (rhs) nxt.rh[r] = rhs[r * es() + k];
+    }
+    nxt.d = d[k];
+    nxt.s = s[k];
+    nxt.sp = t > 0 ? s[at(t - 1)] : Tr(0);
+  }
+  SMNN_HD void commit(int64_t t) {
+    cur = nxt;
+    cur_t = t;
+  }
+
   SMNN_HD void A(int64_t t, Tr (&a)[NB][NB]) const {
     const int64_t k = at(t);
+    const bool st = t == cur_t;
     Tr cv[NB];
 #pragma unroll
-    for (int r = 0; r < NB; ++r) cv[r] = c[r * es() + k];
+    for (int r = 0; r < NB; ++r) cv[r] = st ? cur.c[r] : c[r * es() + k];
 #pragma unroll
     for (int i = 0; i < NB; ++i)
 #pragma unroll
@@ -291,8 +317,8 @@ struct CoefSource {
       for (int r = 0; r < NB; ++r)
         if (r <= R_init) a[r][r] += wi2;
     }
-    if (t + 1 < T) add_smooth<false>(s[k], a);
-    if (t > 0) add_smooth<true>(s[at(t - 1)], a);
+    if (t + 1 < T) add_smooth<false>(st ? cur.s : s[k], a);
+    if (t > 0) add_smooth<true>(st ? cur.sp : s[at(t - 1)], a);
   }
 
   // w_s^2 ((S+- F^T F S+-) + S2) of the pair (t, t+1), seen from t (kMinus = false) or
@@ -316,14 +342,15 @@ struct CoefSource {
 
   SMNN_HD void b(int64_t t, Tr (&v)[NB]) const {
     const int64_t k = at(t);
+    const bool st = t == cur_t;
     if (rhs) {
 #pragma unroll
-      for (int r = 0; r < NB; ++r) v[r] = rhs[r * es() + k];
+      for (int r = 0; r < NB; ++r) v[r] = st ? cur.rh[r] : rhs[r * es() + k];
       return;
     }
-    const Tr dt = d[k];
+    const Tr dt = st ? cur.d : d[k];
 #pragma unroll
-    for (int r = 0; r < NB; ++r) v[r] = wg2 * c[r * es() + k] * dt;
+    for (int r = 0; r < NB; ++r) v[r] = wg2 * (st ? cur.c[r] : c[r * es() + k]) * dt;
     if (t < T_init) {
 #pragma unroll
       for (int r = 0; r < NB; ++r)
@@ -392,6 +419,8 @@ struct ReducedSource {
       for (int j = 0; j < NB; ++j) e[i][j] = r.v[i * NB + j];
   }
   SMNN_HD void E(int64_t k, Tr (&e)[NB][NB]) const { e_from(load_e(k), e); }
+  SMNN_HD void prime(int64_t) {}
+  SMNN_HD void commit(int64_t) {}
 };
 
 // ----------------------------------------------------------------------------- chunk sweeps
@@ -408,6 +437,9 @@ SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
   using ERaw = typename Src::ERaw;
   int64_t fail = 0;
   Tr D[NB][NB], Gm[NB][NB], r[NB], Sl[NB][NB], bl[NB];
+  src.prime(first);
+  src.commit(first);
+  if (first < last) src.prime(first + 1);
   src.b(first, r);
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
@@ -428,6 +460,8 @@ SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
   }
   for (int64_t t = first; t < last; ++t) {
     const int j = int(t - first);
+    src.commit(t + 1);
+    if (t + 2 <= last) src.prime(t + 2);
     Tr Lm[NB][NB], inv[NB];
     Raw nxt;
     ERaw enxt;
