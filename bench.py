@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--only", default="", help="comma-separated variants to time (default: all)")
     ap.add_argument("--max-refine", type=int, default=3, help="forward refinement sweeps")
     ap.add_argument("--adjoint-refine", type=int, default=2, help="adjoint refinement sweeps")
+    ap.add_argument("--refine-tol", type=float, default=1e-8,
+                    help="per-system refinement stop test (0: always run every sweep)")
     return ap.parse_args()
 
 
@@ -202,11 +204,12 @@ class Variant:
     """One precision mode of the library on the benchmark workload: its plan and buffers."""
 
     def __init__(self, pk, prob, precision, dev, inputs, factor=True, chunk=0, max_refine=3,
-                 adjoint_refine=2):
+                 adjoint_refine=2, refine_tol=0.0):
         import torch
         self.precision = precision
         cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=precision,
-                             max_refine=max_refine, adjoint_refine=adjoint_refine, chunk=chunk)
+                             max_refine=max_refine, adjoint_refine=adjoint_refine, chunk=chunk,
+                             refine_tol=refine_tol if precision != pk.F64 else 0.0)
         self.plan = pk.get_plan((prob.R, prob.B, prob.D, prob.T), cfg)
         dt = self.plan.dtype
         self.c, self.d, self.s, self.u = (t.to(dt) for t in inputs)
@@ -264,7 +267,8 @@ def run_ours(args, ws, rank, local):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     only = set(x for x in args.only.split(",") if x)
-    kw = dict(chunk=args.chunk, max_refine=args.max_refine, adjoint_refine=args.adjoint_refine)
+    kw = dict(chunk=args.chunk, max_refine=args.max_refine, adjoint_refine=args.adjoint_refine,
+              refine_tol=args.refine_tol)
     variants = {"F32_REFINED_DF": Variant(pk, prob, pk.F32_REFINED_DF, dev, inputs, **kw)}
     if not only or "F32_REFINED" in only:
         variants["F32_REFINED"] = Variant(pk, prob, pk.F32_REFINED, dev, inputs, **kw)
@@ -459,7 +463,7 @@ def main():
         "config": {"workload": WORKLOAD, "B": prob.B, "D": prob.D, "T": prob.T, "R": prob.R,
                    "time_steps_per_pass": prob.steps, "precision": "SMNN_" + head,
                    "solver": prec_txt, "max_refine": args.max_refine,
-                   "adjoint_refine": args.adjoint_refine,
+                   "adjoint_refine": args.adjoint_refine, "refine_tol": args.refine_tol,
                    "factor": "stored in forward, reused in backward",
                    "l2": "256 MiB write between timed steps (outside the events)",
                    "parallelism": f"replicas x{ws} (independent systems, no collective)"},

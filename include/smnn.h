@@ -37,7 +37,7 @@
  * (int32): 0 ok; k > 0: a non-positive pivot was met at (1-based) step k of that
  * system, and its outputs are NaN (steps eliminated first are reported first: a failure
  * inside a chunk is reported before the separators it poisons); -1: the refinement stop test
- * (desc.refine_tol > 0) failed after the last sweep.
+ * (desc.refine_tol > 0) was not met after the last sweep.
  */
 #ifndef SMNN_H_
 #define SMNN_H_
@@ -93,7 +93,10 @@ typedef struct smnn_desc {
   double w_gov;           /* importance weights of Eq. 9 (unsquared; W holds their  */
   double w_init;          /*   squares, App. A.1), >= 0                             */
   double w_smooth;
-  double refine_tol;      /* > 0: info = -1 where the last sweep's ||dy||/||y|| > tol */
+  double refine_tol;      /* > 0: per-system stop test of the refinement: a system   */
+                          /* stops once its estimated error ||dy_k||^2/||dy_{k-1}|| */
+                          /* is <= refine_tol ||y|| (the remaining sweeps skip it);  */
+                          /* still above after the last sweep: info = -1            */
   int64_t num_seq;        /* B >= 1                                                 */
   int64_t dims_per_seq;   /* D >= 1                                                 */
   int64_t T;              /* steps per sequence (uniform batch; ignored if seq_T)   */

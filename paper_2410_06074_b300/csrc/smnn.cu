@@ -168,10 +168,6 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
   if (i < n) p[i] = v;
 }
 
-__global__ void k_fill_f64(double* p, int64_t n, double v) {
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (i < n) p[i] = v;
-}
 
 // Tiled user <-> level-0 interleaved transposes for per-step arrays of K values.  A CTA
 // takes kTileChunks consecutive chunks; their steps are one contiguous range of the user
@@ -266,10 +262,11 @@ __global__ void __launch_bounds__(kThreads, kFactor ? 3 : 4) k_elim0(LevelTables
 template <class Tr, int NB, bool kFactor, bool kTop>
 __global__ void __launch_bounds__(kThreads) k_elimN(LevelTables lt, LevelBufs<Tr, NB> lb,
                                                     ChunkOut<Tr, NB> prev, const int64_t* T0,
-                                                    int32_t* info) {
+                                                    int32_t* info, const int32_t* skip) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
   const ChunkPos cp = chunk_pos(lt, g);
+  if (skip && skip[cp.i]) return;
   ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[cp.i], cp.T);
   int64_t fail = elim_chunk<Tr, NB, kFactor>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
   if (kTop) {
@@ -298,10 +295,12 @@ struct EmitX {
 
 template <class Tr, int NB>
 __global__ void __launch_bounds__(kThreads) k_backsubN(LevelTables lt, LevelBufs<Tr, NB> lb,
-                                                       ChunkOut<Tr, NB> prev, Tr* x_prev) {
+                                                       ChunkOut<Tr, NB> prev, Tr* x_prev,
+                                                       const int32_t* skip) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
   const ChunkPos cp = chunk_pos(lt, g);
+  if (skip && skip[cp.i]) return;
   const ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[cp.i], cp.T);
   EmitX<Tr, NB> emit{x_prev + lt.base[cp.i] * NB};
   backsub_chunk<Tr, NB>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.xsep + g * NB,
@@ -309,14 +308,14 @@ __global__ void __launch_bounds__(kThreads) k_backsubN(LevelTables lt, LevelBufs
 }
 
 // Level-0 output of a solve pass, interleaved.  mode 0: x = v.  mode 1 (FP32 refinement):
-// float-float accumulator acc = v.  mode 2: acc += v, optionally with the squared norms of
-// v and acc for the refinement stop test.
+// float-float accumulator acc = v.  mode 2: acc += v; with `part`, also each chunk's sums of
+// v^2 and acc^2 (FP32) for the per-system stop test of the refinement.
 template <class Tr>
 struct Level0Out {
   Tr* x;
   float* acc_hi;
   float* acc_lo;
-  double* nrm;
+  float* part;   // [G0][2] or nullptr
 };
 
 template <class Tr, int NB, int kMode>
@@ -325,7 +324,7 @@ struct EmitY {
   int64_t g, G, first;
   int L;
   bool failed;
-  double dd, yy;
+  float dd, yy;
   struct Pre {  // the accumulator of step t (mode 2), loaded ahead of its update
     float hi[NB], lo[NB];
   };
@@ -355,9 +354,9 @@ struct EmitY {
         if (failed) acc = ff{nan_t<float>(), nan_t<float>()};
         o.acc_hi[a * es + n] = acc.hi;
         o.acc_lo[a * es + n] = acc.lo;
-        if (o.nrm) {  // only for the refinement stop test (FP64 work on a narrow pipe)
-          dd += double(v[a]) * double(v[a]);
-          yy += double(acc.hi) * double(acc.hi);
+        if (kMode == 2 && o.part) {
+          dd = fmaf(float(v[a]), float(v[a]), dd);
+          yy = fmaf(acc.hi, acc.hi, yy);
         }
       }
     }
@@ -367,25 +366,39 @@ struct EmitY {
 template <class Tr, int NB, int kMode>
 __global__ void __launch_bounds__(kThreads, 4) k_backsub0(LevelTables lt, LevelBufs<Tr, NB> lb,
                                                        Problem0 p, L0In<Tr> in, Level0Out<Tr> o,
-                                                       const int32_t* info) {
+                                                       const int32_t* info, const int32_t* skip) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
   const ChunkPos cp = chunk_pos(lt, g);
+  if (skip && skip[cp.i]) return;
   const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, in, nullptr, cp.i, g, cp.first, cp.T, lt.L, lt.G);
-  EmitY<Tr, NB, kMode> emit{o, g, lt.G, cp.first, lt.L, info[cp.i] > 0, 0.0, 0.0};
+  EmitY<Tr, NB, kMode> emit{o, g, lt.G, cp.first, lt.L, info[cp.i] > 0, 0.f, 0.f};
   backsub_chunk<Tr, NB>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.xsep + g * NB,
                         cp.k > 0 ? lb.xsep + (g - 1) * NB : nullptr, emit);
-  if (kMode == 2 && o.nrm) {
-    atomicAdd(o.nrm + 2 * cp.i, emit.dd);
-    atomicAdd(o.nrm + 2 * cp.i + 1, emit.yy);
+  if (kMode == 2 && o.part) {
+    o.part[2 * g] = emit.dd;
+    o.part[2 * g + 1] = emit.yy;
   }
 }
 
-__global__ void k_refine_check(const double* nrm, int64_t S, double tol, int32_t* info) {
+// Per-system stop test of the refinement after a sweep: with d_k = ||dy_k|| (this sweep's
+// correction) the error of y_k is estimated as d_k^2 / d_{k-1} (the sweep contracts the
+// error by ~d_k/d_{k-1}); a system whose estimate is <= tol ||y|| skips the remaining sweeps.
+// After the first sweep only d_1 <= tol/100 ||y|| stops.  The chunk partials are summed in
+// chunk order (deterministic).  On the last sweep an unconverged system gets info = -1.
+__global__ void k_converge(int64_t S, const int64_t* coff0, const float* part, float* prev,
+                           int32_t* skip, float tol, bool first, bool last, int32_t* info) {
   const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (i >= S) return;
-  const double dd = nrm[2 * i], yy = nrm[2 * i + 1];
-  if (info[i] == 0 && !(dd <= tol * tol * yy)) info[i] = -1;
+  if (i >= S || skip[i]) return;
+  float d2 = 0.f, y2 = 0.f;
+  for (int64_t g = coff0[i]; g < coff0[i + 1]; ++g) {
+    d2 += part[2 * g];
+    y2 += part[2 * g + 1];
+  }
+  const bool conv = first ? d2 <= 1e-4f * tol * tol * y2 : d2 <= tol * sqrtf(y2 * prev[i]);
+  prev[i] = d2;
+  if (conv) skip[i] = 1;
+  else if (last && info[i] == 0) info[i] = -1;
 }
 
 // ---- refinement residual, in FP64 or float-float ------------------------------------
@@ -560,10 +573,12 @@ struct ResidualSource {
 template <class N, int NB, bool kTop>
 __global__ void __launch_bounds__(kThreads) k_elim0_res(LevelTables lt, LevelBufs<float, NB> lb,
                                                         Problem0 p, L0In<float> in, const float* x_hi,
-                                                        const float* x_lo, const float* rhs) {
+                                                        const float* x_lo, const float* rhs,
+                                                        const int32_t* skip) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
   const ChunkPos cp = chunk_pos(lt, g);
+  if (skip && skip[cp.i]) return;
   ResidualSource<N, NB> src;
   src.cs = make_coef<float, NB>(p, in, nullptr, cp.i, g, cp.first, cp.T, lt.L, lt.G);
   src.xh = x_hi;
@@ -766,7 +781,7 @@ struct smnn_plan_s {
   std::vector<Level> lv;
   size_t factor_bytes = 0, solve_bytes = 0;
   size_t o_fyh = 0, o_fyl = 0;         // factor region: the refined y, float-float (FP32 paths)
-  size_t o_nrm = 0;                    // solve region (bytes), and the level-0 interleaved arrays:
+  size_t o_part = 0, o_prev = 0, o_skip = 0;  // refinement stop test (solve region), and:
   size_t o_c = 0, o_d = 0, o_s = 0;    //   staged inputs
   size_t o_r = 0, o_gy = 0;            //   residual / explicit rhs, staged dl/dy
   size_t o_x = 0, o_g = 0;             //   plain solutions (FP64 and FP32 paths)
@@ -894,7 +909,9 @@ smnn_status build_plan_host(smnn_plan_s* pl) {
     }
     pl->o_gc = take(GL * NB * es);
     pl->o_gd = take(GL * es);
-    pl->o_nrm = take(size_t(S) * 2 * sizeof(double));
+    pl->o_part = take(size_t(L0.G) * 2 * sizeof(float));
+    pl->o_prev = take(size_t(S) * sizeof(float));
+    pl->o_skip = take(size_t(S) * sizeof(int32_t));
   }
   pl->factor_bytes = f;
 
@@ -1009,7 +1026,7 @@ struct ResIn {  // refinement sweep: residual of x (float-float) against rhs (or
 template <class Tr, int NB, class N = double>
 smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, bool factor,
                        char* fac, char* sol, const Level0Out<Tr>& out, int mode, int32_t* info,
-                       cudaStream_t st, const ResIn* res = nullptr) {
+                       cudaStream_t st, const ResIn* res = nullptr, const int32_t* skip = nullptr) {
   const int nl = int(pl->lv.size());
   const L0In<Tr> in = l0_in<Tr>(pl, fac);
   for (int l = 0; l < nl; ++l) {
@@ -1019,8 +1036,8 @@ smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, 
     const bool top = l == nl - 1;
     if constexpr (std::is_same<Tr, float>::value) {
       if (l == 0 && res) {
-        if (top) SMNN_LAUNCH((k_elim0_res<N, NB, true>), L.G, st, lt, lb, p, in, res->xh, res->xl, res->rhs);
-        else SMNN_LAUNCH((k_elim0_res<N, NB, false>), L.G, st, lt, lb, p, in, res->xh, res->xl, res->rhs);
+        if (top) SMNN_LAUNCH((k_elim0_res<N, NB, true>), L.G, st, lt, lb, p, in, res->xh, res->xl, res->rhs, skip);
+        else SMNN_LAUNCH((k_elim0_res<N, NB, false>), L.G, st, lt, lb, p, in, res->xh, res->xl, res->rhs, skip);
         continue;
       }
     }
@@ -1031,25 +1048,25 @@ smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, 
       else SMNN_LAUNCH((k_elim0<Tr, NB, false, false>), L.G, st, lt, lb, p, in, rhs, info);
     } else {
       const ChunkOut<Tr, NB> prev = bufs_of<Tr, NB>(pl->lv[l - 1], fac, sol).out;
-      if (factor && top) SMNN_LAUNCH((k_elimN<Tr, NB, true, true>), L.G, st, lt, lb, prev, pl->d_sys_T, info);
-      else if (factor) SMNN_LAUNCH((k_elimN<Tr, NB, true, false>), L.G, st, lt, lb, prev, pl->d_sys_T, info);
-      else if (top) SMNN_LAUNCH((k_elimN<Tr, NB, false, true>), L.G, st, lt, lb, prev, pl->d_sys_T, info);
-      else SMNN_LAUNCH((k_elimN<Tr, NB, false, false>), L.G, st, lt, lb, prev, pl->d_sys_T, info);
+      if (factor && top) SMNN_LAUNCH((k_elimN<Tr, NB, true, true>), L.G, st, lt, lb, prev, pl->d_sys_T, info, nullptr);
+      else if (factor) SMNN_LAUNCH((k_elimN<Tr, NB, true, false>), L.G, st, lt, lb, prev, pl->d_sys_T, info, nullptr);
+      else if (top) SMNN_LAUNCH((k_elimN<Tr, NB, false, true>), L.G, st, lt, lb, prev, pl->d_sys_T, info, skip);
+      else SMNN_LAUNCH((k_elimN<Tr, NB, false, false>), L.G, st, lt, lb, prev, pl->d_sys_T, info, skip);
     }
   }
   for (int l = nl - 1; l >= 1; --l) {
     const Level& L = pl->lv[l];
     const LevelBufs<Tr, NB> lb = bufs_of<Tr, NB>(L, fac, sol);
     const LevelBufs<Tr, NB> pb = bufs_of<Tr, NB>(pl->lv[l - 1], fac, sol);
-    SMNN_LAUNCH((k_backsubN<Tr, NB>), L.G, st, tables_of(L), lb, pb.out, pb.xsep);
+    SMNN_LAUNCH((k_backsubN<Tr, NB>), L.G, st, tables_of(L), lb, pb.out, pb.xsep, skip);
   }
   const Level& L0 = pl->lv[0];
   const LevelBufs<Tr, NB> lb0 = bufs_of<Tr, NB>(L0, fac, sol);
   if (mode == 0) {
-    SMNN_LAUNCH((k_backsub0<Tr, NB, 0>), L0.G, st, tables_of(L0), lb0, p, in, out, info);
+    SMNN_LAUNCH((k_backsub0<Tr, NB, 0>), L0.G, st, tables_of(L0), lb0, p, in, out, info, skip);
   } else if constexpr (std::is_same<Tr, float>::value) {
-    if (mode == 1) SMNN_LAUNCH((k_backsub0<Tr, NB, 1>), L0.G, st, tables_of(L0), lb0, p, in, out, info);
-    else SMNN_LAUNCH((k_backsub0<Tr, NB, 2>), L0.G, st, tables_of(L0), lb0, p, in, out, info);
+    if (mode == 1) SMNN_LAUNCH((k_backsub0<Tr, NB, 1>), L0.G, st, tables_of(L0), lb0, p, in, out, info, skip);
+    else SMNN_LAUNCH((k_backsub0<Tr, NB, 2>), L0.G, st, tables_of(L0), lb0, p, in, out, info, skip);
   }
   return SMNN_OK;
 }
@@ -1059,7 +1076,7 @@ struct L0Bufs {  // level-0 interleaved scratch of one call
   Tr* c; Tr* d; Tr* s; Tr* r; Tr* gy; Tr* x; Tr* g;
   float* yh; float* yl; float* gh; float* gl;
   Tr* gc; Tr* gd; Tr* gs;
-  double* nrm;
+  float* part; float* prev; int32_t* skip;
 };
 
 template <class Tr>
@@ -1069,7 +1086,8 @@ L0Bufs<Tr> l0_bufs(const smnn_plan_s* pl, char* fac, char* sol) {
   auto PF = [&](size_t o) { return reinterpret_cast<Tr*>(fac + o); };
   return L0Bufs<Tr>{PF(pl->o_c), PF(pl->o_d), PF(pl->o_s), P(pl->o_r), P(pl->o_gy), P(pl->o_x),
                     P(pl->o_g), F(pl->o_yh), F(pl->o_yl), F(pl->o_gh), F(pl->o_gl), P(pl->o_gc),
-                    P(pl->o_gd), P(pl->o_gs), reinterpret_cast<double*>(sol + pl->o_nrm)};
+                    P(pl->o_gd), P(pl->o_gs), F(pl->o_part), F(pl->o_prev),
+                    reinterpret_cast<int32_t*>(sol + pl->o_skip)};
 }
 
 inline int64_t l0_elems(const smnn_plan_s* pl) { return pl->lv[0].G * int64_t(pl->lv[0].L); }
@@ -1135,6 +1153,27 @@ smnn_status gather_inputs(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
 
 #define SMNN_TRY(x) do { const smnn_status rc_ = (x); if (rc_ != SMNN_OK) return rc_; } while (0)
 
+// K refinement sweeps of x (float-float) against rhs (nullptr: beta).  With desc.refine_tol
+// > 0 each system stops as soon as its estimated error is <= refine_tol ||x|| (k_converge),
+// and systems still above it after the last sweep get info = -1.
+template <class N, int NB>
+smnn_status refine_sweeps(const smnn_plan_s* pl, const Problem0& p, char* fac, char* sol, float* xh,
+                          float* xl, const float* rhs, int K, int32_t* info, cudaStream_t st) {
+  const L0Bufs<float> b = l0_bufs<float>(pl, fac, sol);
+  const bool adaptive = pl->desc.refine_tol > 0;
+  if (adaptive) SMNN_LAUNCH(k_fill_i32, pl->S, st, b.skip, pl->S, 0);
+  for (int it = 0; it < K; ++it) {
+    const ResIn ri{xh, xl, rhs};
+    Level0Out<float> oa{nullptr, xh, xl, adaptive ? b.part : nullptr};
+    SMNN_TRY((solve_pass<float, NB, N>(pl, p, nullptr, false, fac, sol, oa, 2, info, st, &ri,
+                                       adaptive ? b.skip : nullptr)));
+    if (adaptive)
+      SMNN_LAUNCH(k_converge, pl->S, st, pl->S, pl->lv[0].d_coff, b.part, b.prev, b.skip,
+                  float(pl->desc.refine_tol), it == 0, it + 1 == K, info);
+  }
+  return SMNN_OK;
+}
+
 // Forward solve with refinement in number type N (double: FP64 residual; ff: float-float).
 // The accumulator's low part lives in the factor region so that smnn_backward, given the same
 // factor buffer, starts from the refined y without refining it again.
@@ -1145,18 +1184,9 @@ smnn_status refine_forward(const smnn_plan_s* pl, const Problem0& p, char* fac, 
   float* yh = reinterpret_cast<float*>(fac + pl->o_fyh);
   float* yl = reinterpret_cast<float*>(fac + pl->o_fyl);
   const int K = pl->desc.max_refine;
-  const bool check = pl->desc.refine_tol > 0;
   Level0Out<float> o{nullptr, yh, yl, nullptr};
   SMNN_TRY((solve_pass<float, NB>(pl, p, nullptr, true, fac, sol, o, 1, info, st)));
-  for (int it = 0; it < K; ++it) {
-    const bool last = it + 1 == K;
-    if (check && last) SMNN_LAUNCH(k_fill_f64, 2 * pl->S, st, b.nrm, 2 * pl->S, 0.0);
-    const ResIn ri{yh, yl, nullptr};
-    Level0Out<float> oa{nullptr, yh, yl, check && last ? b.nrm : nullptr};
-    SMNN_TRY((solve_pass<float, NB, N>(pl, p, nullptr, false, fac, sol, oa, 2, info, st, &ri)));
-  }
-  if (check && K > 0) SMNN_LAUNCH(k_refine_check, pl->S, st, b.nrm, pl->S, pl->desc.refine_tol, info);
-  return SMNN_OK;
+  return refine_sweeps<N, NB>(pl, p, fac, sol, yh, yl, nullptr, K, info, st);
 }
 
 // Adjoint: g = M^{-1} gy refined KA times (float-float accumulator).  y: with a saved factor
@@ -1185,12 +1215,7 @@ smnn_status refine_backward(const smnn_plan_s* pl, const Problem0& p, char* fac,
       *y_lo_used = b.yl;
     }
   }
-  for (int it = 0; it < KA; ++it) {
-    const ResIn ri{b.gh, b.gl, b.gy};
-    Level0Out<float> oa{nullptr, b.gh, b.gl, nullptr};
-    SMNN_TRY((solve_pass<float, NB, N>(pl, p, nullptr, false, fac, sol, oa, 2, info, st, &ri)));
-  }
-  return SMNN_OK;
+  return refine_sweeps<N, NB>(pl, p, fac, sol, b.gh, b.gl, b.gy, KA, info, st);
 }
 
 template <class Tr, class N, int NB>

@@ -252,3 +252,21 @@ def test_autotuner_checks_candidates_and_picks_a_correct_one():
     y, info = pk.solve(c, d, s, u, best)
     yo, _ = oracle_solve(prob.as_f64())
     assert rel_err_per_system(y.double().cpu().numpy(), yo, prob).max() <= TOL_REF
+
+
+@pytest.mark.parametrize("prec", REFINED)
+def test_adaptive_refinement_stop_test(prec):
+    """With refine_tol each system stops once its estimated error is small; results still meet
+    the refined tolerance and no system is flagged on a well-conditioned batch."""
+    pk = P()
+    prob = random_problem(61, 8, 4, 1024, 2)
+    y, info = gpu_solve(prob, getattr(pk, prec), max_refine=4, refine_tol=1e-8)
+    yo, _ = oracle_solve(rounded(prob, pk.F32_REFINED))
+    assert (info == 0).all()
+    assert rel_err_per_system(y, yo, prob).max() <= TOL_REF
+    gy = upstream_gradient(prob).astype(np.float32)
+    out = gpu_grad(prob, gy, getattr(pk, prec), max_refine=4, adjoint_refine=3, refine_tol=1e-8)
+    ref = oracle_grad(rounded(prob, pk.F32_REFINED), gy.astype(np.float64))
+    for a, b in zip(out[:5], ref[:5]):
+        assert rel_err(a, b) <= TOL_REF
+    assert (out[5] == 0).all() and (out[6] == 0).all()
