@@ -986,10 +986,13 @@ LevelBufs<Tr, NB> bufs_of(const Level& L, char* fac, char* sol) {
 
 inline unsigned nblocks(int64_t n) { return unsigned((n + kThreads - 1) / kThreads); }
 
-#define SMNN_LAUNCH(kern, n, st, ...)                                         \
+// The profiler records a launch under the kernel's name, or under `label` (SMNN_LAUNCH_AS) where
+// one kernel serves two passes of different cost (factorisation vs replay).
+#define SMNN_LAUNCH(kern, n, st, ...) SMNN_LAUNCH_AS(#kern, kern, n, st, __VA_ARGS__)
+#define SMNN_LAUNCH_AS(label, kern, n, st, ...)                               \
   do {                                                                        \
     if ((n) > 0) {                                                            \
-      prof_begin(#kern, st);                                                  \
+      prof_begin(label, st);                                                  \
       kern<<<nblocks(n), kThreads, 0, st>>>(__VA_ARGS__);                     \
       prof_end(st);                                                           \
       g_launches.fetch_add(1, std::memory_order_relaxed);                     \
@@ -1042,14 +1045,14 @@ smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, 
       }
     }
     if (l == 0) {
-      if (factor && top) SMNN_LAUNCH((k_elim0<Tr, NB, true, true>), L.G, st, lt, lb, p, in, rhs, info);
-      else if (factor) SMNN_LAUNCH((k_elim0<Tr, NB, true, false>), L.G, st, lt, lb, p, in, rhs, info);
+      if (factor && top) SMNN_LAUNCH_AS("k_elim0[factor]", (k_elim0<Tr, NB, true, true>), L.G, st, lt, lb, p, in, rhs, info);
+      else if (factor) SMNN_LAUNCH_AS("k_elim0[factor]", (k_elim0<Tr, NB, true, false>), L.G, st, lt, lb, p, in, rhs, info);
       else if (top) SMNN_LAUNCH((k_elim0<Tr, NB, false, true>), L.G, st, lt, lb, p, in, rhs, info);
       else SMNN_LAUNCH((k_elim0<Tr, NB, false, false>), L.G, st, lt, lb, p, in, rhs, info);
     } else {
       const ChunkOut<Tr, NB> prev = bufs_of<Tr, NB>(pl->lv[l - 1], fac, sol).out;
-      if (factor && top) SMNN_LAUNCH((k_elimN<Tr, NB, true, true>), L.G, st, lt, lb, prev, pl->d_sys_T, info, nullptr);
-      else if (factor) SMNN_LAUNCH((k_elimN<Tr, NB, true, false>), L.G, st, lt, lb, prev, pl->d_sys_T, info, nullptr);
+      if (factor && top) SMNN_LAUNCH_AS("k_elimN[factor]", (k_elimN<Tr, NB, true, true>), L.G, st, lt, lb, prev, pl->d_sys_T, info, nullptr);
+      else if (factor) SMNN_LAUNCH_AS("k_elimN[factor]", (k_elimN<Tr, NB, true, false>), L.G, st, lt, lb, prev, pl->d_sys_T, info, nullptr);
       else if (top) SMNN_LAUNCH((k_elimN<Tr, NB, false, true>), L.G, st, lt, lb, prev, pl->d_sys_T, info, skip);
       else SMNN_LAUNCH((k_elimN<Tr, NB, false, false>), L.G, st, lt, lb, prev, pl->d_sys_T, info, skip);
     }
