@@ -38,6 +38,7 @@ from smnn_workloads import config2, mse_target  # noqa: E402
 WORKLOAD = "config2: B=512 D=8 T=1024 R=2, FP32 factor + float-float/FP64-residual refinement, fwd+adjoint"
 METRIC = "time-steps solved/s fwd+bwd (FP32-refined, <=1e-6 vs FP64 oracle)"
 UNIT = "time-steps/s"
+ALGOS = {"auto": 0, "seq": 1, "cr": 2, "fused": 3}   # smnn_algo
 
 
 def parse():
@@ -49,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
     ap.add_argument("--chunk", type=int, default=0, help="level-0 chunk length (0: plan's table)")
+    ap.add_argument("--algo", default="auto", choices=sorted(ALGOS),
+                    help="reduction: auto (the plan's choice), seq, cr (a launch per level), "
+                         "fused (a launch per solve pass)")
     ap.add_argument("--only", default="", help="comma-separated variants to time (default: all)")
     ap.add_argument("--max-refine", type=int, default=3, help="forward refinement sweeps")
     ap.add_argument("--adjoint-refine", type=int, default=2, help="adjoint refinement sweeps")
@@ -205,11 +209,12 @@ class Variant:
     """One precision mode of the library on the benchmark workload: its plan and buffers."""
 
     def __init__(self, pk, prob, precision, dev, inputs, factor=True, chunk=0, max_refine=3,
-                 adjoint_refine=2, refine_tol=0.0):
+                 adjoint_refine=2, refine_tol=0.0, algo=0):
         import torch
         self.precision = precision
         cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=precision,
                              max_refine=max_refine, adjoint_refine=adjoint_refine, chunk=chunk,
+                             algo=algo,
                              refine_tol=refine_tol if precision != pk.F64 else 0.0)
         self.plan = pk.get_plan((prob.R, prob.B, prob.D, prob.T), cfg)
         dt = self.plan.dtype
@@ -269,7 +274,7 @@ def run_ours(args, ws, rank, local):
 
     only = set(x for x in args.only.split(",") if x)
     kw = dict(chunk=args.chunk, max_refine=args.max_refine, adjoint_refine=args.adjoint_refine,
-              refine_tol=args.refine_tol)
+              refine_tol=args.refine_tol, algo=ALGOS[args.algo])
     variants = {"F32_REFINED_DF": Variant(pk, prob, pk.F32_REFINED_DF, dev, inputs, **kw)}
     if not only or "F32_REFINED" in only:
         variants["F32_REFINED"] = Variant(pk, prob, pk.F32_REFINED, dev, inputs, **kw)
@@ -282,7 +287,7 @@ def run_ours(args, ws, rank, local):
     for v in variants.values():
         v.gy = gy
     if not args.no_fp64 and (not only or "F64" in only):
-        v64 = Variant(pk, prob, pk.F64, dev, inputs, chunk=args.chunk)
+        v64 = Variant(pk, prob, pk.F64, dev, inputs, chunk=args.chunk, algo=ALGOS[args.algo])
         v64.gy = gy.double()
         variants["F64"] = v64
     torch.cuda.synchronize()
@@ -294,18 +299,22 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         barrier(ws)
         n0 = Bd.launch_count()
-        Bd.profile_enable(True)
         with ClockSampler(local) as clk:
             ms = timed(v.step, args.steps, stream, flush)
-        Bd.profile_enable(False)
         launches = Bd.launch_count() - n0
+        # per-kernel event timing on a second timed run of the same steps, so that the
+        # events around every launch do not lengthen the headline run
+        Bd.profile_enable(True)
+        ms_prof = timed(v.step, args.steps, stream, flush)
+        Bd.profile_enable(False)
         prof = Bd.profile_read()
         ms = max_over_ranks(ms, ws) / args.steps
         fwd_ms = max_over_ranks(timed(v.forward, args.steps, stream, flush), ws) / args.steps
         assert int((v.info != 0).sum()) == 0 and int((v.info_b != 0).sum()) == 0, f"{name}: solver failures"
         results[name] = {"ms_per_step": ms, "value": ws * steps_per_pass / (ms / 1e3),
                          "fwd_ms_per_step": fwd_ms, "fwd_value": ws * steps_per_pass / (fwd_ms / 1e3),
-                         "gpu_launches": launches, "clocks": clk.summary(), "profile": prof}
+                         "gpu_launches": launches, "clocks": clk.summary(), "profile": prof,
+                         "ms_per_step_profiled": max_over_ranks(ms_prof, ws) / args.steps}
     return prob, p32, variants, results, stream, flush, dev
 
 
@@ -465,6 +474,7 @@ def main():
                    "time_steps_per_pass": prob.steps, "precision": "SMNN_" + head,
                    "solver": prec_txt, "max_refine": args.max_refine,
                    "adjoint_refine": args.adjoint_refine, "refine_tol": args.refine_tol,
+                   "algo": args.algo,
                    "factor": "stored in forward, reused in backward",
                    "l2": "256 MiB write between timed steps (outside the events)",
                    "parallelism": f"replicas x{ws} (independent systems, no collective)"},
@@ -474,9 +484,13 @@ def main():
         "clocks": r["clocks"],
         "roofline": roof,
         "whole_step_hbm": whole,
-        "variants": {n: {k: x[k] for k in ("value", "ms_per_step", "fwd_value", "fwd_ms_per_step")}
+        "variants": {n: {k: x[k] for k in ("value", "ms_per_step", "fwd_value", "fwd_ms_per_step",
+                                           "ms_per_step_profiled")}
                      for n, x in results.items()},
         "kernels": {k: {"launches": x[0], "total_ms": x[1]} for k, x in sorted(r["profile"].items())},
+        "kernels_note": "per-launch CUDA events on the launching stream over a second timed run "
+                        "of the same steps (ms_per_step_profiled); the headline run has no events "
+                        "between launches",
         "accuracy_vs_oracle": acc,
     }
     if cpu is not None:

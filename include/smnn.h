@@ -75,9 +75,17 @@ typedef enum {
 } smnn_precision;
 
 typedef enum {
-  SMNN_ALGO_AUTO = 0,  /* autotuner table picks the level structure per (T, S, R)   */
-  SMNN_ALGO_SEQ = 1,   /* one sequential block-Cholesky sweep per system (Alg. 3, 4) */
-  SMNN_ALGO_CR = 2     /* chunked block cyclic reduction, parallel over T           */
+  SMNN_ALGO_AUTO = 0,  /* chunked reduction, one launch per level and direction up   */
+                       /* to the first level whose systems each fit a CTA (<= 128    */
+                       /* chunks), one launch for that level and all above it        */
+  SMNN_ALGO_SEQ = 1,   /* one sequential block-Cholesky sweep per system (Alg. 3, 4), */
+                       /* elimination and substitution in one launch                 */
+  SMNN_ALGO_CR = 2,    /* chunked block cyclic reduction, parallel over T, one       */
+                       /* launch per level and direction                             */
+  SMNN_ALGO_CR_FUSED = 3 /* chunked reduction in one launch per solve pass: a CTA runs */
+                       /* every level of its systems; plan creation returns          */
+                       /* SMNN_ERR_UNSUPPORTED when a system has more than 128       */
+                       /* level-0 chunks                                             */
 } smnn_algo;
 
 typedef struct smnn_desc {
@@ -87,7 +95,7 @@ typedef struct smnn_desc {
   int32_t precision;      /* smnn_precision                                         */
   int32_t algo;           /* smnn_algo                                              */
   int32_t max_refine;     /* forward refinement sweeps (refined modes), 0..16       */
-  int32_t chunk;          /* level-0 chunk length for SMNN_ALGO_CR, 0 = autotuned   */
+  int32_t chunk;          /* level-0 chunk length of the chunked reduction, 0 = auto */
   int32_t adjoint_refine; /* refinement sweeps of the adjoint solve, 0..16; when > 0 */
                           /* the backward also refines y once before the gradients  */
   double w_gov;           /* importance weights of Eq. 9 (unsquared; W holds their  */

@@ -6,7 +6,7 @@ built or loaded: there is no CPU path.
 """
 from . import autotune, binding
 from .api import SmnnSolve, SolveConfig, get_plan, gradients, smnn_layer, solve
-from .binding import ALGO_AUTO, ALGO_CR, ALGO_SEQ, F32, F32_REFINED, F32_REFINED_DF, F64, Plan, SmnnError
+from .binding import ALGO_AUTO, ALGO_CR, ALGO_CR_FUSED, ALGO_SEQ, F32, F32_REFINED, F32_REFINED_DF, F64, Plan, SmnnError
 
 __all__ = ["autotune", "binding", "SmnnSolve", "SolveConfig", "get_plan", "gradients", "smnn_layer", "solve",
-           "Plan", "SmnnError", "F32", "F32_REFINED", "F32_REFINED_DF", "F64", "ALGO_AUTO", "ALGO_SEQ", "ALGO_CR"]
+           "Plan", "SmnnError", "F32", "F32_REFINED", "F32_REFINED_DF", "F64", "ALGO_AUTO", "ALGO_SEQ", "ALGO_CR", "ALGO_CR_FUSED"]

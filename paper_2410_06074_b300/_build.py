@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsmnn.so")
 SOURCES = [os.path.join(CSRC, "smnn.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "smnn_chunk.cuh"),
+DEPS = SOURCES + [os.path.join(CSRC, "smnn_chunk.cuh"), os.path.join(CSRC, "smnn_num.cuh"),
                   os.path.join(os.path.dirname(HERE), "include", "smnn.h")]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-shared", "-Xcompiler", "-fPIC", "-cudart", "shared", "--expt-relaxed-constexpr"]

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 (SMNN_OK, SMNN_ERR_INVALID_ARG, SMNN_ERR_WORKSPACE, SMNN_ERR_CUDA, SMNN_ERR_UNSUPPORTED,
  SMNN_ERR_TOO_LARGE) = range(6)
 F32_REFINED, F32, F64, F32_REFINED_DF = 0, 1, 2, 3
-ALGO_AUTO, ALGO_SEQ, ALGO_CR = 0, 1, 2
+ALGO_AUTO, ALGO_SEQ, ALGO_CR, ALGO_CR_FUSED = 0, 1, 2, 3
 SMNN_MAX_R = 3
 
 

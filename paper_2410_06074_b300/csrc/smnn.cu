@@ -90,6 +90,19 @@ struct LevelBufs {
   Tr* xsep;  // [G][NB] values at this level's separators (= the next level's unknowns)
 };
 
+// Every level of a plan, for the fused launches: CTA c owns systems cta_sys[c] ..
+// cta_sys[c+1]-1, whose chunks at every level from `from` up are consecutive and number at
+// most kThreads.
+template <class Tr, int NB>
+struct FusedLevels {
+  int nl;
+  int from;
+  const int32_t* cta_sys;
+  const int64_t* T0;
+  LevelTables lt[kMaxLevels];
+  LevelBufs<Tr, NB> lb[kMaxLevels];
+};
+
 struct Problem0 {  // level-0 inputs
   const void* c;
   const void* d;
@@ -245,18 +258,47 @@ __global__ void __launch_bounds__(kThreads) k_gather_s(LevelTables lt, Problem0 
   s[n] = static_cast<const Tr*>(p.s)[p.soff[cp.i] + t];
 }
 
+// The per-chunk bodies of the level kernels (one thread = one chunk g of a level), shared by
+// the one-launch-per-level kernels and the fused per-CTA pass (k_pass).
+template <class Tr, int NB, bool kFactor>
+__device__ __forceinline__ void dev_elim0(const LevelTables& lt, const LevelBufs<Tr, NB>& lb,
+                                          const Problem0& p, const L0In<Tr>& in, const Tr* rhs,
+                                          int32_t* info, int64_t g, bool top) {
+  const ChunkPos cp = chunk_pos(lt, g);
+  CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, in, rhs, cp.i, g, cp.first, cp.T, lt.L, lt.G);
+  int64_t fail = elim_chunk<Tr, NB, kFactor>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
+  if (top) {
+    if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = cp.last + 1;
+  }
+  if (kFactor && fail) record_fail(info + cp.i, int32_t(fail));
+}
+
 template <class Tr, int NB, bool kFactor, bool kTop>
 __global__ void __launch_bounds__(kThreads, kFactor ? 3 : 4) k_elim0(LevelTables lt, LevelBufs<Tr, NB> lb, Problem0 p,
                                                     L0In<Tr> in, const Tr* rhs, int32_t* info) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
+  dev_elim0<Tr, NB, kFactor>(lt, lb, p, in, rhs, info, g, kTop);
+}
+
+template <class Tr, int NB, bool kFactor>
+__device__ __forceinline__ void dev_elimN(const LevelTables& lt, const LevelBufs<Tr, NB>& lb,
+                                          const ChunkOut<Tr, NB>& prev, const int64_t* T0,
+                                          int32_t* info, const int32_t* skip, int64_t g, bool top) {
   const ChunkPos cp = chunk_pos(lt, g);
-  CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, in, rhs, cp.i, g, cp.first, cp.T, lt.L, lt.G);
+  if (skip && skip[cp.i]) return;
+  ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[cp.i], cp.T);
   int64_t fail = elim_chunk<Tr, NB, kFactor>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
-  if (kTop) {
+  if (top) {
     if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = cp.last + 1;
   }
-  if (kFactor && fail) record_fail(info + cp.i, int32_t(fail));
+  // Report the level-0 step of the failing separator, unless a lower level (which finished
+  // before this level started) already reported a failure of this system: a bad pivot
+  // there poisons the Schur complement, so the lower level locates the cause.
+  if (kFactor && fail && *reinterpret_cast<volatile int32_t*>(info + cp.i) == 0) {
+    const int64_t step0 = min(fail * lt.stride0, T0[cp.i]);
+    record_fail(info + cp.i, int32_t(step0));
+  }
 }
 
 template <class Tr, int NB, bool kFactor, bool kTop>
@@ -265,20 +307,7 @@ __global__ void __launch_bounds__(kThreads) k_elimN(LevelTables lt, LevelBufs<Tr
                                                     int32_t* info, const int32_t* skip) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  const ChunkPos cp = chunk_pos(lt, g);
-  if (skip && skip[cp.i]) return;
-  ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[cp.i], cp.T);
-  int64_t fail = elim_chunk<Tr, NB, kFactor>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
-  if (kTop) {
-    if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = cp.last + 1;
-  }
-  // Report the level-0 step of the failing separator, unless a lower level (which finished
-  // before this kernel started) already reported a failure of this system: a bad pivot
-  // there poisons the Schur complement, so the lower level locates the cause.
-  if (kFactor && fail && *reinterpret_cast<volatile int32_t*>(info + cp.i) == 0) {
-    const int64_t step0 = min(fail * lt.stride0, T0[cp.i]);
-    record_fail(info + cp.i, int32_t(step0));
-  }
+  dev_elimN<Tr, NB, kFactor>(lt, lb, prev, T0, info, skip, g, kTop);
 }
 
 // Emit functor of level >= 1 back substitution: values of this level's unknowns.
@@ -294,17 +323,24 @@ struct EmitX {
 };
 
 template <class Tr, int NB>
-__global__ void __launch_bounds__(kThreads) k_backsubN(LevelTables lt, LevelBufs<Tr, NB> lb,
-                                                       ChunkOut<Tr, NB> prev, Tr* x_prev,
-                                                       const int32_t* skip) {
-  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (g >= lt.G) return;
+__device__ __forceinline__ void dev_backsubN(const LevelTables& lt, const LevelBufs<Tr, NB>& lb,
+                                             const ChunkOut<Tr, NB>& prev, Tr* x_prev,
+                                             const int32_t* skip, int64_t g) {
   const ChunkPos cp = chunk_pos(lt, g);
   if (skip && skip[cp.i]) return;
   const ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[cp.i], cp.T);
   EmitX<Tr, NB> emit{x_prev + lt.base[cp.i] * NB};
   backsub_chunk<Tr, NB>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.xsep + g * NB,
                         cp.k > 0 ? lb.xsep + (g - 1) * NB : nullptr, emit);
+}
+
+template <class Tr, int NB>
+__global__ void __launch_bounds__(kThreads) k_backsubN(LevelTables lt, LevelBufs<Tr, NB> lb,
+                                                       ChunkOut<Tr, NB> prev, Tr* x_prev,
+                                                       const int32_t* skip) {
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= lt.G) return;
+  dev_backsubN<Tr, NB>(lt, lb, prev, x_prev, skip, g);
 }
 
 // Level-0 output of a solve pass, interleaved.  mode 0: x = v.  mode 1 (FP32 refinement):
@@ -364,11 +400,10 @@ struct EmitY {
 };
 
 template <class Tr, int NB, int kMode>
-__global__ void __launch_bounds__(kThreads, 4) k_backsub0(LevelTables lt, LevelBufs<Tr, NB> lb,
-                                                       Problem0 p, L0In<Tr> in, Level0Out<Tr> o,
-                                                       const int32_t* info, const int32_t* skip) {
-  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (g >= lt.G) return;
+__device__ __forceinline__ void dev_backsub0(const LevelTables& lt, const LevelBufs<Tr, NB>& lb,
+                                             const Problem0& p, const L0In<Tr>& in,
+                                             const Level0Out<Tr>& o, const int32_t* info,
+                                             const int32_t* skip, int64_t g) {
   const ChunkPos cp = chunk_pos(lt, g);
   if (skip && skip[cp.i]) return;
   const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, in, nullptr, cp.i, g, cp.first, cp.T, lt.L, lt.G);
@@ -379,6 +414,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_backsub0(LevelTables lt, LevelB
     o.part[2 * g] = emit.dd;
     o.part[2 * g + 1] = emit.yy;
   }
+}
+
+template <class Tr, int NB, int kMode>
+__global__ void __launch_bounds__(kThreads, 4) k_backsub0(LevelTables lt, LevelBufs<Tr, NB> lb,
+                                                       Problem0 p, L0In<Tr> in, Level0Out<Tr> o,
+                                                       const int32_t* info, const int32_t* skip) {
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= lt.G) return;
+  dev_backsub0<Tr, NB, kMode>(lt, lb, p, in, o, info, skip, g);
 }
 
 // Per-system stop test of the refinement after a sweep: with d_k = ||dy_k|| (this sweep's
@@ -570,13 +614,12 @@ struct ResidualSource {
 };
 
 // Level-0 replay of the stored FP32 factor on the refinement residual (fused, see above).
-template <class N, int NB, bool kTop>
-__global__ void __launch_bounds__(kThreads) k_elim0_res(LevelTables lt, LevelBufs<float, NB> lb,
-                                                        Problem0 p, L0In<float> in, const float* x_hi,
-                                                        const float* x_lo, const float* rhs,
-                                                        const int32_t* skip) {
-  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (g >= lt.G) return;
+template <class N, int NB>
+__device__ __forceinline__ void dev_elim0_res(const LevelTables& lt, const LevelBufs<float, NB>& lb,
+                                              const Problem0& p, const L0In<float>& in,
+                                              const float* x_hi, const float* x_lo,
+                                              const float* rhs, const int32_t* skip, int64_t g,
+                                              bool top) {
   const ChunkPos cp = chunk_pos(lt, g);
   if (skip && skip[cp.i]) return;
   ResidualSource<N, NB> src;
@@ -591,7 +634,86 @@ __global__ void __launch_bounds__(kThreads) k_elim0_res(LevelTables lt, LevelBuf
   src.last = cp.last;
   src.init();
   elim_chunk<float, NB, false>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
-  if (kTop) solve_top<float, NB>(lb.out, g, lb.xsep + g * NB);
+  if (top) solve_top<float, NB>(lb.out, g, lb.xsep + g * NB);
+}
+
+template <class N, int NB, bool kTop>
+__global__ void __launch_bounds__(kThreads) k_elim0_res(LevelTables lt, LevelBufs<float, NB> lb,
+                                                        Problem0 p, L0In<float> in, const float* x_hi,
+                                                        const float* x_lo, const float* rhs,
+                                                        const int32_t* skip) {
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= lt.G) return;
+  dev_elim0_res<N, NB>(lt, lb, p, in, x_hi, x_lo, rhs, skip, g, kTop);
+}
+
+// One whole solve pass in one launch, for plans whose systems fit a CTA at every level: the
+// CTA eliminates its systems' level-0 chunks (kSrc 0: factorise, 1: replay the stored factor
+// on rhs or beta, 2: replay on the refinement residual of x), then every upper level and the
+// back substitution down to level 0, with a block barrier between levels in place of a
+// launch.  The upper levels' few, short chunks run while the CTA's other warps wait, and
+// other CTAs of the SM, in other phases, keep its pipes and memory busy.
+template <class Tr, int NB, int kSrc, class N, int kMode>
+__global__ void __launch_bounds__(kThreads, 3) k_pass(const __grid_constant__ FusedLevels<Tr, NB> fl,
+                                                      Problem0 p, L0In<Tr> in, const Tr* rhs,
+                                                      const float* x_hi, const float* x_lo,
+                                                      Level0Out<Tr> o, int32_t* info,
+                                                      const int32_t* skip) {
+  const int32_t s0 = fl.cta_sys[blockIdx.x], s1 = fl.cta_sys[blockIdx.x + 1];
+  const int nl = fl.nl;
+  {
+    const LevelTables& lt = fl.lt[0];
+    const int64_t g = lt.coff[s0] + threadIdx.x;
+    if (g < lt.coff[s1]) {
+      if constexpr (kSrc == 2) {
+        dev_elim0_res<N, NB>(lt, fl.lb[0], p, in, x_hi, x_lo, rhs, skip, g, nl == 1);
+      } else {
+        if (!(skip && skip[lt.csys[g]]))
+          dev_elim0<Tr, NB, kSrc == 0>(lt, fl.lb[0], p, in, rhs, info, g, nl == 1);
+      }
+    }
+  }
+  for (int l = 1; l < nl; ++l) {
+    __syncthreads();
+    const LevelTables& lt = fl.lt[l];
+    const int64_t g = lt.coff[s0] + threadIdx.x;
+    if (g < lt.coff[s1])
+      dev_elimN<Tr, NB, kSrc == 0>(lt, fl.lb[l], fl.lb[l - 1].out, fl.T0, info, skip, g, l == nl - 1);
+  }
+  for (int l = nl - 1; l >= 1; --l) {
+    __syncthreads();
+    const LevelTables& lt = fl.lt[l];
+    const int64_t g = lt.coff[s0] + threadIdx.x;
+    if (g < lt.coff[s1]) dev_backsubN<Tr, NB>(lt, fl.lb[l], fl.lb[l - 1].out, fl.lb[l - 1].xsep, skip, g);
+  }
+  __syncthreads();
+  const LevelTables& lt = fl.lt[0];
+  const int64_t g = lt.coff[s0] + threadIdx.x;
+  if (g < lt.coff[s1]) dev_backsub0<Tr, NB, kMode>(lt, fl.lb[0], p, in, o, info, skip, g);
+}
+
+// Levels from..top of a solve pass in one launch, for plans whose level-0 chunks exceed a CTA:
+// the reduced systems of levels >= `from` fit a CTA per system, so the CTA eliminates them
+// level by level and back substitutes down to level `from`, leaving the values of level
+// from-1's separators; a barrier stands in for each launch of the per-level path.
+template <class Tr, int NB, bool kFactor>
+__global__ void __launch_bounds__(kThreads) k_upper(const __grid_constant__ FusedLevels<Tr, NB> fl,
+                                                    int32_t* info, const int32_t* skip) {
+  const int32_t s0 = fl.cta_sys[blockIdx.x], s1 = fl.cta_sys[blockIdx.x + 1];
+  const int nl = fl.nl;
+  for (int l = fl.from; l < nl; ++l) {
+    if (l > fl.from) __syncthreads();
+    const LevelTables& lt = fl.lt[l];
+    const int64_t g = lt.coff[s0] + threadIdx.x;
+    if (g < lt.coff[s1])
+      dev_elimN<Tr, NB, kFactor>(lt, fl.lb[l], fl.lb[l - 1].out, fl.T0, info, skip, g, l == nl - 1);
+  }
+  for (int l = nl - 1; l >= fl.from; --l) {
+    __syncthreads();
+    const LevelTables& lt = fl.lt[l];
+    const int64_t g = lt.coff[s0] + threadIdx.x;
+    if (g < lt.coff[s1]) dev_backsubN<Tr, NB>(lt, fl.lb[l], fl.lb[l - 1].out, fl.lb[l - 1].xsep, skip, g);
+  }
 }
 
 // ---- parameter gradients ----------------------------------------------------------------
@@ -779,6 +901,12 @@ struct smnn_plan_s {
   int32_t* d_sq_k = nullptr;
   int64_t Q = 0;
   std::vector<Level> lv;
+  bool fused = false;                  // one launch per solve pass (k_pass)
+  std::vector<int32_t> cta_sys;        // fused: first system of each CTA, [n_cta + 1]
+  int32_t* d_cta_sys = nullptr;
+  int up = 0;                          // > 0: levels up..top in one launch (k_upper)
+  std::vector<int32_t> up_sys;         //   first system of each of its CTAs
+  int32_t* d_up_sys = nullptr;
   size_t factor_bytes = 0, solve_bytes = 0;
   size_t o_fyh = 0, o_fyl = 0;         // factor region: the refined y, float-float (FP32 paths)
   size_t o_part = 0, o_prev = 0, o_skip = 0;  // refinement stop test (solve region), and:
@@ -871,6 +999,34 @@ smnn_status build_plan_host(smnn_plan_s* pl) {
     base = nb;
     stride0 *= L.L;
   }
+  // Fused launches: a level fits when every system's chunks there (and so at every higher
+  // level) number at most kThreads; consecutive systems are packed greedily into CTAs of up
+  // to kThreads chunks of that level.
+  auto fits = [&](const Level& L) {
+    for (int64_t i = 0; i < S; ++i)
+      if (L.coff[i + 1] - L.coff[i] > kThreads) return false;
+    return true;
+  };
+  auto pack = [&](const Level& L, std::vector<int32_t>& cta) {
+    cta.assign(1, 0);
+    for (int64_t i = 0; i < S; ++i)
+      if (L.coff[i + 1] - L.coff[cta.back()] > kThreads) cta.push_back(int32_t(i));
+    cta.push_back(int32_t(S));
+  };
+  pl->fused = false;
+  pl->cta_sys.clear();
+  pl->up = 0;
+  pl->up_sys.clear();
+  const bool want_fused = d.algo == SMNN_ALGO_CR_FUSED || d.algo == SMNN_ALGO_SEQ;
+  if (want_fused) {
+    if (!fits(pl->lv[0])) return SMNN_ERR_UNSUPPORTED;
+    pl->fused = true;
+    pack(pl->lv[0], pl->cta_sys);
+  } else if (d.algo == SMNN_ALGO_AUTO) {
+    for (int l = 1; l < int(pl->lv.size()) && !pl->up; ++l)
+      if (fits(pl->lv[l])) pl->up = l;
+    if (pl->up) pack(pl->lv[pl->up], pl->up_sys);
+  }
   size_t f = 0, s = 0;  // buffer layout
   for (auto& L : pl->lv) {
     const size_t GL = size_t(L.G) * size_t(L.L);
@@ -930,6 +1086,7 @@ smnn_status build_plan_host(smnn_plan_s* pl) {
   size_t tb = 0;  // every index table, packed into one blob (one device allocation)
   for (auto& L : pl->lv) tb += align_up(L.G * 4) + align_up((S + 1) * 8) + 2 * align_up(S * 8);
   tb += 3 * align_up(S * 8) + 2 * align_up(pl->B * 8) + 2 * align_up(pl->Q * 4);
+  tb += align_up(pl->cta_sys.size() * 4) + align_up(pl->up_sys.size() * 4);
   pl->table_blob.assign(tb, 0);
   pl->table_binds.clear();
   size_t off = 0;
@@ -953,6 +1110,8 @@ smnn_status build_plan_host(smnn_plan_s* pl) {
   put(pl->seq_T.data(), pl->B * 8, &pl->d_seq_T);
   put(sq_b.data(), pl->Q * 4, &pl->d_sq_b);
   put(sq_k.data(), pl->Q * 4, &pl->d_sq_k);
+  put(pl->cta_sys.data(), pl->cta_sys.size() * 4, &pl->d_cta_sys);
+  put(pl->up_sys.data(), pl->up_sys.size() * 4, &pl->d_up_sys);
   return SMNN_OK;
 }
 
@@ -1026,12 +1185,58 @@ struct ResIn {  // refinement sweep: residual of x (float-float) against rhs (or
   const float* rhs;
 };
 
+template <class Tr, int NB>
+FusedLevels<Tr, NB> fused_levels(const smnn_plan_s* pl, char* fac, char* sol, int from = 0) {
+  FusedLevels<Tr, NB> fl{};
+  fl.nl = int(pl->lv.size());
+  fl.from = from;
+  fl.cta_sys = from ? pl->d_up_sys : pl->d_cta_sys;
+  fl.T0 = pl->d_sys_T;
+  for (int l = 0; l < fl.nl; ++l) {
+    fl.lt[l] = tables_of(pl->lv[l]);
+    fl.lb[l] = bufs_of<Tr, NB>(pl->lv[l], fac, sol);
+  }
+  return fl;
+}
+
+// solve_pass of a fused plan: one k_pass launch, one CTA per entry of the CTA table.
+template <class Tr, int NB, class N>
+smnn_status fused_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, bool factor,
+                       char* fac, char* sol, const Level0Out<Tr>& out, int mode, int32_t* info,
+                       cudaStream_t st, const ResIn* res, const int32_t* skip) {
+  const FusedLevels<Tr, NB> fl = fused_levels<Tr, NB>(pl, fac, sol);
+  const L0In<Tr> in = l0_in<Tr>(pl, fac);
+  const int64_t n = int64_t(pl->cta_sys.size() - 1) * kThreads;
+  if constexpr (std::is_same<Tr, float>::value) {
+    if (res) {
+      if (mode != 2) return SMNN_ERR_INVALID_ARG;
+      SMNN_LAUNCH_AS("k_pass[res]", (k_pass<float, NB, 2, N, 2>), n, st, fl, p, in, res->rhs, res->xh,
+                     res->xl, out, info, skip);
+      return SMNN_OK;
+    }
+    if (mode == 1) {
+      if (factor) SMNN_LAUNCH_AS("k_pass[factor]", (k_pass<float, NB, 0, double, 1>), n, st, fl, p, in, rhs,
+                                 nullptr, nullptr, out, info, skip);
+      else SMNN_LAUNCH_AS("k_pass[rhs]", (k_pass<float, NB, 1, double, 1>), n, st, fl, p, in, rhs,
+                          nullptr, nullptr, out, info, skip);
+      return SMNN_OK;
+    }
+  }
+  if (res || mode != 0) return SMNN_ERR_INVALID_ARG;
+  if (factor) SMNN_LAUNCH_AS("k_pass[factor]", (k_pass<Tr, NB, 0, double, 0>), n, st, fl, p, in, rhs,
+                             nullptr, nullptr, out, info, skip);
+  else SMNN_LAUNCH_AS("k_pass[rhs]", (k_pass<Tr, NB, 1, double, 0>), n, st, fl, p, in, rhs, nullptr,
+                      nullptr, out, info, skip);
+  return SMNN_OK;
+}
+
 template <class Tr, int NB, class N = double>
 smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, bool factor,
                        char* fac, char* sol, const Level0Out<Tr>& out, int mode, int32_t* info,
                        cudaStream_t st, const ResIn* res = nullptr, const int32_t* skip = nullptr) {
   const int nl = int(pl->lv.size());
   const L0In<Tr> in = l0_in<Tr>(pl, fac);
+  if (pl->fused) return fused_pass<Tr, NB, N>(pl, p, rhs, factor, fac, sol, out, mode, info, st, res, skip);
   for (int l = 0; l < nl; ++l) {
     const Level& L = pl->lv[l];
     const LevelTables lt = tables_of(L);
@@ -1043,6 +1248,13 @@ smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, 
         else SMNN_LAUNCH((k_elim0_res<N, NB, false>), L.G, st, lt, lb, p, in, res->xh, res->xl, res->rhs, skip);
         continue;
       }
+    }
+    if (l > 0 && l == pl->up) {
+      const FusedLevels<Tr, NB> fl = fused_levels<Tr, NB>(pl, fac, sol, l);
+      const int64_t n = int64_t(pl->up_sys.size() - 1) * kThreads;
+      if (factor) SMNN_LAUNCH_AS("k_upper[factor]", (k_upper<Tr, NB, true>), n, st, fl, info, nullptr);
+      else SMNN_LAUNCH((k_upper<Tr, NB, false>), n, st, fl, info, skip);
+      break;
     }
     if (l == 0) {
       if (factor && top) SMNN_LAUNCH_AS("k_elim0[factor]", (k_elim0<Tr, NB, true, true>), L.G, st, lt, lb, p, in, rhs, info);
@@ -1057,7 +1269,7 @@ smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, 
       else SMNN_LAUNCH((k_elimN<Tr, NB, false, false>), L.G, st, lt, lb, prev, pl->d_sys_T, info, skip);
     }
   }
-  for (int l = nl - 1; l >= 1; --l) {
+  for (int l = (pl->up ? pl->up - 1 : nl - 1); l >= 1; --l) {
     const Level& L = pl->lv[l];
     const LevelBufs<Tr, NB> lb = bufs_of<Tr, NB>(L, fac, sol);
     const LevelBufs<Tr, NB> pb = bufs_of<Tr, NB>(pl->lv[l - 1], fac, sol);
@@ -1348,7 +1560,7 @@ smnn_status plan_init(const smnn_desc* desc, smnn_plan_s* pl) {
   const smnn_desc& d = *desc;
   if (d.R < 1 || d.R > SMNN_MAX_R || d.R_init < 0 || d.R_init > d.R || d.T_init < 1) return SMNN_ERR_INVALID_ARG;
   if (d.precision < SMNN_F32_REFINED || d.precision > SMNN_F32_REFINED_DF) return SMNN_ERR_INVALID_ARG;
-  if (d.algo < SMNN_ALGO_AUTO || d.algo > SMNN_ALGO_CR) return SMNN_ERR_INVALID_ARG;
+  if (d.algo < SMNN_ALGO_AUTO || d.algo > SMNN_ALGO_CR_FUSED) return SMNN_ERR_INVALID_ARG;
   if (d.max_refine < 0 || d.max_refine > 16 || d.adjoint_refine < 0 || d.adjoint_refine > 16 ||
       d.chunk < 0 || d.chunk == 1)
     return SMNN_ERR_INVALID_ARG;
@@ -1431,7 +1643,7 @@ smnn_status smnn_plan_get_stats(smnn_plan plan, smnn_plan_stats* st) {
   st->total_steps = plan->N0;
   st->num_levels = int32_t(plan->lv.size());
   for (size_t l = 0; l < plan->lv.size() && l < 8; ++l) st->chunk[l] = plan->lv[l].L;
-  st->kernels_per_solve = int32_t(2 * plan->lv.size());
+  st->kernels_per_solve = plan->fused ? 1 : plan->up ? 2 * plan->up + 1 : int32_t(2 * plan->lv.size());
   st->workspace_bytes = plan->factor_bytes + plan->solve_bytes;
   st->factor_bytes = plan->factor_bytes;
   return SMNN_OK;

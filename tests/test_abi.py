@@ -62,3 +62,13 @@ def test_ragged_seq_T_validation():
                ctypes.cast(seq, ctypes.POINTER(ctypes.c_int64)))
     h = ctypes.c_void_p()
     assert B.lib.smnn_plan_create(ctypes.byref(d), ctypes.byref(h)) == B.SMNN_ERR_INVALID_ARG
+
+
+def test_fused_pass_needs_every_system_within_one_cta():
+    """SMNN_ALGO_CR_FUSED runs all levels of a system in one CTA (128 level-0 chunks at
+    most); a longer system is refused at plan creation, before any device call."""
+    from paper_2410_06074_b300 import binding as B
+    d = B.Desc(2, 1, 1, B.F32_REFINED, B.ALGO_CR_FUSED, 2, 8, 0, 1.0, 1.0, 1.0, 0.0, 2, 2, 8 * 129, None)
+    h = ctypes.c_void_p()
+    assert B.lib.smnn_plan_create(ctypes.byref(d), ctypes.byref(h)) == B.SMNN_ERR_UNSUPPORTED
+    assert not h.value

@@ -62,6 +62,26 @@ def test_refined_fp32_forward(T, algo, chunk, prec):
     assert rel_err_per_system(y, yo, prob).max() <= TOL_REF
 
 
+@pytest.mark.parametrize("prec", ["F64", "F32", "F32_REFINED", "F32_REFINED_DF"])
+@pytest.mark.parametrize("seq_T,D,chunk", [([1024] * 3, 4, 32), ([4099] * 2, 3, 64),
+                                           ([1, 2, 3, 5, 64, 65, 1000, 3001], 2, 32),
+                                           ([200, 17, 500], 2, 0)])
+def test_fused_pass_equals_per_level_launches(seq_T, D, chunk, prec):
+    """One launch per solve pass (a CTA runs every level of its systems), or one launch for
+    the levels whose systems fit a CTA, performs the same operations in the same order as
+    one launch per level: the outputs agree bit for bit, forward and adjoint."""
+    pk = P()
+    prob = ragged_problem(seq_T, D=D, seed=21)
+    gy = upstream_gradient(prob)
+    p = getattr(pk, prec)
+    split = gpu_grad(prob, gy, p, algo=pk.ALGO_CR, chunk=chunk)
+    for algo in (pk.ALGO_CR_FUSED, pk.ALGO_AUTO):   # one launch per pass; per level below
+        fused = gpu_grad(prob, gy, p, algo=algo, chunk=chunk)   # a CTA's size
+        for a, b in zip(fused, split):
+            np.testing.assert_array_equal(a, b)
+        assert (fused[-2] == 0).all() and (fused[-1] == 0).all()
+
+
 @pytest.mark.parametrize("T,chunk", [(1000, 0), (2500, 16)])
 def test_fp64_forward(T, chunk):
     pk = P()
