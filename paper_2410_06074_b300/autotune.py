@@ -2,7 +2,9 @@
 
 For a batch shape (R, number of systems, steps per system) and precision it times the
 candidates -- one sequential block-Cholesky sweep per system (SMNN_ALGO_SEQ, Alg. 3/4 as
-written) and the chunked cyclic reduction with level-0 chunks of 8, 16, 32 or 64 steps --
+written), the chunked cyclic reduction with level-0 chunks of 8, 16, 32 or 64 steps, and the
+same reduction in one launch per solve pass (SMNN_ALGO_CR_FUSED, where every system fits a
+CTA; the plan is refused otherwise) --
 on the caller's inputs, forward + adjoint, after checking that each candidate reproduces the
 default plan's solution (so no candidate is ever picked for speed alone).  Winners are kept in
 ``autotune_table.json`` next to this file, keyed by R, precision and power-of-two buckets of the
@@ -25,7 +27,8 @@ TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_table
 _lock = threading.Lock()
 _table = None
 
-CANDIDATES = [(B.ALGO_SEQ, 0), (B.ALGO_CR, 8), (B.ALGO_CR, 16), (B.ALGO_CR, 32), (B.ALGO_CR, 64)]
+CANDIDATES = [(B.ALGO_SEQ, 0)] + [(B.ALGO_AUTO, L) for L in (8, 16, 32, 64)] + \
+    [(B.ALGO_CR_FUSED, L) for L in (16, 32, 64)]
 
 
 def _bucket(x: float) -> int:

@@ -273,8 +273,11 @@ __device__ __forceinline__ void dev_elim0(const LevelTables& lt, const LevelBufs
   if (kFactor && fail) record_fail(info + cp.i, int32_t(fail));
 }
 
+#ifndef SMNN_FACTOR_MIN_BLOCKS
+#define SMNN_FACTOR_MIN_BLOCKS 4   // factor pass: 4 CTAs per SM (128 registers) beat 3 (168)
+#endif
 template <class Tr, int NB, bool kFactor, bool kTop>
-__global__ void __launch_bounds__(kThreads, kFactor ? 3 : 4) k_elim0(LevelTables lt, LevelBufs<Tr, NB> lb, Problem0 p,
+__global__ void __launch_bounds__(kThreads, kFactor ? SMNN_FACTOR_MIN_BLOCKS : 4) k_elim0(LevelTables lt, LevelBufs<Tr, NB> lb, Problem0 p,
                                                     L0In<Tr> in, const Tr* rhs, int32_t* info) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
@@ -485,33 +488,71 @@ __device__ __forceinline__ void taylor_coefs(Ts s, N (&cp)[NB], N (&cm)[NB]) {
   }
 }
 
+// v / k! in number type N: exact scalings for k <= 2, a float-float (or FP64) constant for k = 3.
+template <class N> __device__ __forceinline__ N half_n(const N& v);
+template <> __device__ __forceinline__ double half_n<double>(const double& v) { return 0.5 * v; }
+template <> __device__ __forceinline__ ff half_n<ff>(const ff& v) {
+  return ff{__fmul_rn(0.5f, v.hi), __fmul_rn(0.5f, v.lo)};
+}
+template <class N> __device__ __forceinline__ N over_fact(const N& v, int k) {
+  return k <= 1 ? v : (k == 2 ? half_n<N>(v) : v * inv_fact_n<N>(k));
+}
+
 // Contributions of the 2(R+1) smoothness rows between steps t and t+1 (Eq. 6-7, weights
-// w_r = w_s^2 s^{2r}) to -(M x)_t and -(M x)_{t+1}: with e+ = exp(sN) x_t - x_{t+1} and
-// e- = exp(-sN) x_{t+1} - x_t (the rows' values),
-//   -(M x)_t     += w.e- - exp(sN)^T (w.e+),   -(M x)_{t+1} += w.e+ - exp(-sN)^T (w.e-).
+// w_r = w_s^2 s^{2r}) to -(M x)_t and -(M x)_{t+1}.  With P = diag(s^r), D = diag((-1)^r) and
+// F_ij = 1/(j-i)! (App. A.2), the rows' Taylor maps factor as exp(sN) = P^-1 F P and
+// exp(-sN) = P^-1 D F D P, and W = w_s^2 P^2.  So with x~ = P x_t, x^ = P x_{t+1},
+//   f = F x~ - x^ (so the forward rows are e+ = P^-1 f),  h = F D x^ - D x~ (e- = P^-1 D h),
+//   -(M x)_t     += W e- - exp(sN)^T W e+   = w_s^2 P (D h - F^T f),
+//   -(M x)_{t+1} += W e+ - exp(-sN)^T W e-  = w_s^2 P (f - D F^T h),
+// where F and F^T carry only the constants 1/k! (exact for k <= 2), so the inner work is
+// additions; P is applied twice per vector.
 template <class N, int NB>
 __device__ __forceinline__ void smooth_pair_residual(float s, N ws2, const N (&xa)[NB],
                                                      const N (&xb)[NB], N (&ra)[NB], N (&rb)[NB]) {
-  N cp[NB], cm[NB], w[NB];
-  taylor_coefs<N, NB, float>(s, cp, cm);
-  w[0] = ws2;
-  const N s2 = Num<N>::from_f(s) * s;
+  N sp[NB];   // s^r, r >= 2
+  N xt[NB], xh[NB];
+  xt[0] = xa[0];
+  xh[0] = xb[0];
 #pragma unroll
-  for (int r = 1; r < NB; ++r) w[r] = w[r - 1] * s2;
-  N pa[NB], qb[NB], vp[NB], vm[NB], tp[NB], tm[NB];
-  taylor_fw<N, NB>(cp, xa, pa);
-  taylor_fw<N, NB>(cm, xb, qb);
-#pragma unroll
-  for (int r = 0; r < NB; ++r) {
-    vp[r] = w[r] * (pa[r] - xb[r]);
-    vm[r] = w[r] * (qb[r] - xa[r]);
+  for (int r = 1; r < NB; ++r) {
+    if (r == 2) sp[2] = Num<N>::from_f(s) * s;
+    if (r > 2) sp[r] = sp[r - 1] * s;
+    xt[r] = r == 1 ? xa[1] * s : xa[r] * sp[r];
+    xh[r] = r == 1 ? xb[1] * s : xb[r] * sp[r];
   }
-  taylor_tr<N, NB>(cp, vp, tp);
-  taylor_tr<N, NB>(cm, vm, tm);
+  N f[NB], h[NB];
 #pragma unroll
   for (int r = 0; r < NB; ++r) {
-    ra[r] = vm[r] - tp[r];
-    rb[r] = vp[r] - tm[r];
+    N af = xt[r], ah = (r & 1) ? -xh[r] : xh[r];
+#pragma unroll
+    for (int k = 1; r + k < NB; ++k) {
+      af = af + over_fact<N>(xt[r + k], k);
+      const N v = over_fact<N>(xh[r + k], k);
+      ah = ((r + k) & 1) ? ah - v : ah + v;
+    }
+    f[r] = af - xh[r];
+    h[r] = (r & 1) ? ah + xt[r] : ah - xt[r];
+  }
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    N tf = f[r], th = h[r];   // (F^T f)_r, (F^T h)_r
+#pragma unroll
+    for (int k = 1; k <= r; ++k) {
+      tf = tf + over_fact<N>(f[r - k], k);
+      th = th + over_fact<N>(h[r - k], k);
+    }
+    N ut = (r & 1) ? -(h[r] + tf) : h[r] - tf;
+    N un = (r & 1) ? f[r] + th : f[r] - th;
+    if (r == 1) {
+      ut = ut * s;
+      un = un * s;
+    } else if (r > 1) {
+      ut = ut * sp[r];
+      un = un * sp[r];
+    }
+    ra[r] = ws2 * ut;
+    rb[r] = ws2 * un;
   }
 }
 

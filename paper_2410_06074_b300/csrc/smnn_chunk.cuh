@@ -361,7 +361,10 @@ struct CoefSource {
   // E_t = N_t = block (t+1, t), t < T-1; its raw data is the step size s_t
   using ERaw = Tr;
   SMNN_HD ERaw load_e(int64_t t) const { return s[at(t)]; }
-  SMNN_HD void E(int64_t t, Tr (&e)[NB][NB]) const { e_from(load_e(t), e); }
+  // s_t is staged with step t (as s) and with step t+1 (as its previous step size)
+  SMNN_HD void E(int64_t t, Tr (&e)[NB][NB]) const {
+    e_from(t + 1 == cur_t ? cur.sp : (t == cur_t ? cur.s : load_e(t)), e);
+  }
   SMNN_HD void e_from(ERaw st, Tr (&e)[NB][NB]) const {
     Tr pw[2 * NB - 1];
     pw[0] = Tr(1);
