@@ -180,9 +180,16 @@ def residual_ops(NB: int, explicit_rhs: bool, df: bool) -> float:
     ff+float 10, ff+ff 11 FP32 instructions; in FP64 every operation is one instruction."""
     n = NB
     mf, mm, af, aa = (6, 7, 10, 11) if df else (1, 1, 1, 1)
+    half = 2 if df else 1                                # v/2: two exact scalings
     gov = n * (mf + aa) + (mm + n * (mf + af + aa) if explicit_rhs else (af + mm) + n * (mf + aa))
-    tay = n * (n - 1) // 2 * (mm + aa)                  # one exp(+-sN) product
-    pair = (n - 1) * (mf + mf) + mf + (n - 1) * mm + 4 * tay + 2 * n * (aa + mm) + 2 * n * aa
+    # smoothness pair in the P F P form: powers s^r, x~ = P x_t and x^ = P x_{t+1}; f, h
+    # (F x - ..., n(n-1)/2 additions each plus n subtractions); F^T f, F^T h; D h - F^T f and
+    # f - D F^T h; times P and w_s^2.  v/k! costs `half` for k = 2 and a product for k = 3.
+    scal = 2 * ((n - 2) * half + max(n - 3, 0) * mm)     # the 1/k! factors of two vectors
+    pair = (max(n - 2, 0) * mf + 2 * (mf + (n - 2) * mm)
+            + 2 * (n * (n - 1) // 2 * aa) + 2 * n * aa + scal
+            + 2 * (n * (n - 1) // 2 * aa) + scal
+            + 2 * n * aa + 2 * (mf + (n - 2) * mm) + 2 * n * mm)
     return float(gov + pair + n * aa + n)
 
 

@@ -809,6 +809,41 @@ __device__ __forceinline__ N smooth_pair_grad(Ts s, N ws2, const N (&ya)[NB], co
   return -(ws2 * acc);
 }
 
+// The same for FP32 outputs: only the four row values e+, f+, e-, f- (differences of nearly
+// equal Taylor-propagated states, where y and g are float-float or FP64) need N; they and
+// the propagated states are then rounded to FP32 and the product rule is summed in FP32,
+// which leaves errors of a few FP32 roundings relative to the largest term.
+template <class N, int NB>
+__device__ __forceinline__ float smooth_pair_grad_f32(float s, float ws2, const N (&ya)[NB],
+                                                      const N (&yb)[NB], const N (&ga)[NB],
+                                                      const N (&gb)[NB]) {
+  N cp[NB], cm[NB];
+  taylor_coefs<N, NB, float>(s, cp, cm);
+  N pya[NB], pga[NB], qyb[NB], qgb[NB];
+  taylor_fw<N, NB>(cp, ya, pya);
+  taylor_fw<N, NB>(cp, ga, pga);
+  taylor_fw<N, NB>(cm, yb, qyb);
+  taylor_fw<N, NB>(cm, gb, qgb);
+  float acc = 0.f;
+  float s2r = 1.f, ds2r = 0.f;   // s^{2r}, 2r s^{2r-1}
+  const float s2 = s * s;
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    const float ep = Num<N>::to_f(pya[r] - yb[r]), fp = Num<N>::to_f(pga[r] - gb[r]);
+    const float em = Num<N>::to_f(qyb[r] - ya[r]), fm = Num<N>::to_f(qgb[r] - ga[r]);
+    float inner = 0.f;
+    if (r + 1 < NB) {
+      const float a1 = Num<N>::to_f(pga[r + 1]), b1 = Num<N>::to_f(pya[r + 1]);
+      const float c1 = Num<N>::to_f(qgb[r + 1]), d1 = Num<N>::to_f(qyb[r + 1]);
+      inner = fmaf(a1, ep, fp * b1) - fmaf(c1, em, fm * d1);
+    }
+    acc = fmaf(ds2r, fmaf(fp, ep, fm * em), fmaf(s2r, inner, acc));
+    ds2r = s2r * s * float(2 * r + 2);
+    s2r = s2r * s2;
+  }
+  return -(ws2 * acc);
+}
+
 // One thread per level-0 chunk of one system: gc, gd (interleaved), this system's share of
 // gs (interleaved; the D systems of a sequence are summed in k_scatter_gs) and gu.
 template <class Tr, class N, int NB>
@@ -830,6 +865,8 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
     ya[a] = ld_pair<N>(y_hi, y_lo, a * es + k);
     ga[a] = ld_pair<N>(g_hi, g_lo, a * es + k);
   }
+  constexpr bool kF32 = std::is_same<Tr, float>::value;
+  const float wg2f = float(p.wg2), ws2f = float(p.ws2);
   for (int64_t t = cp.first; t <= cp.last; ++t) {
     N cy = Num<N>::zero(), cg = Num<N>::zero();
 #pragma unroll
@@ -839,10 +876,20 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
       cg = cg + cv * ga[a];
     }
     const N e = ld_n<N>(in.d[k]) - cy;
+    if constexpr (kF32) {
+      // e = d - c.y and c.g cancel and need N; the rest is FP32
+      const float ef = Num<N>::to_f(e), cgf = Num<N>::to_f(cg);
 #pragma unroll
-    for (int a = 0; a < NB; ++a)
-      gc[a * es + k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * (e * ga[a] - cg * ya[a]));
-    gd[k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * cg);
+      for (int a = 0; a < NB; ++a)
+        gc[a * es + k] = failed ? nan_t<Tr>()
+                                : wg2f * fmaf(ef, Num<N>::to_f(ga[a]), -(cgf * Num<N>::to_f(ya[a])));
+      gd[k] = failed ? nan_t<Tr>() : wg2f * cgf;
+    } else {
+#pragma unroll
+      for (int a = 0; a < NB; ++a)
+        gc[a * es + k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * (e * ga[a] - cg * ya[a]));
+      gd[k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * cg);
+    }
     if (t < p.T_init) {
       for (int a = 0; a <= p.R_init; ++a)
         gu[cp.i * nu + t * (p.R_init + 1) + a] = failed ? nan_t<Tr>() : st_n<Tr, N>(wi2 * ga[a]);
@@ -856,7 +903,8 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
         yb[a] = ld_pair<N>(y_hi, y_lo, a * es + kn);
         gb[a] = ld_pair<N>(g_hi, g_lo, a * es + kn);
       }
-      gsum = smooth_pair_grad<N, NB, Tr>(in.s[k], ws2, ya, yb, ga, gb);
+      if constexpr (kF32) gsum = Num<N>::from_f(smooth_pair_grad_f32<N, NB>(in.s[k], ws2f, ya, yb, ga, gb));
+      else gsum = smooth_pair_grad<N, NB, Tr>(in.s[k], ws2, ya, yb, ga, gb);
 #pragma unroll
       for (int a = 0; a < NB; ++a) { ya[a] = yb[a]; ga[a] = gb[a]; }
     }
