@@ -173,6 +173,12 @@ FP32_PEAK_TOPS = 148 * 128 * 2.032e9 / 1e12
 FP64_PEAK_TOPS = 148 * 2 * 2.032e9 / 1e12
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch on this workload, from the ncu
+# capture summarised in the named file (to be re-taken whenever the kernel changes)
+NCU_TRAFFIC = {"k_elim0_res": (435.530240e6 + 48.868352e6, "profiles/k_elim0_res_config2.md"),
+               "k_backsub0": (411.675648e6 + 86.956800e6, "profiles/k_backsub0_config2.md")}
+
+
 def residual_ops(NB: int, explicit_rhs: bool, df: bool) -> float:
     """Arithmetic instructions per time-step of the refinement residual r = rhs - M x
     (governing row, 2(R+1) smoothness rows, accumulation), counted from the formulas in
@@ -366,7 +372,10 @@ def e2e_and_roofline(prob, v, res, ws, args, stream, flush):
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                 "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"}
-    roof.update({"traffic": None, "per_step": per_step, "per_step_unit": unit,
+    tr = NCU_TRAFFIC.get(name)
+    roof.update({"traffic": tr[0] if tr else None, "traffic_unit": "B per launch",
+                 "traffic_source": tr[1] if tr else None,
+                 "per_step": per_step, "per_step_unit": unit,
                  "launch_ms": per_launch_ms,
                  "share": tms / max(sum(x[1] for x in prof.values()), 1e-9)})
     step_bytes = (16 * NB + 8 + 8.0 / D + 8 * NB + 4 + 4.0 / D)
