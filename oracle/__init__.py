@@ -84,7 +84,7 @@ def _load():
                                         _i32, ctypes.c_int]
         lib.orc_grad_batch.restype = ctypes.c_int
         lib.orc_grad_batch.argtypes = [pp, ctypes.c_int64, _i64, _i64, _i64, _d, _d, _d, _d, _d, _d,
-                                       _d, _d, _d, _d, _d, _i32, ctypes.c_int]
+                                       _d, _d, _d, _d, _d, _d, _i32, ctypes.c_int]
         lib.orc_solve_dense_batch.restype = ctypes.c_int
         lib.orc_solve_dense_batch.argtypes = [pp, ctypes.c_int64, _i64, _i64, _i64, _d, _d, _d, _d,
                                               _d, _i32, ctypes.c_int]
@@ -197,18 +197,27 @@ def solve(p: Params, c, d, s, u, *, D: int | None = None, seq_T=None, mode: str 
     return y, info
 
 
-def gradient(p: Params, c, d, s, u, gy, *, D: int | None = None, seq_T=None, nthreads: int = 0):
-    """(y, gc, gd, gs, gu, info) for dl/dy = gy (Eq. 14 chain rule, App. A.3)."""
+def gradient(p: Params, c, d, s, u, gy, *, D: int | None = None, seq_T=None, nthreads: int = 0,
+             weights: bool = False):
+    """(y, gc, gd, gs, gu, info) for dl/dy = gy (Eq. 14 chain rule, App. A.3).  With
+    weights=True, (y, gc, gd, gs, gu, gw, info): gw [3] = dl/d(w_gov, w_init, w_smooth),
+    the importance weights being shared by every system of the batch (summed in order)."""
     c, d, s, u, gy = _f64(c), _f64(d), _f64(s), _f64(u), _f64(gy)
     L = _layout(c, D, seq_T)
     y = np.zeros_like(c); gc = np.zeros_like(c); gd = np.zeros_like(d)
     gs = np.zeros_like(s); gu = np.zeros_like(u); gs_sys = np.zeros_like(d)
+    gw_sys = np.zeros((L.S, 3))
     info = np.zeros(L.S, np.int32)
     rc = _load().orc_grad_batch(ctypes.byref(p.c()), L.S, _ptr(L.T_sys, ctypes.c_int64),
                                 _ptr(L.off, ctypes.c_int64), _ptr(L.soff, ctypes.c_int64),
                                 _ptr(c), _ptr(d), _ptr(s), _ptr(u), _ptr(gy), _ptr(y), _ptr(gc),
-                                _ptr(gd), _ptr(gs), _ptr(gu), _ptr(gs_sys),
+                                _ptr(gd), _ptr(gs), _ptr(gu), _ptr(gs_sys), _ptr(gw_sys),
                                 _ptr(info, ctypes.c_int32), int(nthreads))
     if rc != 0:
         raise ValueError("oracle rejected the parameters")
+    if weights:
+        gw = np.zeros(3)
+        for i in range(L.S):
+            gw += gw_sys[i]
+        return y, gc, gd, gs, gu, gw, info
     return y, gc, gd, gs, gu, info

@@ -75,6 +75,7 @@ typedef struct {
   double val[ORC_MAX_NZ];
   double dval_ds[ORC_MAX_NZ];
   double b, w, dw_ds;
+  double dw_dimp;  /* d w / d (the row's importance weight w_gov, w_init or w_smooth) */
 } orc_row;
 
 static double orc_factorial(int k) {
@@ -113,6 +114,7 @@ void orc_build_rows(const orc_params* p, int64_t T, const double* c, const doubl
     }
     w->b = d[t];
     w->w = p->w_gov * p->w_gov;
+    w->dw_dimp = 2.0 * p->w_gov;
   }
 
   /* Eq. 5: y_{t,r} = u_{t,r} for t < T_init, r <= R_init, weight w_init^2. */
@@ -124,6 +126,7 @@ void orc_build_rows(const orc_params* p, int64_t T, const double* c, const doubl
       w->val[0] = 1.0;
       w->b = u[t * (p->R_init + 1) + r];
       w->w = p->w_init * p->w_init;
+      w->dw_dimp = 2.0 * p->w_init;
     }
   }
 
@@ -148,6 +151,7 @@ void orc_build_rows(const orc_params* p, int64_t T, const double* c, const doubl
       w->b = 0.0;
       w->w = orc_powi(p->w_smooth * orc_powi(st, r), 2);
       w->dw_ds = r > 0 ? 2.0 * r * p->w_smooth * p->w_smooth * orc_powi(st, 2 * r - 1) : 0.0;
+      w->dw_dimp = 2.0 * p->w_smooth * orc_powi(st, 2 * r);
     }
   }
 
@@ -173,6 +177,7 @@ void orc_build_rows(const orc_params* p, int64_t T, const double* c, const doubl
       w->b = 0.0;
       w->w = orc_powi(p->w_smooth * orc_powi(st, r), 2);
       w->dw_ds = r > 0 ? 2.0 * r * p->w_smooth * p->w_smooth * orc_powi(st, 2 * r - 1) : 0.0;
+      w->dw_dimp = 2.0 * p->w_smooth * orc_powi(st, 2 * r);
     }
   }
 }
@@ -391,7 +396,7 @@ static int orc_solve_one_band(const orc_params* p, int64_t T, const double* c, c
  * share; the last entry is 0), gu [T_init][R_init+1]. */
 static int orc_grad_one(const orc_params* p, int64_t T, const double* c, const double* d,
                         const double* s, const double* u, const double* gy, double* y,
-                        double* gc, double* gd, double* gs, double* gu) {
+                        double* gc, double* gd, double* gs, double* gu, double* gw) {
   const int nb = p->R + 1;
   const int64_t m = orc_num_rows(p, T), n = T * nb;
   const int kd = orc_band_width(p);
@@ -405,6 +410,7 @@ static int orc_grad_one(const orc_params* p, int64_t T, const double* c, const d
   memset(gd, 0, sizeof(double) * (size_t)T);
   memset(gs, 0, sizeof(double) * (size_t)T);
   memset(gu, 0, sizeof(double) * (size_t)(p->T_init * (p->R_init + 1)));
+  gw[0] = gw[1] = gw[2] = 0.0;
   if (info == 0) {
     orc_band_solve(n, kd, band, y);                   /* y = M^{-1} beta    */
     memcpy(g, gy, sizeof(double) * (size_t)n);
@@ -419,6 +425,8 @@ static int orc_grad_one(const orc_params* p, int64_t T, const double* c, const d
         dag += w->dval_ds[j] * g[w->col[j]];
       }
       const double e = w->b - ay;
+      /* theta = the row's importance weight: da = db = 0, dw = dw_dimp (App. A.1's W). */
+      gw[w->kind == ROW_GOV ? 0 : (w->kind == ROW_INIT ? 1 : 2)] += ag * w->dw_dimp * e;
       if (w->kind == ROW_GOV) {
         /* theta = c_{t,r}: da = unit vector at column (t,r); dw = db = 0.
          * theta = d_t:     db = 1. */
@@ -470,7 +478,8 @@ int orc_solve_batch(const orc_params* p, int64_t S, const int64_t* T_sys, const 
 int orc_grad_batch(const orc_params* p, int64_t S, const int64_t* T_sys, const int64_t* off,
                    const int64_t* soff, const double* c, const double* d, const double* s,
                    const double* u, const double* gy, double* y, double* gc, double* gd,
-                   double* gs, double* gu, double* gs_sys, int32_t* info, int nthreads) {
+                   double* gs, double* gu, double* gs_sys, double* gw_sys, int32_t* info,
+                   int nthreads) {
   const int nb = p->R + 1;
   const int nu = p->T_init * (p->R_init + 1);
   if (p->R < 0 || p->R > ORC_MAX_R || p->R_init < 0 || p->R_init > p->R || p->T_init < 1) return -1;
@@ -481,7 +490,7 @@ int orc_grad_batch(const orc_params* p, int64_t S, const int64_t* T_sys, const i
   for (int64_t i = 0; i < S; ++i) {
     const int r = orc_grad_one(p, T_sys[i], c + off[i] * nb, d + off[i], s + soff[i], u + i * nu,
                                gy + off[i] * nb, y + off[i] * nb, gc + off[i] * nb, gd + off[i],
-                               gs_sys + off[i], gu + i * nu);
+                               gs_sys + off[i], gu + i * nu, gw_sys + 3 * i);
     info[i] = r == 0 ? 0 : (int32_t)((r - 1) / nb + 1);
   }
   /* chain rule for the shared step sizes: sum the systems' shares in order */

@@ -30,7 +30,8 @@ from dataclasses import dataclass, field, replace
 import numpy as np
 
 __all__ = ["Problem", "config1", "config2", "config2_slice", "config3", "config3b", "config4",
-           "config5", "random_problem", "upstream_gradient", "mse_target", "CONFIGS"]
+           "config5", "random_problem", "upstream_gradient", "mse_target", "CONFIGS",
+           "table5_odes", "table5_batch", "ODE_T", "ODE_H"]
 
 
 @dataclass
@@ -196,3 +197,71 @@ def mse_target(prob: Problem, seed: int = 1) -> np.ndarray:
 
 CONFIGS = {"config1": config1, "config2": config2, "config3": config3, "config3b": config3b,
            "config4": config4, "config5": config5}
+
+
+# ----------------------------------------------------------------------------- App. B.1 ODEs
+
+ODE_T, ODE_H = 1000, 0.01   # Sec. 5.1 standalone setting: 1000 steps of 0.01
+
+
+def table5_odes(T: int = ODE_T, h: float = ODE_H) -> list[dict]:
+    """The six linear ODEs of App. B.1 with their closed-form solutions (Table 5's cases).
+
+    Each case: name, order R of the solve (R = 2 for the first-order ODEs, whose Table 5
+    columns include y''; R = 3 for the second- and third-order ones, the largest order the
+    GPU path supports), R_init, coefficients c_0..c_R of sum_r c_r y^(r) = rhs, rhs, initial
+    values u (orders 0..R_init at t = 0), and ``exact`` = [y, y', y''] on t_k = k h."""
+    t = np.arange(T) * h
+    out = []
+    c0, c1, c2, u0 = 0.7, 1.2, 2.31, 10.0                 # RC circuit: y/c1 + c2 y' = c0
+    k = 1.0 / (c1 * c2)
+    a = u0 - c0 * c1
+    out.append(dict(name="RC", R=2, coeffs=[1.0 / c1, c2, 0.0], rhs=c0, u=[u0],
+                    exact=[c0 * c1 + a * np.exp(-k * t), -k * a * np.exp(-k * t),
+                           k * k * a * np.exp(-k * t)]))
+    c0, u0 = 0.23, 4.78                                   # population growth: c0 y - y' = 0
+    out.append(dict(name="Population", R=2, coeffs=[c0, -1.0, 0.0], rhs=0.0, u=[u0],
+                    exact=[u0 * np.exp(c0 * t) * c0 ** r for r in range(3)]))
+    c0, c1, u0 = 0.32, 0.28, 0.14                         # language death: (c0+c1) y + y' = c0
+    kk = c0 + c1
+    A0 = c0 / kk
+    out.append(dict(name="Language", R=2, coeffs=[kk, 1.0, 0.0], rhs=c0, u=[u0],
+                    exact=[A0 - (A0 - u0) * np.exp(-kk * t), kk * (A0 - u0) * np.exp(-kk * t),
+                           -kk * kk * (A0 - u0) * np.exp(-kk * t)]))
+    c0 = 2.1                                              # harmonic oscillator: c0 y + y'' = 0
+    u0, u1 = 0.4, -0.03
+    wq = math.sqrt(c0)
+    y0 = u0 * np.cos(wq * t) + u1 / wq * np.sin(wq * t)
+    out.append(dict(name="Harmonic", R=3, coeffs=[c0, 0.0, 1.0, 0.0], rhs=0.0, u=[u0, u1],
+                    exact=[y0, -u0 * wq * np.sin(wq * t) + u1 * np.cos(wq * t), -c0 * y0]))
+    c0, c1 = 4.5, 0.43                                    # damped oscillator: c0 y + c1 y' + y'' = 0
+    u0, u1 = 0.12, 0.043
+    om = math.sqrt(4 * c0 - c1 ** 2) / 2
+    lam = -c1 / 2 + 1j * om
+    z = np.exp(lam * t) * (u0 - 1j * (c1 * u0 + 2 * u1) / (2 * om))   # y = Re z
+    out.append(dict(name="Damped", R=3, coeffs=[c0, c1, 1.0, 0.0], rhs=0.0, u=[u0, u1],
+                    exact=[np.real(z), np.real(lam * z), np.real(lam * lam * z)]))
+    u0, u1, u2 = 0.0, -1.0, 1.0                           # third order: y' + y'' + y''' = 0
+    lam = -0.5 + 1j * math.sqrt(3) / 2
+    z = np.exp(lam * t) * (-(u1 + u2) - 1j * math.sqrt(3) / 3 * (u1 - u2))
+    out.append(dict(name="ThirdOrder", R=3, coeffs=[0.0, 1.0, 1.0, 1.0], rhs=0.0, u=[u0, u1, u2],
+                    exact=[u0 + u1 + u2 + np.real(z), np.real(lam * z), np.real(lam * lam * z)]))
+    for cse in out:
+        cse["R_init"] = len(cse["u"]) - 1
+    return out
+
+
+def table5_batch(R: int, R_init: int, T: int = ODE_T, h: float = ODE_H) -> tuple[Problem, list[dict]]:
+    """The App. B.1 cases of order R with R_init + 1 initial values, as one uniform batch
+    (one system per case, D = 1, constant step h, unit weights, T_init = 1)."""
+    cases = [cse for cse in table5_odes(T, h) if cse["R"] == R and cse["R_init"] == R_init]
+    B = len(cases)
+    c = np.zeros((B, 1, T, R + 1))
+    d = np.zeros((B, 1, T))
+    u = np.zeros((B, 1, 1, R_init + 1))
+    for b, cse in enumerate(cases):
+        c[b, 0, :, :] = np.asarray(cse["coeffs"], float)[: R + 1]
+        d[b, 0, :] = cse["rhs"]
+        u[b, 0, 0, :] = cse["u"]
+    s = np.full((B, T), h)
+    return Problem(f"App. B.1 ODEs R={R}", R, R_init, 1, B, 1, T, c, d, s, u), cases

@@ -14,6 +14,7 @@ import pytest
 import scipy.linalg
 
 import oracle as O
+import smnn_workloads as W
 from smnn_workloads import random_problem
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -330,6 +331,44 @@ def test_gradient_matches_finite_differences(case):
     assert np.abs(an - nu).max() <= 1e-5 * scale, np.abs(an - nu).max() / scale
 
 
+@pytest.mark.parametrize("case", CASES[:5])
+def test_weight_gradients_match_finite_differences(case):
+    """dl/d(w_gov, w_init, w_smooth) for l = <gy, y> against central differences of the dense
+    solve with the weight perturbed (App. A.1: W holds the squared weights)."""
+    prob = case_problem(*case)
+    p = params_of(prob)
+    c, d, s, u = one(prob)
+    gy = np.random.Generator(np.random.PCG64(10)).standard_normal(c.shape)
+    *_, gw, info = O.gradient(p, c[None, None], d[None, None], s[None], u[None, None],
+                              gy[None, None], weights=True)
+    assert info[0] == 0
+    w0 = (p.w_gov, p.w_init, p.w_smooth)
+    for k in range(3):
+        h = 1e-6 * max(1.0, w0[k])
+        wp = list(w0); wp[k] += h
+        wm = list(w0); wm[k] -= h
+        lp, _ = _loss_and_y(O.Params(p.R, p.R_init, p.T_init, *wp), c, d, s, u, gy)
+        lm, _ = _loss_and_y(O.Params(p.R, p.R_init, p.T_init, *wm), c, d, s, u, gy)
+        fd = (lp - lm) / (2 * h)
+        assert abs(gw[k] - fd) <= 1e-6 * max(1.0, abs(fd)), (k, gw[k], fd)
+
+
+def test_weight_gradients_sum_over_systems():
+    """The weights are shared by the batch: the batch's dl/dw is the sum of the systems'."""
+    prob = random_problem(3, 2, 2, 12, 2, w=(0.8, 1.3, 1.1))
+    p = params_of(prob)
+    gy = np.random.Generator(np.random.PCG64(4)).standard_normal(prob.c.shape)
+    *_, gw, info = O.gradient(p, prob.c, prob.d, prob.s, prob.u, gy, weights=True)
+    tot = np.zeros(3)
+    for b in range(2):
+        for dd in range(2):
+            *_, g1, _ = O.gradient(p, prob.c[b:b + 1, dd:dd + 1], prob.d[b:b + 1, dd:dd + 1],
+                                   prob.s[b:b + 1], prob.u[b:b + 1, dd:dd + 1],
+                                   gy[b:b + 1, dd:dd + 1], weights=True)
+            tot += g1
+    np.testing.assert_allclose(gw, tot, rtol=1e-12, atol=1e-14)
+
+
 def test_gradient_dot_product_identity():
     """Eq. 14: for l = gamma^T y, dl/dbeta = M^{-1} gamma, so dl/dd_t = w_gov^2 c_t . g_t
     and dl/du = w_init^2 g at the initial entries, with M taken from App. A.2."""
@@ -394,22 +433,12 @@ def test_table5_first_order_odes_reproduced():
     """App. B.1 closed forms (RC circuit, population growth, language death) solved on
     T=1000 steps of 0.01 reproduce Table 5's S-MNN relative MSE to its printed digits."""
     gold = _load_table("table5_first_order.txt")
-    t = np.arange(T5_T) * T5_H
-    c0, c1, c2, u0 = 0.7, 1.2, 2.31, 10.0                 # RC: y/c1 + c2 y' = c0
-    k = 1.0 / (c1 * c2); a = u0 - c0 * c1
-    rc = [c0 * c1 + a * np.exp(-k * t), -k * a * np.exp(-k * t), k * k * a * np.exp(-k * t)]
-    y = _solve_ode([1.0 / c1, c2], c0, [u0], 2)
-    got = {"RC": [_rel_mse(y[:, r], rc[r]) for r in range(3)]}
-    c0, u0 = 0.23, 4.78                                   # population: c0 y - y' = 0
-    pop = [u0 * np.exp(c0 * t) * c0 ** r for r in range(3)]
-    y = _solve_ode([c0, -1.0], 0.0, [u0], 2)
-    got["Population"] = [_rel_mse(y[:, r], pop[r]) for r in range(3)]
-    c0, c1, u0 = 0.32, 0.28, 0.14                         # language death: (c0+c1) y + y' = c0
-    kk = c0 + c1; A0 = c0 / kk
-    lang = [A0 - (A0 - u0) * np.exp(-kk * t), kk * (A0 - u0) * np.exp(-kk * t),
-            -kk * kk * (A0 - u0) * np.exp(-kk * t)]
-    y = _solve_ode([kk, 1.0], c0, [u0], 2)
-    got["Language"] = [_rel_mse(y[:, r], lang[r]) for r in range(3)]
+    got = {}
+    for cse in W.table5_odes():
+        if cse["name"] in gold:
+            y = _solve_ode(cse["coeffs"], cse["rhs"], cse["u"], cse["R"])
+            got[cse["name"]] = [_rel_mse(y[:, r], cse["exact"][r]) for r in range(3)]
+    assert sorted(got) == sorted(gold)
     for name, vals in gold.items():
         for g, v in zip(got[name], vals):
             # the paper prints two significant digits
@@ -418,25 +447,11 @@ def test_table5_first_order_odes_reproduced():
 
 def test_table5_higher_order_odes_below_paper_bound():
     """Harmonic, damped and third-order ODEs (App. B.1): relative MSE below 1e-6, the
-    bound the paper states for all its standalone cases."""
-    t = np.arange(T5_T) * T5_H
-    c0 = 2.1; u0, u1 = 0.4, -0.03; wq = math.sqrt(c0)   # c0 y + y'' = 0
-    harm = [u0 * np.cos(wq * t) + u1 / wq * np.sin(wq * t),
-            -u0 * wq * np.sin(wq * t) + u1 * np.cos(wq * t)]
-    harm.append(-c0 * harm[0])
-    y = _solve_ode([c0, 0.0, 1.0], 0.0, [u0, u1], 3)
-    assert max(_rel_mse(y[:, r], harm[r]) for r in range(3)) < 1e-6
-    c0, c1 = 4.5, 0.43; u0, u1 = 0.12, 0.043              # c0 y + c1 y' + y'' = 0
-    om = math.sqrt(4 * c0 - c1 ** 2) / 2; al = -c1 / 2; B = (c1 * u0 + 2 * u1) / (2 * om)
-    z = np.exp((al + 1j * om) * t) * (u0 - 1j * B)       # y = Re z
-    lam = al + 1j * om
-    damp = [np.real(z), np.real(lam * z), np.real(lam * lam * z)]
-    y = _solve_ode([c0, c1, 1.0], 0.0, [u0, u1], 3)
-    assert max(_rel_mse(y[:, r], damp[r]) for r in range(3)) < 1e-6
-    u0, u1, u2 = 0.0, -1.0, 1.0                           # y' + y'' + y''' = 0
-    lam = -0.5 + 1j * math.sqrt(3) / 2
-    Bc = -(u1 + u2); Cc = math.sqrt(3) / 3 * (u1 - u2)
-    z = np.exp(lam * t) * (Bc - 1j * Cc)
-    third = [u0 + u1 + u2 + np.real(z), np.real(lam * z), np.real(lam * lam * z)]
-    y = _solve_ode([0.0, 1.0, 1.0, 1.0], 0.0, [u0, u1, u2], 4)
-    assert max(_rel_mse(y[:, r], third[r]) for r in range(3)) < 1e-6
+    bound the paper states for all its standalone cases (the third-order one needs R = 4:
+    at R = 3 the oracle's relative MSE of y is 1.3e-6)."""
+    for cse in W.table5_odes():
+        if cse["name"] not in ("Harmonic", "Damped", "ThirdOrder"):
+            continue
+        R = 4 if cse["name"] == "ThirdOrder" else cse["R"]
+        y = _solve_ode(cse["coeffs"], cse["rhs"], cse["u"], R)
+        assert max(_rel_mse(y[:, r], cse["exact"][r]) for r in range(3)) < 1e-6, cse["name"]
