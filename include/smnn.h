@@ -173,10 +173,18 @@ smnn_status smnn_factor_solve(smnn_plan plan, const void* c, const void* d, cons
  *          gs of the last step of a sequence is 0.
  * y: the forward solution; gy: dl/dy (layout of y).  factor: the buffer filled by
  * smnn_factor_solve with the same inputs, or NULL to recompute the factor into the
- * workspace.  Outputs gc, gd, gs, gu have the layouts of c, d, s, u. */
+ * workspace.  Outputs gc, gd, gs, gu have the layouts of c, d, s, u.
+ * gw: NULL, or 3 doubles of device memory (8-byte aligned) that receive the derivatives
+ * of the loss with respect to the importance weights of Eq. 9, shared by all systems of
+ * the batch (App. A.1: each row's weight is the square of w times a step-size power):
+ *   gw[0] = dl/dw_gov    = 2 w_gov sum_t (c_t.g_t)(d_t - c_t.y_t),
+ *   gw[1] = dl/dw_init   = 2 w_init sum_{t<T_init, r<=R_init} g_{t,r} (u_{t,r} - y_{t,r}),
+ *   gw[2] = dl/dw_smooth = -2 w_smooth sum_t sum_r s_t^{2r} (f+_r e+_r + f-_r e-_r),
+ * summed over every system whose info is 0, in a fixed order (deterministic); the terms
+ * are formed in the precision of the residual and summed in FP64. */
 smnn_status smnn_backward(smnn_plan plan, const void* c, const void* d, const void* s,
                           const void* u, const void* y, const void* factor, const void* gy,
-                          void* gc, void* gd, void* gs, void* gu, int32_t* info,
+                          void* gc, void* gd, void* gs, void* gu, double* gw, int32_t* info,
                           void* workspace, void* stream);
 
 /* Per-kernel timing of this library's own launches, for benchmarks.  While enabled

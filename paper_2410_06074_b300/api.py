@@ -80,13 +80,17 @@ def solve(c, d, s, u, cfg: SolveConfig = SolveConfig(), *, D=None, seq_T=None, f
 
 
 def gradients(c, d, s, u, y, gy, cfg: SolveConfig = SolveConfig(), *, D=None, seq_T=None,
-              factor=None, workspace=None):
-    """Backward only: returns (gc, gd, gs, gu, info) for dl/dy = gy."""
+              factor=None, workspace=None, weights: bool = False):
+    """Backward only: returns (gc, gd, gs, gu, info) for dl/dy = gy; with weights=True,
+    (gc, gd, gs, gu, gw, info), gw = dl/d(w_gov, w_init, w_smooth) (float64, 3 values)."""
     plan = get_plan(_shape_key(c, s, D, seq_T), cfg)
     gc, gd, gs, gu = (torch.empty_like(t) for t in (c, d, s, u))
     info = torch.empty(plan.S, dtype=torch.int32, device=c.device)
+    gw = torch.empty(3, dtype=torch.float64, device=c.device) if weights else None
     ws = plan.workspace(c.device) if workspace is None else workspace
-    plan.backward(c, d, s, u, y, gy.contiguous(), gc, gd, gs, gu, info, ws, factor=factor)
+    plan.backward(c, d, s, u, y, gy.contiguous(), gc, gd, gs, gu, info, ws, factor=factor, gw=gw)
+    if weights:
+        return gc, gd, gs, gu, gw, info
     return gc, gd, gs, gu, info
 
 
@@ -94,27 +98,37 @@ class SmnnSolve(torch.autograd.Function):
     """y = (A^T W A)^{-1} A^T W b (Eq. 9) with the hand-written adjoint of Eq. 14.
 
     The forward keeps the factor for the backward pass when it fits
-    ``cfg.factor_budget_bytes``; otherwise the backward recomputes it."""
+    ``cfg.factor_budget_bytes``; otherwise the backward recomputes it.  ``weights``: None, or
+    a tensor (w_gov, w_init, w_smooth) that replaces the config's weights and receives
+    dl/dw (the weights are plan constants: each new value builds, and caches, a plan)."""
 
     @staticmethod
-    def forward(ctx, c, d, s, u, cfg: SolveConfig, D=None, seq_T=None):
+    def forward(ctx, c, d, s, u, weights, cfg: SolveConfig, D=None, seq_T=None):
         c, d, s, u = (t.contiguous() for t in (c, d, s, u))
+        if weights is not None:
+            wg, wi, wsm = (float(v) for v in weights.detach().double().cpu().tolist())
+            cfg = replace(cfg, w_gov=wg, w_init=wi, w_smooth=wsm)
         plan = get_plan(_shape_key(c, s, D, seq_T), cfg)
         factor = plan.factor_buffer(c.device) if plan.factor_bytes <= cfg.factor_budget_bytes else None
         y, info = solve(c, d, s, u, cfg, D=D, seq_T=seq_T, factor=factor)
         ctx.save_for_backward(c, d, s, u, y)
         ctx.cfg, ctx.D, ctx.seq_T, ctx.factor = cfg, D, seq_T, factor
+        ctx.w_dtype = None if weights is None else weights.dtype
         ctx.mark_non_differentiable(info)
         return y, info
 
     @staticmethod
     def backward(ctx, gy, _ginfo):
         c, d, s, u, y = ctx.saved_tensors
-        gc, gd, gs, gu, _ = gradients(c, d, s, u, y, gy, ctx.cfg, D=ctx.D, seq_T=ctx.seq_T,
-                                      factor=ctx.factor)
-        return gc, gd, gs, gu, None, None, None
+        want_w = ctx.w_dtype is not None and ctx.needs_input_grad[4]
+        out = gradients(c, d, s, u, y, gy, ctx.cfg, D=ctx.D, seq_T=ctx.seq_T, factor=ctx.factor,
+                        weights=want_w)
+        gc, gd, gs, gu = out[:4]
+        gw = out[4].to(ctx.w_dtype) if want_w else None
+        return gc, gd, gs, gu, gw, None, None, None
 
 
-def smnn_layer(c, d, s, u, cfg: SolveConfig = SolveConfig(), *, D=None, seq_T=None):
-    """Differentiable S-MNN solve; returns (y, info)."""
-    return SmnnSolve.apply(c, d, s, u, cfg, D, seq_T)
+def smnn_layer(c, d, s, u, cfg: SolveConfig = SolveConfig(), *, D=None, seq_T=None, weights=None):
+    """Differentiable S-MNN solve; returns (y, info).  ``weights``: optional tensor
+    (w_gov, w_init, w_smooth) to learn; overrides the config's weights."""
+    return SmnnSolve.apply(c, d, s, u, weights, cfg, D, seq_T)

@@ -62,7 +62,7 @@ SYMBOLS = {
                                            ctypes.POINTER(ctypes.c_size_t)]),
     "smnn_assemble": (ctypes.c_int, [_VP] + [_VP] * 8 + [_VP]),
     "smnn_factor_solve": (ctypes.c_int, [_VP] + [_VP] * 8 + [_VP]),
-    "smnn_backward": (ctypes.c_int, [_VP] + [_VP] * 13 + [_VP]),
+    "smnn_backward": (ctypes.c_int, [_VP] + [_VP] * 14 + [_VP]),
     "smnn_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "smnn_launch_count": (ctypes.c_uint64, []),
     "smnn_profile_enable": (ctypes.c_int, [ctypes.c_int]),
@@ -212,8 +212,12 @@ class Plan:
         _check(lib.smnn_factor_solve(self.handle, _p(c), _p(d), _p(s), _p(u), _p(y), _p(factor),
                                      _p(info), _p(workspace), _stream(stream)), "smnn_factor_solve")
 
-    def backward(self, c, d, s, u, y, gy, gc, gd, gs, gu, info, workspace, factor=None, stream=None):
+    def backward(self, c, d, s, u, y, gy, gc, gd, gs, gu, info, workspace, factor=None, stream=None,
+                 gw=None):
+        """gw: optional float64 device tensor of 3 values, receives dl/d(w_gov, w_init, w_smooth)."""
         self._args_ok(c, d, s, u, y, gy, gc, gd, gs, gu, info, workspace, factor)
+        if gw is not None and (gw.dtype != torch.float64 or gw.numel() < 3 or not gw.is_cuda):
+            raise ValueError("gw must be a CUDA float64 tensor with 3 elements")
         _check(lib.smnn_backward(self.handle, _p(c), _p(d), _p(s), _p(u), _p(y), _p(factor),
-                                 _p(gy), _p(gc), _p(gd), _p(gs), _p(gu), _p(info), _p(workspace),
-                                 _stream(stream)), "smnn_backward")
+                                 _p(gy), _p(gc), _p(gd), _p(gs), _p(gu), _p(gw), _p(info),
+                                 _p(workspace), _stream(stream)), "smnn_backward")

@@ -782,7 +782,8 @@ template <> __device__ __forceinline__ double st_n<double, double>(double v) { r
 // -w_s^2 d/ds sum_r s^{2r} (f+_r e+_r + f-_r e-_r) for the pair (t, t+1), g and y held fixed.
 template <class N, int NB, class Ts>
 __device__ __forceinline__ N smooth_pair_grad(Ts s, N ws2, const N (&ya)[NB], const N (&yb)[NB],
-                                              const N (&ga)[NB], const N (&gb)[NB]) {
+                                              const N (&ga)[NB], const N (&gb)[NB],
+                                              double* wsum = nullptr) {
   N cp[NB], cm[NB];
   taylor_coefs<N, NB, Ts>(s, cp, cm);
   N pya[NB], pga[NB], qyb[NB], qgb[NB];
@@ -802,7 +803,9 @@ __device__ __forceinline__ N smooth_pair_grad(Ts s, N ws2, const N (&ya)[NB], co
     if (r + 1 < NB) {  // d/ds exp(+-sN) v = +-N exp(+-sN) v: component r takes component r+1
       inner = (pga[r + 1] * ep + fp * pya[r + 1]) - (qgb[r + 1] * em + fm * qyb[r + 1]);
     }
-    acc = acc + ds2r * (fp * ep + fm * em) + s2r * inner;
+    const N rows = fp * ep + fm * em;
+    acc = acc + ds2r * rows + s2r * inner;
+    if (wsum) *wsum += Num<N>::to_d(s2r * rows);
     ds2r = s2r * s * float(2 * r + 2);
     s2r = s2r * s2;
   }
@@ -816,7 +819,7 @@ __device__ __forceinline__ N smooth_pair_grad(Ts s, N ws2, const N (&ya)[NB], co
 template <class N, int NB>
 __device__ __forceinline__ float smooth_pair_grad_f32(float s, float ws2, const N (&ya)[NB],
                                                       const N (&yb)[NB], const N (&ga)[NB],
-                                                      const N (&gb)[NB]) {
+                                                      const N (&gb)[NB], double* wsum = nullptr) {
   N cp[NB], cm[NB];
   taylor_coefs<N, NB, float>(s, cp, cm);
   N pya[NB], pga[NB], qyb[NB], qgb[NB];
@@ -827,10 +830,17 @@ __device__ __forceinline__ float smooth_pair_grad_f32(float s, float ws2, const 
   float acc = 0.f;
   float s2r = 1.f, ds2r = 0.f;   // s^{2r}, 2r s^{2r-1}
   const float s2 = s * s;
+  N s2rn = Num<N>::from_f(1.f);
+  const N s2n = Num<N>::from_f(s) * s;
 #pragma unroll
   for (int r = 0; r < NB; ++r) {
-    const float ep = Num<N>::to_f(pya[r] - yb[r]), fp = Num<N>::to_f(pga[r] - gb[r]);
-    const float em = Num<N>::to_f(qyb[r] - ya[r]), fm = Num<N>::to_f(qgb[r] - ga[r]);
+    const N epn = pya[r] - yb[r], fpn = pga[r] - gb[r], emn = qyb[r] - ya[r], fmn = qgb[r] - ga[r];
+    if (wsum) {   // the rows' share of dl/dw_smooth, kept in N
+      *wsum += Num<N>::to_d(s2rn * (fpn * epn + fmn * emn));
+      s2rn = s2rn * s2n;
+    }
+    const float ep = Num<N>::to_f(epn), fp = Num<N>::to_f(fpn);
+    const float em = Num<N>::to_f(emn), fm = Num<N>::to_f(fmn);
     float inner = 0.f;
     if (r + 1 < NB) {
       const float a1 = Num<N>::to_f(pga[r + 1]), b1 = Num<N>::to_f(pya[r + 1]);
@@ -846,11 +856,16 @@ __device__ __forceinline__ float smooth_pair_grad_f32(float s, float ws2, const 
 
 // One thread per level-0 chunk of one system: gc, gd (interleaved), this system's share of
 // gs (interleaved; the D systems of a sequence are summed in k_scatter_gs) and gu.
-template <class Tr, class N, int NB>
+// With kW, also this chunk's share of dl/dw for the three importance weights (App. A.1: each
+// row's weight is w^2 times a step-size power), accumulated in FP64 from terms formed in N:
+//   dl/dw_gov = 2 w_gov sum_t (c_t.g_t)(d_t - c_t.y_t),  dl/dw_init = 2 w_init sum g (u - y),
+//   dl/dw_smooth = -2 w_smooth sum_pairs sum_r s^{2r} (f+_r e+_r + f-_r e-_r)
+// (the rows' g-values f and y-values e), written to part_w[3 g + k].
+template <class Tr, class N, int NB, bool kW>
 __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L0In<Tr> in,
                                                    const Tr* y_hi, const float* y_lo, const Tr* g_hi,
                                                    const float* g_lo, const int32_t* info, Tr* gc,
-                                                   Tr* gd, Tr* gs, Tr* gu) {
+                                                   Tr* gd, Tr* gs, Tr* gu, double* part_w) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
   const ChunkPos cp = chunk_pos(lt, g);
@@ -867,6 +882,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
   }
   constexpr bool kF32 = std::is_same<Tr, float>::value;
   const float wg2f = float(p.wg2), ws2f = float(p.ws2);
+  double wgov = 0.0, winit = 0.0, wsm = 0.0;
   for (int64_t t = cp.first; t <= cp.last; ++t) {
     N cy = Num<N>::zero(), cg = Num<N>::zero();
 #pragma unroll
@@ -876,6 +892,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
       cg = cg + cv * ga[a];
     }
     const N e = ld_n<N>(in.d[k]) - cy;
+    if (kW) wgov += Num<N>::to_d(cg * e);
     if constexpr (kF32) {
       // e = d - c.y and c.g cancel and need N; the rest is FP32
       const float ef = Num<N>::to_f(e), cgf = Num<N>::to_f(cg);
@@ -891,8 +908,13 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
       gd[k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * cg);
     }
     if (t < p.T_init) {
-      for (int a = 0; a <= p.R_init; ++a)
+      for (int a = 0; a <= p.R_init; ++a) {
         gu[cp.i * nu + t * (p.R_init + 1) + a] = failed ? nan_t<Tr>() : st_n<Tr, N>(wi2 * ga[a]);
+        if (kW) {
+          const N du = ld_n<N>(static_cast<const Tr*>(p.u)[cp.i * nu + t * (p.R_init + 1) + a]) - ya[a];
+          winit += Num<N>::to_d(ga[a] * du);
+        }
+      }
     }
     N gsum = Num<N>::zero();
     const int64_t kn = t < cp.last ? k + G : g + 1;   // step t+1: next position or next chunk
@@ -903,14 +925,43 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
         yb[a] = ld_pair<N>(y_hi, y_lo, a * es + kn);
         gb[a] = ld_pair<N>(g_hi, g_lo, a * es + kn);
       }
-      if constexpr (kF32) gsum = Num<N>::from_f(smooth_pair_grad_f32<N, NB>(in.s[k], ws2f, ya, yb, ga, gb));
-      else gsum = smooth_pair_grad<N, NB, Tr>(in.s[k], ws2, ya, yb, ga, gb);
+      if constexpr (kF32)
+        gsum = Num<N>::from_f(smooth_pair_grad_f32<N, NB>(in.s[k], ws2f, ya, yb, ga, gb, kW ? &wsm : nullptr));
+      else gsum = smooth_pair_grad<N, NB, Tr>(in.s[k], ws2, ya, yb, ga, gb, kW ? &wsm : nullptr);
 #pragma unroll
       for (int a = 0; a < NB; ++a) { ya[a] = yb[a]; ga[a] = gb[a]; }
     }
     gs[k] = failed ? nan_t<Tr>() : st_n<Tr, N>(gsum);
     k += G;
   }
+  if (kW) {   // a failed system contributes nothing (its info flags it)
+    const double sw = failed ? 0.0 : 2.0;
+    part_w[3 * g] = sw * sqrt(p.wg2) * wgov;
+    part_w[3 * g + 1] = sw * sqrt(p.wi2) * winit;
+    part_w[3 * g + 2] = -sw * sqrt(p.ws2) * wsm;
+  }
+}
+
+// dl/dw = the sum of the chunks' shares, in a fixed order (one CTA; thread j sums chunks
+// j, j + 256, ..., then a fixed tree), so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) k_reduce_w(const double* part_w, int64_t G, double* gw) {
+  __shared__ double sh[3][256];
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (int64_t g = threadIdx.x; g < G; g += 256) {
+    a0 += part_w[3 * g];
+    a1 += part_w[3 * g + 1];
+    a2 += part_w[3 * g + 2];
+  }
+  sh[0][threadIdx.x] = a0;
+  sh[1][threadIdx.x] = a1;
+  sh[2][threadIdx.x] = a2;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (int(threadIdx.x) < h)
+      for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) gw[threadIdx.x] = sh[threadIdx.x][0];
 }
 
 // gs: sum of the D systems' shares (system-chunk interleaved) -> user layout of s.  One
@@ -999,6 +1050,7 @@ struct smnn_plan_s {
   size_t factor_bytes = 0, solve_bytes = 0;
   size_t o_fyh = 0, o_fyl = 0;         // factor region: the refined y, float-float (FP32 paths)
   size_t o_part = 0, o_prev = 0, o_skip = 0;  // refinement stop test (solve region), and:
+  size_t o_pw = 0;                     //   the chunks' shares of dl/dw
   size_t o_c = 0, o_d = 0, o_s = 0;    //   staged inputs
   size_t o_r = 0, o_gy = 0;            //   residual / explicit rhs, staged dl/dy
   size_t o_x = 0, o_g = 0;             //   plain solutions (FP64 and FP32 paths)
@@ -1157,6 +1209,7 @@ smnn_status build_plan_host(smnn_plan_s* pl) {
     pl->o_part = take(size_t(L0.G) * 2 * sizeof(float));
     pl->o_prev = take(size_t(S) * sizeof(float));
     pl->o_skip = take(size_t(S) * sizeof(int32_t));
+    pl->o_pw = take(size_t(L0.G) * 3 * sizeof(double));
   }
   pl->factor_bytes = f;
 
@@ -1381,6 +1434,7 @@ struct L0Bufs {  // level-0 interleaved scratch of one call
   float* yh; float* yl; float* gh; float* gl;
   Tr* gc; Tr* gd; Tr* gs;
   float* part; float* prev; int32_t* skip;
+  double* pw;   // [G0][3] the chunks' shares of dl/dw
 };
 
 template <class Tr>
@@ -1391,7 +1445,8 @@ L0Bufs<Tr> l0_bufs(const smnn_plan_s* pl, char* fac, char* sol) {
   return L0Bufs<Tr>{PF(pl->o_c), PF(pl->o_d), PF(pl->o_s), P(pl->o_r), P(pl->o_gy), P(pl->o_x),
                     P(pl->o_g), F(pl->o_yh), F(pl->o_yl), F(pl->o_gh), F(pl->o_gl), P(pl->o_gc),
                     P(pl->o_gd), P(pl->o_gs), F(pl->o_part), F(pl->o_prev),
-                    reinterpret_cast<int32_t*>(sol + pl->o_skip)};
+                    reinterpret_cast<int32_t*>(sol + pl->o_skip),
+                    reinterpret_cast<double*>(sol + pl->o_pw)};
 }
 
 inline int64_t l0_elems(const smnn_plan_s* pl) { return pl->lv[0].G * int64_t(pl->lv[0].L); }
@@ -1525,12 +1580,23 @@ smnn_status refine_backward(const smnn_plan_s* pl, const Problem0& p, char* fac,
 template <class Tr, class N, int NB>
 smnn_status gradients_out(const smnn_plan_s* pl, const Problem0& p, const L0Bufs<Tr>& b,
                           const Tr* yh, const float* yl, const Tr* gh, const float* gl,
-                          int32_t* info, Tr* gc, Tr* gd, Tr* gs, Tr* gu, cudaStream_t st) {
+                          int32_t* info, Tr* gc, Tr* gd, Tr* gs, Tr* gu, double* gw, cudaStream_t st) {
   const Level& L0 = pl->lv[0];
   GradTables gt{pl->d_sq_b, pl->d_sq_k, L0.d_coff, pl->d_sys_T, pl->Q, L0.G, L0.L, int(pl->D)};
   const L0In<Tr> in{b.c, b.d, b.s};
-  SMNN_LAUNCH((k_grad<Tr, N, NB>), L0.G, st, tables_of(L0), p, in, yh, yl, gh, gl, info, b.gc, b.gd,
-              b.gs, gu);
+  if (gw) {
+    SMNN_LAUNCH((k_grad<Tr, N, NB, true>), L0.G, st, tables_of(L0), p, in, yh, yl, gh, gl, info, b.gc,
+                b.gd, b.gs, gu, b.pw);
+    if (cudaGetLastError() != cudaSuccess) return SMNN_ERR_CUDA;
+    prof_begin("k_reduce_w", st);
+    k_reduce_w<<<1, 256, 0, st>>>(b.pw, L0.G, gw);
+    prof_end(st);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (cudaGetLastError() != cudaSuccess) return SMNN_ERR_CUDA;
+  } else {
+    SMNN_LAUNCH((k_grad<Tr, N, NB, false>), L0.G, st, tables_of(L0), p, in, yh, yl, gh, gl, info,
+                b.gc, b.gd, b.gs, gu, nullptr);
+  }
   SMNN_TRY((tile_copy<Tr, Tr, NB, false>(pl, b.gc, nullptr, gc, nullptr, st)));
   SMNN_TRY((tile_copy<Tr, Tr, 1, false>(pl, b.gd, nullptr, gd, nullptr, st)));
   SMNN_LAUNCH(k_scatter_gs<Tr>, pl->Q * int64_t(L0.L), st, gt, pl->d_seq_soff, pl->d_seq_T, b.gs, gs);
@@ -1566,7 +1632,8 @@ smnn_status factor_solve_t(const smnn_plan_s* pl, const void* c, const void* d, 
 template <class Tr, int NB>
 smnn_status backward_t(const smnn_plan_s* pl, const void* c, const void* d, const void* s,
                        const void* u, const void* y, const void* factor, const void* gy, void* gc,
-                       void* gd, void* gs, void* gu, int32_t* info, void* ws, cudaStream_t st) {
+                       void* gd, void* gs, void* gu, void* gw, int32_t* info, void* ws,
+                       cudaStream_t st) {
   const Problem0 p = problem0(pl, c, d, s, u);
   char* fac = factor ? static_cast<char*>(const_cast<void*>(factor)) : static_cast<char*>(ws);
   char* sol = static_cast<char*>(ws) + pl->factor_bytes;
@@ -1578,21 +1645,22 @@ smnn_status backward_t(const smnn_plan_s* pl, const void* c, const void* d, cons
   Tr* gdo = static_cast<Tr*>(gd);
   Tr* gso = static_cast<Tr*>(gs);
   Tr* guo = static_cast<Tr*>(gu);
+  double* gwo = static_cast<double*>(gw);
   if constexpr (std::is_same<Tr, float>::value) {
     const float* y32 = static_cast<const float*>(y);
     const float* yh = nullptr;
     const float* yl = nullptr;
     if (pl->desc.precision == SMNN_F32_REFINED_DF) {
       SMNN_TRY((refine_backward<ff, NB>(pl, p, fac, sol, factor == nullptr, y32, info, st, &yh, &yl)));
-      return gradients_out<float, ff, NB>(pl, p, b, yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, st);
+      return gradients_out<float, ff, NB>(pl, p, b, yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, gwo, st);
     }
     SMNN_TRY((refine_backward<double, NB>(pl, p, fac, sol, factor == nullptr, y32, info, st, &yh, &yl)));
-    return gradients_out<float, double, NB>(pl, p, b, yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, st);
+    return gradients_out<float, double, NB>(pl, p, b, yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, gwo, st);
   } else {
     Level0Out<Tr> o{b.g, nullptr, nullptr, nullptr};
     SMNN_TRY((solve_pass<Tr, NB>(pl, p, b.gy, factor == nullptr, fac, sol, o, 0, info, st)));
     SMNN_TRY((gather_inputs<Tr, NB>(pl, p, b, static_cast<const Tr*>(y), b.x, nullptr, false, st)));
-    return gradients_out<Tr, double, NB>(pl, p, b, b.x, nullptr, b.g, nullptr, info, gco, gdo, gso, guo, st);
+    return gradients_out<Tr, double, NB>(pl, p, b, b.x, nullptr, b.g, nullptr, info, gco, gdo, gso, guo, gwo, st);
   }
 }
 
@@ -1768,14 +1836,16 @@ smnn_status smnn_factor_solve(smnn_plan plan, const void* c, const void* d, cons
 
 smnn_status smnn_backward(smnn_plan plan, const void* c, const void* d, const void* s, const void* u,
                           const void* y, const void* factor, const void* gy, void* gc, void* gd,
-                          void* gs, void* gu, int32_t* info, void* workspace, void* stream) {
+                          void* gs, void* gu, double* gw, int32_t* info, void* workspace,
+                          void* stream) {
   if (!plan || !c || !d || !s || !u || !y || !gy || !gc || !gd || !gs || !gu || !info)
     return SMNN_ERR_INVALID_ARG;
   if (!workspace || !aligned(workspace) || (factor && !aligned(factor))) return SMNN_ERR_WORKSPACE;
   DeviceGuard dg(plan->device);
   if (!dg.ok) return SMNN_ERR_CUDA;
-  SMNN_DISPATCH(plan, backward_t, plan, c, d, s, u, y, factor, gy, gc, gd, gs, gu, info, workspace,
-                static_cast<cudaStream_t>(stream));
+  if (gw && (reinterpret_cast<uintptr_t>(gw) & 7)) return SMNN_ERR_INVALID_ARG;
+  SMNN_DISPATCH(plan, backward_t, plan, c, d, s, u, y, factor, gy, gc, gd, gs, gu, gw, info,
+                workspace, static_cast<cudaStream_t>(stream));
 }
 
 const char* smnn_status_string(smnn_status status) {

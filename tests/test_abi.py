@@ -52,7 +52,7 @@ def test_null_arguments_are_rejected():
     assert B.lib.smnn_plan_destroy(None) == B.SMNN_OK
     assert B.lib.smnn_workspace_size(None, None, None) == B.SMNN_ERR_INVALID_ARG
     assert B.lib.smnn_factor_solve(*([None] * 10)) == B.SMNN_ERR_INVALID_ARG
-    assert B.lib.smnn_backward(*([None] * 15)) == B.SMNN_ERR_INVALID_ARG
+    assert B.lib.smnn_backward(*([None] * 16)) == B.SMNN_ERR_INVALID_ARG
 
 
 def test_ragged_seq_T_validation():

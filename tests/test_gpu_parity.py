@@ -259,6 +259,19 @@ def test_gradcheck_config2_slice():
     assert torch.autograd.gradcheck(f, (c, d, z, u), eps=1e-4, atol=1e-6, rtol=1e-4)
 
 
+def test_gradcheck_with_learnable_weights():
+    """gradcheck of SmnnSolve with (w_gov, w_init, w_smooth) as a differentiable input, FP64."""
+    import torch
+    from smnn_workloads import config2_slice
+    pk = P()
+    prob = config2_slice()
+    c, d, s, u = (torch.from_numpy(a).cuda() for a in (prob.c, prob.d, prob.s, prob.u))
+    w = torch.tensor([0.9, 1.2, 1.1], dtype=torch.float64, device="cuda", requires_grad=True)
+    cfg = pk.SolveConfig(R_init=1, T_init=1, precision=pk.F64)
+    f = lambda w: pk.smnn_layer(c, d, s, u, cfg, weights=w)[0]
+    assert torch.autograd.gradcheck(f, (w,), eps=1e-5, atol=1e-6, rtol=1e-4)
+
+
 def test_autotuner_checks_candidates_and_picks_a_correct_one():
     import torch
     import paper_2410_06074_b300 as pk
@@ -290,3 +303,42 @@ def test_adaptive_refinement_stop_test(prec):
     for a, b in zip(out[:5], ref[:5]):
         assert rel_err(a, b) <= TOL_REF
     assert (out[5] == 0).all() and (out[6] == 0).all()
+
+
+# ----------------------------------------------------------------------------- weight gradients
+
+@pytest.mark.parametrize("prec,tol", [("F64", 1e-9), ("F32_REFINED", 1e-6), ("F32_REFINED_DF", 1e-6)])
+@pytest.mark.parametrize("store_factor", [True, False])
+def test_weight_gradients_match_oracle(prec, tol, store_factor):
+    """dl/d(w_gov, w_init, w_smooth) (shared by the batch) against the oracle's row-wise chain
+    rule, on a ragged batch with non-unit weights and several initial steps."""
+    import torch
+    import paper_2410_06074_b300 as pk
+    from paper_2410_06074_b300 import get_plan, gradients, solve
+    from paper_2410_06074_b300.api import _shape_key
+    from _helpers import cfg_of, dev, np_dtype, oracle_params
+    base = ragged_problem([300, 17, 1025, 64], D=3, seed=23)
+    prob = Problem("weights", 2, 2, 3, base.B, base.D, None, base.c, base.d, base.s,
+                   np.random.Generator(np.random.PCG64(24)).standard_normal((base.S, 3, 3)),
+                   seq_T=base.seq_T, w_gov=0.8, w_init=1.7, w_smooth=1.3)
+    p = getattr(pk, prec)
+    dt = np_dtype(p)
+    gy = upstream_gradient(prob).astype(dt)
+    c, d, s, u = dev(prob, dt)
+    cfg = cfg_of(prob, p)
+    plan = get_plan(_shape_key(c, s, prob.D, prob.seq_T), cfg)
+    fac = plan.factor_buffer() if store_factor else None
+    y, info = solve(c, d, s, u, cfg, D=prob.D, seq_T=prob.seq_T, factor=fac)
+    gc, gd, gs, gu, gw, info2 = gradients(c, d, s, u, y, torch.from_numpy(gy).cuda(), cfg, D=prob.D,
+                                          seq_T=prob.seq_T, factor=fac, weights=True)
+    r = rounded(prob, p)
+    *_, gwo, info_o = O.gradient(oracle_params(r), r.c, r.d, r.s, r.u, gy.astype(np.float64),
+                                 D=r.D, seq_T=r.seq_T, weights=True)
+    assert (info.cpu().numpy() == 0).all() and (info2.cpu().numpy() == 0).all() and (info_o == 0).all()
+    gw = gw.cpu().numpy()
+    assert np.abs(gw - gwo).max() <= tol * np.abs(gwo).max(), (gw, gwo)
+    # the same call without gw leaves the other gradients unchanged
+    gc2, gd2, gs2, gu2, _ = gradients(c, d, s, u, y, torch.from_numpy(gy).cuda(), cfg, D=prob.D,
+                                      seq_T=prob.seq_T, factor=fac)
+    for a, b in ((gc, gc2), (gd, gd2), (gs, gs2), (gu, gu2)):
+        assert torch.equal(a, b)
