@@ -55,10 +55,10 @@ def parse():
                          "fused (a launch per solve pass)")
     ap.add_argument("--only", default="", help="comma-separated variants to time (default: all)")
     ap.add_argument("--max-refine", type=int, default=3, help="forward refinement sweeps")
-    ap.add_argument("--adjoint-refine", type=int, default=2, help="adjoint refinement sweeps")
-    ap.add_argument("--refine-tol", type=float, default=0.0,
-                    help="per-system refinement stop test (0: always run every sweep; on the "
-                         "uniform-conditioning benchmark workload the fixed sweeps are faster)")
+    ap.add_argument("--adjoint-refine", type=int, default=3, help="adjoint refinement sweeps (at most; the stop test skips converged systems)")
+    ap.add_argument("--refine-tol", type=float, default=1e-7,
+                    help="per-system refinement stop test, the library's default (0: run every "
+                         "sweep with no convergence check)")
     return ap.parse_args()
 
 

@@ -24,12 +24,14 @@ class SolveConfig:
     w_gov: float = 1.0
     w_init: float = 1.0
     w_smooth: float = 1.0
-    precision: int = B.F32_REFINED
+    precision: int = B.F32_REFINED_DF
     algo: int = B.ALGO_AUTO
     max_refine: int = 3
-    adjoint_refine: int = 2
+    adjoint_refine: int = 3
     chunk: int = 0
-    refine_tol: float = 0.0
+    # per-system stop test of the refinement; a system whose estimated error is still above
+    # it after the last sweep gets info = -1 (refinement that stagnates is never silent)
+    refine_tol: float = 1e-7
     factor_budget_bytes: int = 16 << 30   # store the factor for backward if it fits
 
 

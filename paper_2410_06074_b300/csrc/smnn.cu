@@ -577,7 +577,7 @@ struct ResidualSource {
   __device__ void load(int64_t t, N (&v)[NB]) const {
     const int64_t k = idx(t), es = cs.es();
 #pragma unroll
-    for (int a = 0; a < NB; ++a) v[a] = Num<N>::pair(xh[a * es + k], xl ? xl[a * es + k] : 0.f);
+    for (int a = 0; a < NB; ++a) v[a] = Num<N>::pair(ld_ro(xh + a * es + k), xl ? ld_ro(xl + a * es + k) : 0.f);
   }
   // raw inputs of the next step, loaded one call ahead
   float pc[NB], prh[NB], pd, ps;
@@ -587,12 +587,12 @@ struct ResidualSource {
     const int64_t k = (t - cs.first) * cs.G + cs.g, es = cs.es();
 #pragma unroll
     for (int a = 0; a < NB; ++a) {
-      pc[a] = cs.c[a * es + k];
-      prh[a] = rhs ? rhs[a * es + k] : 0.f;
+      pc[a] = ld_ro(cs.c + a * es + k);
+      prh[a] = rhs ? ld_ro(rhs + a * es + k) : 0.f;
     }
-    pd = cs.d[k];
+    pd = ld_ro(cs.d + k);
     if (t + 1 < cs.T) {
-      ps = cs.s[k];
+      ps = ld_ro(cs.s + k);
       load(t + 1, px);
     }
   }

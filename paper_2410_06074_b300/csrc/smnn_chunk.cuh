@@ -40,7 +40,14 @@
 
 namespace smnn {
 
-constexpr double inv_fact(int k) { return k <= 1 ? 1.0 : inv_fact(k - 1) / double(k); }
+// 1/k!.  A plain loop rather than recursion: in the unrolled kernels the argument is a
+// compile-time constant and the whole expression folds (a recursive form was left as FP64
+// arithmetic at run time, which then bounded the FP32 kernels on the FP64 pipe).
+constexpr double inv_fact(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= double(i);
+  return 1.0 / f;
+}
 
 // (F^T F)_ab = sum_{k <= min(a,b)} 1/((a-k)! (b-k)!)
 constexpr double ftf_coef(int a, int b) {
@@ -73,6 +80,16 @@ template <> SMNN_HD double rsqrt_t<double>(double x) {
 }
 
 template <class Tr> SMNN_HD Tr nan_t() { return Tr(NAN); }
+
+// Load of data no thread writes during the kernel (the read-only data path): lets the
+// compiler issue the sweeps' one-step-ahead loads early, past the stores of the current step.
+template <class Tr> SMNN_HD Tr ld_ro(const Tr* p) {
+#ifdef __CUDA_ARCH__
+  return __ldg(p);
+#else
+  return *p;
+#endif
+}
 
 // ----------------------------------------------------------------------------- block ops
 
@@ -216,14 +233,14 @@ struct FactorView {
   };
   SMNN_HD void load_raw(int j, int64_t g, Raw& r, bool with_h, bool with_z) const {
 #pragma unroll
-    for (int e = 0; e < NB * (NB + 1) / 2; ++e) r.l[e] = lf[at(e, j, g)];
+    for (int e = 0; e < NB * (NB + 1) / 2; ++e) r.l[e] = ld_ro(lf + at(e, j, g));
     if (with_h) {
 #pragma unroll
-      for (int e = 0; e < NB * NB; ++e) r.h[e] = h[at(e, j, g)];
+      for (int e = 0; e < NB * NB; ++e) r.h[e] = ld_ro(h + at(e, j, g));
     }
     if (with_z) {
 #pragma unroll
-      for (int e = 0; e < NB; ++e) r.z[e] = z[at(e, j, g)];
+      for (int e = 0; e < NB; ++e) r.z[e] = ld_ro(z + at(e, j, g));
     }
   }
   static SMNN_HD void unpack_l(const Raw& r, Tr (&l)[NB][NB], Tr (&inv)[NB]) {
@@ -290,12 +307,12 @@ struct CoefSource {
     const int64_t k = at(t);
 #pragma unroll
     for (int r = 0; r < NB; ++r) {
-      nxt.c[r] = c[r * es() + k];
-      if (rhs) nxt.rh[r] = rhs[r * es() + k];
+      nxt.c[r] = ld_ro(c + r * es() + k);
+      if (rhs) nxt.rh[r] = ld_ro(rhs + r * es() + k);
     }
-    nxt.d = d[k];
-    nxt.s = s[k];
-    nxt.sp = t > 0 ? s[at(t - 1)] : Tr(0);
+    nxt.d = ld_ro(d + k);
+    nxt.s = ld_ro(s + k);
+    nxt.sp = t > 0 ? ld_ro(s + at(t - 1)) : Tr(0);
   }
   SMNN_HD void commit(int64_t t) {
     cur = nxt;
@@ -360,7 +377,7 @@ struct CoefSource {
 
   // E_t = N_t = block (t+1, t), t < T-1; its raw data is the step size s_t
   using ERaw = Tr;
-  SMNN_HD ERaw load_e(int64_t t) const { return s[at(t)]; }
+  SMNN_HD ERaw load_e(int64_t t) const { return ld_ro(s + at(t)); }
   // s_t is staged with step t (as s) and with step t+1 (as its previous step size)
   SMNN_HD void E(int64_t t, Tr (&e)[NB][NB]) const {
     e_from(t + 1 == cur_t ? cur.sp : (t == cur_t ? cur.s : load_e(t)), e);

@@ -28,7 +28,7 @@ def tune(name: str, precisions=(B.F32_REFINED_DF, B.F64)):
         dt = np.float64 if prec == B.F64 else np.float32
         c, d, s, u = (torch.from_numpy(np.ascontiguousarray(a, dt)).cuda() for a in (prob.c, prob.d, prob.s, prob.u))
         gy = torch.from_numpy(W.upstream_gradient(prob).astype(dt)).cuda()
-        cfg = SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=prec, max_refine=3, adjoint_refine=2)
+        cfg = SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=prec)
         best, res = autotune.autotune(c, d, s, u, cfg, gy, D=prob.D,
                                       seq_T=None if prob.seq_T is None else tuple(int(x) for x in prob.seq_T))
         out[f"{name}/P{prec}"] = {"best": [best.algo, best.chunk],

@@ -22,8 +22,7 @@ def run_full(prob, precision_name="F32_REFINED_DF", seed=2, store_factor=True, *
     prec = getattr(pk, precision_name)
     dt = np.float64 if prec == pk.F64 else np.float32
     c, d, s, u = (torch.from_numpy(np.ascontiguousarray(a, dt)).cuda() for a in (prob.c, prob.d, prob.s, prob.u))
-    cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=prec, max_refine=3,
-                         adjoint_refine=2, **kw)
+    cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=prec, **kw)
     seq_T = None if prob.seq_T is None else tuple(int(x) for x in prob.seq_T)
     plan = pk.get_plan(_shape_key(c, s, prob.D, seq_T), cfg)
     fac = plan.factor_buffer() if store_factor else None
