@@ -5,8 +5,8 @@ and the ``SmnnSolve`` autograd.Function.  Importing fails loudly if libsmnn.so c
 built or loaded: there is no CPU path.
 """
 from . import autotune, binding
-from .api import SmnnSolve, SolveConfig, get_plan, gradients, smnn_layer, solve
+from .api import HostPipeline, HostStream, SmnnSolve, SolveConfig, get_plan, gradients, smnn_layer, solve
 from .binding import ALGO_AUTO, ALGO_CR, ALGO_CR_FUSED, ALGO_SEQ, F32, F32_REFINED, F32_REFINED_DF, F64, Plan, SmnnError
 
-__all__ = ["autotune", "binding", "SmnnSolve", "SolveConfig", "get_plan", "gradients", "smnn_layer", "solve",
+__all__ = ["HostPipeline", "HostStream", "autotune", "binding", "SmnnSolve", "SolveConfig", "get_plan", "gradients", "smnn_layer", "solve",
            "Plan", "SmnnError", "F32", "F32_REFINED", "F32_REFINED_DF", "F64", "ALGO_AUTO", "ALGO_SEQ", "ALGO_CR", "ALGO_CR_FUSED"]

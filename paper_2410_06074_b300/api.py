@@ -134,3 +134,132 @@ def smnn_layer(c, d, s, u, cfg: SolveConfig = SolveConfig(), *, D=None, seq_T=No
     """Differentiable S-MNN solve; returns (y, info).  ``weights``: optional tensor
     (w_gov, w_init, w_smooth) to learn; overrides the config's weights."""
     return SmnnSolve.apply(c, d, s, u, weights, cfg, D, seq_T)
+
+
+class HostPipeline:
+    """Forward + adjoint of a uniform batch held in pinned host memory, streamed through the
+    GPU in parts of whole sequences.  Part p's host->device copies, solve, backward and
+    device->host copies are issued on stream p % 2 with that stream's own device buffers, so
+    one part's transfers run on the copy engines while the other part's kernels run on the SMs.
+    The systems are independent, so every part is an ordinary solve of its sequences (the
+    level structure of a part's plan follows its size).
+
+    run(c, d, s, u, gy, y, gc, gd, gs, gu) takes host tensors in the layouts of ``solve`` and
+    ``gradients`` (uniform batch; outputs preallocated, pinned) and returns (info, info_b)
+    of the forward and backward passes (device tensors, [B*D]), ordered after the copies on
+    the caller's stream."""
+
+    def __init__(self, shape_key, cfg: SolveConfig = SolveConfig(), n_parts: int = 4,
+                 device="cuda", dtype=torch.float32):
+        R, B, D, T = shape_key
+        n_parts = max(1, min(int(n_parts), B))
+        step = -(-B // n_parts)
+        self.bounds = [(b, min(b + step, B)) for b in range(0, B, step)]
+        self.D, self.T, self.nb = D, T, R + 1
+        self.plans = {n: get_plan((R, n, D, T), cfg) for n in {b1 - b0 for b0, b1 in self.bounds}}
+        big = max(self.plans)
+        plan = self.plans[big]
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(2)]
+        self.bufs = []
+        for _ in range(2):
+            f = lambda *sh: torch.empty(sh, dtype=dtype, device=device)
+            b = dict(c=f(big, D, T, R + 1), d=f(big, D, T), s=f(big, T),
+                     u=f(big, D, cfg.T_init, cfg.R_init + 1), gy=f(big, D, T, R + 1))
+            b.update(y=torch.empty_like(b["c"]), gc=torch.empty_like(b["c"]), gd=torch.empty_like(b["d"]),
+                     gs=torch.empty_like(b["s"]), gu=torch.empty_like(b["u"]),
+                     ws=plan.workspace(device), fac=plan.factor_buffer(device))
+            self.bufs.append(b)
+        self.info = torch.empty(B * D, dtype=torch.int32, device=device)
+        self.info_b = torch.empty_like(self.info)
+
+    def run(self, c, d, s, u, gy, y, gc, gd, gs, gu):
+        main = torch.cuda.current_stream()
+        for st in self.streams:
+            st.wait_stream(main)
+        for p, (b0, b1) in enumerate(self.bounds):
+            st, b = self.streams[p % 2], self.bufs[p % 2]
+            n = b1 - b0
+            plan = self.plans[n]
+            with torch.cuda.stream(st):
+                for key, h in (("c", c), ("d", d), ("s", s), ("u", u), ("gy", gy)):
+                    b[key][:n].copy_(h[b0:b1], non_blocking=True)
+                info = self.info[b0 * self.D:b1 * self.D]
+                info_b = self.info_b[b0 * self.D:b1 * self.D]
+                plan.factor_solve(b["c"][:n], b["d"][:n], b["s"][:n], b["u"][:n], b["y"][:n], info,
+                                  b["ws"], factor=b["fac"], stream=st)
+                plan.backward(b["c"][:n], b["d"][:n], b["s"][:n], b["u"][:n], b["y"][:n], b["gy"][:n],
+                              b["gc"][:n], b["gd"][:n], b["gs"][:n], b["gu"][:n], info_b, b["ws"],
+                              factor=b["fac"], stream=st)
+                for h, key in ((y, "y"), (gc, "gc"), (gd, "gd"), (gs, "gs"), (gu, "gu")):
+                    h[b0:b1].copy_(b[key][:n], non_blocking=True)
+        for st in self.streams:
+            main.wait_stream(st)
+        return self.info, self.info_b
+
+
+class HostStream:
+    """Forward + adjoint of successive uniform batches held in pinned host memory, with the
+    transfers of neighbouring steps overlapped: step k's host->device copy (copy-in stream)
+    runs while step k-1 computes (compute stream), and step k-1's device->host copy (copy-out
+    stream) while step k computes.  Two device buffer sets alternate between the steps; events
+    order each set's reuse after the reads of the step that used it before.
+
+    submit(c, d, s, u, gy, y, gc, gd, gs, gu): host tensors of one step (layouts of ``solve``
+    and ``gradients``; outputs preallocated, pinned).  Returns (info, info_b, done): device
+    tensors that hold the step's flags once ``done`` (a CUDA event) has completed; the host
+    outputs are complete then too.  wait(stream=None) orders the caller's stream after every
+    submitted step."""
+
+    def __init__(self, shape_key, cfg: SolveConfig = SolveConfig(), device="cuda",
+                 dtype=torch.float32):
+        R, B, D, T = shape_key
+        self.plan = get_plan((R, B, D, T), cfg)
+        self.s_in, self.s_cmp, self.s_out = (torch.cuda.Stream(device=device) for _ in range(3))
+        self.k = 0
+        self.sets = []
+        for _ in range(2):
+            f = lambda *sh: torch.empty(sh, dtype=dtype, device=device)
+            b = dict(c=f(B, D, T, R + 1), d=f(B, D, T), s=f(B, T),
+                     u=f(B, D, cfg.T_init, cfg.R_init + 1), gy=f(B, D, T, R + 1))
+            b.update(y=torch.empty_like(b["c"]), gc=torch.empty_like(b["c"]), gd=torch.empty_like(b["d"]),
+                     gs=torch.empty_like(b["s"]), gu=torch.empty_like(b["u"]),
+                     info=torch.empty(B * D, dtype=torch.int32, device=device),
+                     info_b=torch.empty(B * D, dtype=torch.int32, device=device),
+                     freed=None)
+            self.sets.append(b)
+        self.ws = self.plan.workspace(device)
+        self.fac = self.plan.factor_buffer(device)
+
+    def submit(self, c, d, s, u, gy, y, gc, gd, gs, gu):
+        b = self.sets[self.k % 2]
+        self.k += 1
+        main = torch.cuda.current_stream()
+        self.s_in.wait_stream(main)
+        if b["freed"] is not None:               # the set's previous step has been copied out
+            self.s_in.wait_event(b["freed"])
+        with torch.cuda.stream(self.s_in):
+            for key, h in (("c", c), ("d", d), ("s", s), ("u", u), ("gy", gy)):
+                b[key].copy_(h, non_blocking=True)
+            loaded = torch.cuda.Event()
+            loaded.record(self.s_in)
+        self.s_cmp.wait_event(loaded)
+        p = self.plan
+        p.factor_solve(b["c"], b["d"], b["s"], b["u"], b["y"], b["info"], self.ws, factor=self.fac,
+                       stream=self.s_cmp)
+        p.backward(b["c"], b["d"], b["s"], b["u"], b["y"], b["gy"], b["gc"], b["gd"], b["gs"], b["gu"],
+                   b["info_b"], self.ws, factor=self.fac, stream=self.s_cmp)
+        solved = torch.cuda.Event()
+        solved.record(self.s_cmp)
+        self.s_out.wait_event(solved)
+        with torch.cuda.stream(self.s_out):
+            for h, key in ((y, "y"), (gc, "gc"), (gd, "gd"), (gs, "gs"), (gu, "gu")):
+                h.copy_(b[key], non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(self.s_out)
+        b["freed"] = done
+        return b["info"], b["info_b"], done
+
+    def wait(self, stream=None):
+        st = torch.cuda.current_stream() if stream is None else stream
+        for s_ in (self.s_in, self.s_cmp, self.s_out):
+            st.wait_stream(s_)

@@ -210,11 +210,13 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(LevelTables lt, const Ts*
   const int64_t span = s_u[nch - 1] + s_len[nch - 1] - u0;   // contiguous user steps
   const int64_t es = int64_t(lt.L) * lt.G;
   if (kIn) {
+#pragma unroll 4
     for (int64_t x = threadIdx.x; x < span * K; x += blockDim.x) {
       Tr v = Tr(src[u0 * K + x]);
       buf[pad32(int(x))] = v;
     }
     __syncthreads();
+#pragma unroll 4
     for (int w = threadIdx.x; w < kTileChunks * lt.L; w += blockDim.x) {
       const int gl = w % kTileChunks, j = w / kTileChunks;
       if (gl >= nch || j >= s_len[gl]) continue;
@@ -227,6 +229,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(LevelTables lt, const Ts*
       }
     }
   } else {
+#pragma unroll 4
     for (int w = threadIdx.x; w < kTileChunks * lt.L; w += blockDim.x) {
       const int gl = w % kTileChunks, j = w / kTileChunks;
       if (gl >= nch || j >= s_len[gl]) continue;
@@ -240,6 +243,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(LevelTables lt, const Ts*
       }
     }
     __syncthreads();
+#pragma unroll 4
     for (int64_t x = threadIdx.x; x < span * K; x += blockDim.x) dst[u0 * K + x] = buf[pad32(int(x))];
   }
 }
@@ -431,17 +435,26 @@ __global__ void __launch_bounds__(kThreads, 4) k_backsub0(LevelTables lt, LevelB
 // Per-system stop test of the refinement after a sweep: with d_k = ||dy_k|| (this sweep's
 // correction) the error of y_k is estimated as d_k^2 / d_{k-1} (the sweep contracts the
 // error by ~d_k/d_{k-1}); a system whose estimate is <= tol ||y|| skips the remaining sweeps.
-// After the first sweep only d_1 <= tol/100 ||y|| stops.  The chunk partials are summed in
-// chunk order (deterministic).  On the last sweep an unconverged system gets info = -1.
+// After the first sweep only d_1 <= tol/100 ||y|| stops.  One warp per system: lane j sums
+// the chunk partials j, j+32, ... in order, then a fixed shuffle tree (deterministic).  On the
+// last sweep an unconverged system gets info = -1.
 __global__ void k_converge(int64_t S, const int64_t* coff0, const float* part, float* prev,
                            int32_t* skip, float tol, bool first, bool last, int32_t* info) {
-  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (i >= S || skip[i]) return;
+  const int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= S) return;   // whole warps: S rounds the grid to warps
+  if (skip[i]) return;
   float d2 = 0.f, y2 = 0.f;
-  for (int64_t g = coff0[i]; g < coff0[i + 1]; ++g) {
+  for (int64_t g = coff0[i] + lane; g < coff0[i + 1]; g += 32) {
     d2 += part[2 * g];
     y2 += part[2 * g + 1];
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    y2 += __shfl_xor_sync(0xffffffffu, y2, o);
+  }
+  if (lane != 0) return;
   const bool conv = first ? d2 <= 1e-4f * tol * tol * y2 : d2 <= tol * sqrtf(y2 * prev[i]);
   prev[i] = d2;
   if (conv) skip[i] = 1;
@@ -1527,7 +1540,7 @@ smnn_status refine_sweeps(const smnn_plan_s* pl, const Problem0& p, char* fac, c
     SMNN_TRY((solve_pass<float, NB, N>(pl, p, nullptr, false, fac, sol, oa, 2, info, st, &ri,
                                        adaptive ? b.skip : nullptr)));
     if (adaptive)
-      SMNN_LAUNCH(k_converge, pl->S, st, pl->S, pl->lv[0].d_coff, b.part, b.prev, b.skip,
+      SMNN_LAUNCH(k_converge, pl->S * 32, st, pl->S, pl->lv[0].d_coff, b.part, b.prev, b.skip,
                   float(pl->desc.refine_tol), it == 0, it + 1 == K, info);
   }
   return SMNN_OK;

@@ -342,3 +342,59 @@ def test_weight_gradients_match_oracle(prec, tol, store_factor):
                                       seq_T=prob.seq_T, factor=fac)
     for a, b in ((gc, gc2), (gd, gd2), (gs, gs2), (gu, gu2)):
         assert torch.equal(a, b)
+
+
+# ----------------------------------------------------------------------------- host pipeline
+
+@pytest.mark.parametrize("n_parts", [1, 3])
+def test_host_pipeline_matches_device_calls(n_parts):
+    """HostPipeline (pinned host buffers, parts of the batch on two streams) gives the forward
+    and adjoint results of one device call on the whole batch."""
+    import torch
+    import paper_2410_06074_b300 as pk
+    prob = random_problem(31, 8, 2, 300, 2).cast(np.float32)
+    gy = upstream_gradient(prob).astype(np.float32)
+    cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=pk.F32_REFINED_DF)
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            for a in (prob.c, prob.d, prob.s, prob.u, gy)]
+    outs = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (host[0], host[0], host[1], host[2], host[3])]
+    pipe = pk.HostPipeline((prob.R, prob.B, prob.D, prob.T), cfg, n_parts=n_parts)
+    info, info_b = pipe.run(*host, *outs)
+    torch.cuda.synchronize()
+    assert (info.cpu() == 0).all() and (info_b.cpu() == 0).all()
+    c, d, s, u, g = (t.cuda() for t in host)
+    y, _ = pk.solve(c, d, s, u, cfg)
+    ref = [y] + list(pk.gradients(c, d, s, u, y, g, cfg)[:4])
+    for got, want in zip(outs, ref):
+        want = want.cpu().double()
+        assert float((got.double() - want).norm() / want.norm()) <= 1e-6
+
+
+def test_host_stream_steps_match_device_calls():
+    """HostStream (three streams, two device buffer sets, the steps' transfers overlapped)
+    returns for every step exactly what the device calls return for that step's inputs."""
+    import torch
+    import paper_2410_06074_b300 as pk
+    cfg = pk.SolveConfig(R_init=1, T_init=1, precision=pk.F32_REFINED_DF)
+    steps = []
+    for seed in (41, 42, 43):
+        prob = random_problem(seed, 6, 2, 257, 2).cast(np.float32)
+        gy = upstream_gradient(prob, seed).astype(np.float32)
+        host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                for a in (prob.c, prob.d, prob.s, prob.u, gy)]
+        outs = [torch.empty(t.shape, dtype=t.dtype).pin_memory()
+                for t in (host[0], host[0], host[1], host[2], host[3])]
+        steps.append((host, outs))
+    hs = pk.HostStream((2, 6, 2, 257), cfg)
+    flags = [hs.submit(*h, *o) for h, o in steps]
+    hs.wait()
+    torch.cuda.synchronize()
+    for info, info_b, _ in flags[-2:]:   # a set's flags are reused two steps later
+        assert (info.cpu() == 0).all() and (info_b.cpu() == 0).all()
+    fac = pk.get_plan((2, 6, 2, 257), cfg).factor_buffer()   # the saved-factor path, as HostStream
+    for h, o in steps:
+        c, d, s, u, g = (t.cuda() for t in h)
+        y, _ = pk.solve(c, d, s, u, cfg, factor=fac)
+        ref = [y] + list(pk.gradients(c, d, s, u, y, g, cfg, factor=fac)[:4])
+        for got, want in zip(o, ref):
+            assert torch.equal(got, want.cpu())
