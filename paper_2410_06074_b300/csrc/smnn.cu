@@ -1032,7 +1032,7 @@ struct Level {
   int64_t* d_coff = nullptr;
   int64_t* d_P = nullptr;
   int64_t* d_base = nullptr;
-  size_t o_lf = 0, o_h = 0, o_ar = 0, o_al = 0, o_ec = 0;  // factor region (bytes)
+  size_t o_lh = 0, o_ar = 0, o_al = 0, o_ec = 0;  // factor region (bytes)
   size_t o_z = 0, o_br = 0, o_bl = 0, o_xs = 0;            // solve region (bytes)
 };
 
@@ -1184,8 +1184,8 @@ smnn_status build_plan_host(smnn_plan_s* pl) {
   size_t f = 0, s = 0;  // buffer layout
   for (auto& L : pl->lv) {
     const size_t GL = size_t(L.G) * size_t(L.L);
-    L.o_lf = f; f += align_up(GL * NT * es);
-    L.o_h = f;  f += align_up(GL * NB * NB * es);
+    const size_t V = 16 / es, RLH = (NT + NB * NB + V - 1) / V * V;   // FactorView's record
+    L.o_lh = f; f += align_up(GL * RLH * es);
     L.o_ar = f; f += align_up(size_t(L.G) * NT * es);
     L.o_al = f; f += align_up(size_t(L.G) * NT * es);
     L.o_ec = f; f += align_up(size_t(L.G) * NB * NB * es);
@@ -1284,8 +1284,7 @@ LevelTables tables_of(const Level& L) {
 template <class Tr, int NB>
 LevelBufs<Tr, NB> bufs_of(const Level& L, char* fac, char* sol) {
   LevelBufs<Tr, NB> b;
-  b.fac.lf = reinterpret_cast<Tr*>(fac + L.o_lf);
-  b.fac.h = reinterpret_cast<Tr*>(fac + L.o_h);
+  b.fac.lh = reinterpret_cast<Tr*>(fac + L.o_lh);
   b.fac.z = reinterpret_cast<Tr*>(sol + L.o_z);
   b.fac.G = L.G;
   b.fac.L = L.L;

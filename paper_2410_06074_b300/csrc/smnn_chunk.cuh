@@ -173,71 +173,65 @@ SMNN_HD void trsm_l(const Tr (&l)[NB][NB], const Tr (&inv)[NB], const Tr (&b)[NB
     }
   }
 }
+// Factor of one level.  Per in-chunk step j of chunk g, one record of RLH values holds L_t
+// packed lower with its inverse diagonal ((R+1)(R+2)/2 values), then the fill block H_t
+// ((R+1)^2 values, zero for a chunk without a left separator), padded to a multiple of 16
+// bytes: the records of step j lie at [(j*G + g) * RLH], so a warp's threads (consecutive
+// chunks g) move consecutive records, each with RLH*sizeof(Tr)/16 vector accesses.  z holds
+// the forward-sweep vectors z_t of the current right-hand side, element e at
+// [(e*L + j)*G + g] (scalar, coalesced: a 16-byte record would add a third to its bytes).
+template <class Tr> struct Vec16;
+template <> struct Vec16<float> { using T = float4; };
+template <> struct Vec16<double> { using T = double2; };
 
-// ----------------------------------------------------------------------------- factor I/O
-
-// Factor of one level, stored chunk-interleaved so that a warp's threads (consecutive
-// chunks g) touch consecutive addresses: element e of in-chunk step j of chunk g sits at
-// [(e*L + j)*G + g].  lf holds L_t packed lower with the inverse diagonal, h the fill
-// blocks H_t, z the forward-sweep vectors z_t of the current right-hand side.
 template <class Tr, int NB>
 struct FactorView {
-  Tr* lf;
-  Tr* h;
+  static constexpr int NT = NB * (NB + 1) / 2;
+  static constexpr int V = 16 / int(sizeof(Tr));                 // values per 16-byte vector
+  static constexpr int RLH = (NT + NB * NB + V - 1) / V * V;     // record length
+  static constexpr int NV = RLH / V;                             // vectors per record
+  using Vec = typename Vec16<Tr>::T;
+  Tr* lh;
   Tr* z;
   int64_t G;
   int L;
   SMNN_HD int64_t at(int e, int j, int64_t g) const { return (int64_t(e) * L + j) * G + g; }
+  SMNN_HD int64_t rec(int j, int64_t g) const { return (int64_t(j) * G + g) * RLH; }
 
-  SMNN_HD void store_l(int j, int64_t g, const Tr (&l)[NB][NB], const Tr (&inv)[NB]) const {
+  // One step's L_t (with its inverse diagonal) and H_t (zero without a left separator).
+  SMNN_HD void store_lh(int j, int64_t g, const Tr (&l)[NB][NB], const Tr (&inv)[NB],
+                        const Tr (&m)[NB][NB], bool with_h) const {
+    union { Tr v[RLH]; Vec w[NV]; } r;
 #pragma unroll
     for (int a = 0; a < NB; ++a)
 #pragma unroll
-      for (int b = 0; b <= a; ++b) lf[at(tri(a, b), j, g)] = a == b ? inv[a] : l[a][b];
-  }
-  SMNN_HD void load_l(int j, int64_t g, Tr (&l)[NB][NB], Tr (&inv)[NB]) const {
+      for (int b = 0; b <= a; ++b) r.v[tri(a, b)] = a == b ? inv[a] : l[a][b];
 #pragma unroll
     for (int a = 0; a < NB; ++a)
 #pragma unroll
-      for (int b = 0; b <= a; ++b) {
-        const Tr v = lf[at(tri(a, b), j, g)];
-        if (a == b) inv[a] = v; else l[a][b] = v;
-      }
-  }
-  SMNN_HD void store_h(int j, int64_t g, const Tr (&m)[NB][NB]) const {
+      for (int b = 0; b < NB; ++b) r.v[NT + a * NB + b] = with_h ? m[a][b] : Tr(0);
 #pragma unroll
-    for (int a = 0; a < NB; ++a)
+    for (int e = NT + NB * NB; e < RLH; ++e) r.v[e] = Tr(0);
+    Vec* dst = reinterpret_cast<Vec*>(lh + rec(j, g));
 #pragma unroll
-      for (int b = 0; b < NB; ++b) h[at(a * NB + b, j, g)] = m[a][b];
-  }
-  SMNN_HD void load_h(int j, int64_t g, Tr (&m)[NB][NB]) const {
-#pragma unroll
-    for (int a = 0; a < NB; ++a)
-#pragma unroll
-      for (int b = 0; b < NB; ++b) m[a][b] = h[at(a * NB + b, j, g)];
+    for (int q = 0; q < NV; ++q) dst[q] = r.w[q];
   }
   SMNN_HD void store_z(int j, int64_t g, const Tr (&v)[NB]) const {
 #pragma unroll
     for (int a = 0; a < NB; ++a) z[at(a, j, g)] = v[a];
   }
-  SMNN_HD void load_z(int j, int64_t g, Tr (&v)[NB]) const {
-#pragma unroll
-    for (int a = 0; a < NB; ++a) v[a] = z[at(a, j, g)];
-  }
 
   // Raw stored data of one step, loaded ahead of its use by the pipelined sweeps.
   struct Raw {
-    Tr l[NB * (NB + 1) / 2];
-    Tr h[NB * NB];
+    union { Tr v[RLH]; Vec w[NV]; } lh;
     Tr z[NB];
   };
   SMNN_HD void load_raw(int j, int64_t g, Raw& r, bool with_h, bool with_z) const {
+    const Vec* src = reinterpret_cast<const Vec*>(lh + rec(j, g));
+    constexpr int NVL = (NT + V - 1) / V;   // vectors holding L
 #pragma unroll
-    for (int e = 0; e < NB * (NB + 1) / 2; ++e) r.l[e] = ld_ro(lf + at(e, j, g));
-    if (with_h) {
-#pragma unroll
-      for (int e = 0; e < NB * NB; ++e) r.h[e] = ld_ro(h + at(e, j, g));
-    }
+    for (int q = 0; q < NV; ++q)
+      if (q < NVL || with_h) r.lh.w[q] = ld_ro(src + q);
     if (with_z) {
 #pragma unroll
       for (int e = 0; e < NB; ++e) r.z[e] = ld_ro(z + at(e, j, g));
@@ -248,14 +242,14 @@ struct FactorView {
     for (int a = 0; a < NB; ++a)
 #pragma unroll
       for (int b = 0; b <= a; ++b) {
-        if (a == b) inv[a] = r.l[tri(a, b)]; else l[a][b] = r.l[tri(a, b)];
+        if (a == b) inv[a] = r.lh.v[tri(a, b)]; else l[a][b] = r.lh.v[tri(a, b)];
       }
   }
   static SMNN_HD void unpack_h(const Raw& r, Tr (&m)[NB][NB]) {
 #pragma unroll
     for (int a = 0; a < NB; ++a)
 #pragma unroll
-      for (int b = 0; b < NB; ++b) m[a][b] = r.h[a * NB + b];
+      for (int b = 0; b < NB; ++b) m[a][b] = r.lh.v[NT + a * NB + b];
   }
 };
 
@@ -496,7 +490,6 @@ SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
 #pragma unroll
         for (int b = 0; b < NB; ++b) Lm[a][b] = D[a][b];
       if (!chol<Tr, NB>(Lm, inv) && fail == 0) fail = t + 1;
-      fac.store_l(j, g, Lm, inv);
     } else {
       FactorView<Tr, NB>::unpack_l(cur, Lm, inv);
     }
@@ -506,10 +499,12 @@ SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
     trsv_l<Tr, NB>(Lm, inv, z);
     fac.store_z(j, g, z);
     Tr Hm[NB][NB];
+    if (kFactor) {
+      if (has_left) trsm_l<Tr, NB>(Lm, inv, Gm, Hm);
+      fac.store_lh(j, g, Lm, inv, Hm, has_left);
+    }
     if (has_left) {
       if (kFactor) {
-        trsm_l<Tr, NB>(Lm, inv, Gm, Hm);
-        fac.store_h(j, g, Hm);
 #pragma unroll
         for (int a = 0; a < NB; ++a)
 #pragma unroll
