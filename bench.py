@@ -33,7 +33,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from smnn_workloads import config2, mse_target  # noqa: E402
+from smnn_workloads import config2, mse_target, upstream_gradient  # noqa: E402
 
 WORKLOAD = "config2: B=512 D=8 T=1024 R=2, FP32 factor + float-float/FP64-residual refinement, fwd+adjoint"
 METRIC = "time-steps solved/s fwd+bwd (FP32-refined, <=1e-6 vs FP64 oracle)"
@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
     ap.add_argument("--chunk", type=int, default=0, help="level-0 chunk length (0: plan's table)")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="skip the secondary config-4 and config-3b timings")
     ap.add_argument("--algo", default="auto", choices=sorted(ALGOS),
                     help="reduction: auto (the plan's choice), seq, cr (a launch per level), "
                          "fused (a launch per solve pass)")
@@ -332,6 +334,46 @@ def run_ours(args, ws, rank, local):
     return prob, p32, variants, results, stream, flush, dev
 
 
+def other_configs(args, ws, stream, flush):
+    """Forward + adjoint time of the other large workloads (library defaults, saved factor,
+    L2 flushed between steps): config 4 (4096 ragged systems, T in [32, 65536], R = 2) and
+    config 3b (4 systems of 2^20 steps, R = 3) on SMNN_F32_REFINED_DF.  Secondary lines: their
+    accuracy against the oracle is covered by the full-size tests."""
+    import torch
+    import paper_2410_06074_b300 as pk
+    from smnn_workloads import config3b, config4
+    out = {}
+    for name, make in (("config4", config4), ("config3b", config3b)):
+        prob = make().cast(np.float32)
+        seq_T = None if prob.seq_T is None else tuple(int(x) for x in prob.seq_T)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        c, d, s, u = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (prob.c, prob.d, prob.s, prob.u))
+        gy = torch.from_numpy(upstream_gradient(prob).astype(np.float32)).to(dev)
+        cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=pk.F32_REFINED_DF)
+        plan = pk.get_plan(pk.api._shape_key(c, s, prob.D, seq_T), cfg)
+        wsb, fac = plan.workspace(dev), plan.factor_buffer(dev)
+        y = torch.empty_like(c)
+        info, info_b = (torch.empty(plan.S, dtype=torch.int32, device=dev) for _ in range(2))
+        g = [torch.empty_like(t) for t in (c, d, s, u)]
+
+        def step():
+            plan.factor_solve(c, d, s, u, y, info, wsb, factor=fac)
+            plan.backward(c, d, s, u, y, gy, *g, info_b, wsb, factor=fac)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        barrier(ws)
+        ms = max_over_ranks(timed(step, max(3, args.steps // 4), stream, flush), ws) / max(3, args.steps // 4)
+        bad = int((info != 0).sum()) + int((info_b != 0).sum())
+        st = plan.stats()
+        out[name] = {"workload": prob.name, "time_steps_per_pass": prob.steps, "ms_per_step": ms,
+                     "value": ws * prob.steps / (ms / 1e3), "unit": UNIT, "flagged_systems": bad,
+                     "levels": int(st.num_levels), "chunks": [int(x) for x in st.chunk][:int(st.num_levels)]}
+        del c, d, s, u, gy, wsb, fac, y, g
+        torch.cuda.empty_cache()
+    return out
+
+
 def e2e_and_roofline(prob, v, res, ws, args, stream, flush):
     """End-to-end rate through the public API with host buffers, and the roofline of the
     dominant kernel of variant v."""
@@ -488,6 +530,7 @@ def main():
     head = max(pool, key=lambda n: results[n]["value"])
     r = results[head]
     e2e, roof, whole = e2e_and_roofline(prob, variants[head], r, ws, args, stream, flush)
+    others = None if args.no_other_configs else other_configs(args, ws, stream, flush)
     prec_txt = {"F32_REFINED_DF": "FP32 factor + float-float residual refinement",
                 "F32_REFINED": "FP32 factor + FP64 residual refinement"}[head]
     out = {
@@ -519,6 +562,8 @@ def main():
                         "between launches",
         "accuracy_vs_oracle": acc,
     }
+    if others is not None:
+        out["other_configs"] = others
     if cpu is not None:
         out["cpu_baseline"] = cpu
     if rank == 0:
