@@ -264,13 +264,13 @@ __global__ void __launch_bounds__(kThreads) k_gather_s(LevelTables lt, Problem0 
 
 // The per-chunk bodies of the level kernels (one thread = one chunk g of a level), shared by
 // the one-launch-per-level kernels and the fused per-CTA pass (k_pass).
-template <class Tr, int NB, bool kFactor>
+template <class Tr, int NB, bool kFactor, bool kRO>
 __device__ __forceinline__ void dev_elim0(const LevelTables& lt, const LevelBufs<Tr, NB>& lb,
                                           const Problem0& p, const L0In<Tr>& in, const Tr* rhs,
                                           int32_t* info, int64_t g, bool top) {
   const ChunkPos cp = chunk_pos(lt, g);
   CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, in, rhs, cp.i, g, cp.first, cp.T, lt.L, lt.G);
-  int64_t fail = elim_chunk<Tr, NB, kFactor>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
+  int64_t fail = elim_chunk<Tr, NB, kFactor, kRO>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
   if (top) {
     if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = cp.last + 1;
   }
@@ -285,17 +285,18 @@ __global__ void __launch_bounds__(kThreads, kFactor ? SMNN_FACTOR_MIN_BLOCKS : 4
                                                     L0In<Tr> in, const Tr* rhs, int32_t* info) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  dev_elim0<Tr, NB, kFactor>(lt, lb, p, in, rhs, info, g, kTop);
+  dev_elim0<Tr, NB, kFactor, true>(lt, lb, p, in, rhs, info, g, kTop);
 }
 
-template <class Tr, int NB, bool kFactor>
+template <class Tr, int NB, bool kFactor, bool kRO>
 __device__ __forceinline__ void dev_elimN(const LevelTables& lt, const LevelBufs<Tr, NB>& lb,
                                           const ChunkOut<Tr, NB>& prev, const int64_t* T0,
                                           int32_t* info, const int32_t* skip, int64_t g, bool top) {
   const ChunkPos cp = chunk_pos(lt, g);
   if (skip && skip[cp.i]) return;
   ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[cp.i], cp.T);
-  int64_t fail = elim_chunk<Tr, NB, kFactor>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
+  src.stage_a = kFactor;
+  int64_t fail = elim_chunk<Tr, NB, kFactor, kRO>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
   if (top) {
     if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = cp.last + 1;
   }
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(kThreads) k_elimN(LevelTables lt, LevelBufs<Tr
                                                     int32_t* info, const int32_t* skip) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  dev_elimN<Tr, NB, kFactor>(lt, lb, prev, T0, info, skip, g, kTop);
+  dev_elimN<Tr, NB, kFactor, true>(lt, lb, prev, T0, info, skip, g, kTop);
 }
 
 // Emit functor of level >= 1 back substitution: values of this level's unknowns.
@@ -329,7 +330,7 @@ struct EmitX {
   }
 };
 
-template <class Tr, int NB>
+template <class Tr, int NB, bool kRO>
 __device__ __forceinline__ void dev_backsubN(const LevelTables& lt, const LevelBufs<Tr, NB>& lb,
                                              const ChunkOut<Tr, NB>& prev, Tr* x_prev,
                                              const int32_t* skip, int64_t g) {
@@ -337,7 +338,7 @@ __device__ __forceinline__ void dev_backsubN(const LevelTables& lt, const LevelB
   if (skip && skip[cp.i]) return;
   const ReducedSource<Tr, NB> src = make_reduced<Tr, NB>(prev, lt.base[cp.i], cp.T);
   EmitX<Tr, NB> emit{x_prev + lt.base[cp.i] * NB};
-  backsub_chunk<Tr, NB>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.xsep + g * NB,
+  backsub_chunk<Tr, NB, kRO>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.xsep + g * NB,
                         cp.k > 0 ? lb.xsep + (g - 1) * NB : nullptr, emit);
 }
 
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(kThreads) k_backsubN(LevelTables lt, LevelBufs
                                                        const int32_t* skip) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  dev_backsubN<Tr, NB>(lt, lb, prev, x_prev, skip, g);
+  dev_backsubN<Tr, NB, true>(lt, lb, prev, x_prev, skip, g);
 }
 
 // Level-0 output of a solve pass, interleaved.  mode 0: x = v.  mode 1 (FP32 refinement):
@@ -406,7 +407,7 @@ struct EmitY {
   }
 };
 
-template <class Tr, int NB, int kMode>
+template <class Tr, int NB, int kMode, bool kRO>
 __device__ __forceinline__ void dev_backsub0(const LevelTables& lt, const LevelBufs<Tr, NB>& lb,
                                              const Problem0& p, const L0In<Tr>& in,
                                              const Level0Out<Tr>& o, const int32_t* info,
@@ -415,7 +416,7 @@ __device__ __forceinline__ void dev_backsub0(const LevelTables& lt, const LevelB
   if (skip && skip[cp.i]) return;
   const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, in, nullptr, cp.i, g, cp.first, cp.T, lt.L, lt.G);
   EmitY<Tr, NB, kMode> emit{o, g, lt.G, cp.first, lt.L, info[cp.i] > 0, 0.f, 0.f};
-  backsub_chunk<Tr, NB>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.xsep + g * NB,
+  backsub_chunk<Tr, NB, kRO>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.xsep + g * NB,
                         cp.k > 0 ? lb.xsep + (g - 1) * NB : nullptr, emit);
   if (kMode == 2 && o.part) {
     o.part[2 * g] = emit.dd;
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_backsub0(LevelTables lt, LevelB
                                                        const int32_t* info, const int32_t* skip) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  dev_backsub0<Tr, NB, kMode>(lt, lb, p, in, o, info, skip, g);
+  dev_backsub0<Tr, NB, kMode, true>(lt, lb, p, in, o, info, skip, g);
 }
 
 // Per-system stop test of the refinement after a sweep: with d_k = ||dy_k|| (this sweep's
@@ -579,6 +580,7 @@ struct ResidualSource {
   const float* xl;
   const float* rhs;     // explicit right-hand side (interleaved) or nullptr for beta
   const float* u;
+  bool ro_x;            // x is not written during the kernel (read-only loads allowed)
   N wg2, wi2, ws2;
   int64_t last;
   N xc[NB], carry[NB];
@@ -590,7 +592,11 @@ struct ResidualSource {
   __device__ void load(int64_t t, N (&v)[NB]) const {
     const int64_t k = idx(t), es = cs.es();
 #pragma unroll
-    for (int a = 0; a < NB; ++a) v[a] = Num<N>::pair(ld_ro(xh + a * es + k), xl ? ld_ro(xl + a * es + k) : 0.f);
+    for (int a = 0; a < NB; ++a) {
+      const float h = ro_x ? ld_ro(xh + a * es + k) : xh[a * es + k];
+      const float l = xl ? (ro_x ? ld_ro(xl + a * es + k) : xl[a * es + k]) : 0.f;
+      v[a] = Num<N>::pair(h, l);
+    }
   }
   // raw inputs of the next step, loaded one call ahead
   float pc[NB], prh[NB], pd, ps;
@@ -668,7 +674,7 @@ struct ResidualSource {
 };
 
 // Level-0 replay of the stored FP32 factor on the refinement residual (fused, see above).
-template <class N, int NB>
+template <class N, int NB, bool kRO>
 __device__ __forceinline__ void dev_elim0_res(const LevelTables& lt, const LevelBufs<float, NB>& lb,
                                               const Problem0& p, const L0In<float>& in,
                                               const float* x_hi, const float* x_lo,
@@ -682,12 +688,13 @@ __device__ __forceinline__ void dev_elim0_res(const LevelTables& lt, const Level
   src.xl = x_lo;
   src.rhs = rhs;
   src.u = src.cs.u;
+  src.ro_x = kRO;
   src.wg2 = Num<N>::from_d(p.wg2);
   src.wi2 = Num<N>::from_d(p.wi2);
   src.ws2 = Num<N>::from_d(p.ws2);
   src.last = cp.last;
   src.init();
-  elim_chunk<float, NB, false>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
+  elim_chunk<float, NB, false, kRO>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
   if (top) solve_top<float, NB>(lb.out, g, lb.xsep + g * NB);
 }
 
@@ -698,7 +705,7 @@ __global__ void __launch_bounds__(kThreads) k_elim0_res(LevelTables lt, LevelBuf
                                                         const int32_t* skip) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  dev_elim0_res<N, NB>(lt, lb, p, in, x_hi, x_lo, rhs, skip, g, kTop);
+  dev_elim0_res<N, NB, true>(lt, lb, p, in, x_hi, x_lo, rhs, skip, g, kTop);
 }
 
 // One whole solve pass in one launch, for plans whose systems fit a CTA at every level: the
@@ -720,10 +727,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass(const __grid_constant__ Fu
     const int64_t g = lt.coff[s0] + threadIdx.x;
     if (g < lt.coff[s1]) {
       if constexpr (kSrc == 2) {
-        dev_elim0_res<N, NB>(lt, fl.lb[0], p, in, x_hi, x_lo, rhs, skip, g, nl == 1);
+        // x is accumulated by this launch's back substitution: plain loads
+        dev_elim0_res<N, NB, false>(lt, fl.lb[0], p, in, x_hi, x_lo, rhs, skip, g, nl == 1);
       } else {
         if (!(skip && skip[lt.csys[g]]))
-          dev_elim0<Tr, NB, kSrc == 0>(lt, fl.lb[0], p, in, rhs, info, g, nl == 1);
+          dev_elim0<Tr, NB, kSrc == 0, false>(lt, fl.lb[0], p, in, rhs, info, g, nl == 1);
       }
     }
   }
@@ -732,18 +740,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass(const __grid_constant__ Fu
     const LevelTables& lt = fl.lt[l];
     const int64_t g = lt.coff[s0] + threadIdx.x;
     if (g < lt.coff[s1])
-      dev_elimN<Tr, NB, kSrc == 0>(lt, fl.lb[l], fl.lb[l - 1].out, fl.T0, info, skip, g, l == nl - 1);
+      dev_elimN<Tr, NB, kSrc == 0, false>(lt, fl.lb[l], fl.lb[l - 1].out, fl.T0, info, skip, g, l == nl - 1);
   }
   for (int l = nl - 1; l >= 1; --l) {
     __syncthreads();
     const LevelTables& lt = fl.lt[l];
     const int64_t g = lt.coff[s0] + threadIdx.x;
-    if (g < lt.coff[s1]) dev_backsubN<Tr, NB>(lt, fl.lb[l], fl.lb[l - 1].out, fl.lb[l - 1].xsep, skip, g);
+    if (g < lt.coff[s1]) dev_backsubN<Tr, NB, false>(lt, fl.lb[l], fl.lb[l - 1].out, fl.lb[l - 1].xsep, skip, g);
   }
   __syncthreads();
   const LevelTables& lt = fl.lt[0];
   const int64_t g = lt.coff[s0] + threadIdx.x;
-  if (g < lt.coff[s1]) dev_backsub0<Tr, NB, kMode>(lt, fl.lb[0], p, in, o, info, skip, g);
+  if (g < lt.coff[s1]) dev_backsub0<Tr, NB, kMode, false>(lt, fl.lb[0], p, in, o, info, skip, g);
 }
 
 // Levels from..top of a solve pass in one launch, for plans whose level-0 chunks exceed a CTA:
@@ -760,13 +768,13 @@ __global__ void __launch_bounds__(kThreads) k_upper(const __grid_constant__ Fuse
     const LevelTables& lt = fl.lt[l];
     const int64_t g = lt.coff[s0] + threadIdx.x;
     if (g < lt.coff[s1])
-      dev_elimN<Tr, NB, kFactor>(lt, fl.lb[l], fl.lb[l - 1].out, fl.T0, info, skip, g, l == nl - 1);
+      dev_elimN<Tr, NB, kFactor, false>(lt, fl.lb[l], fl.lb[l - 1].out, fl.T0, info, skip, g, l == nl - 1);
   }
   for (int l = nl - 1; l >= fl.from; --l) {
     __syncthreads();
     const LevelTables& lt = fl.lt[l];
     const int64_t g = lt.coff[s0] + threadIdx.x;
-    if (g < lt.coff[s1]) dev_backsubN<Tr, NB>(lt, fl.lb[l], fl.lb[l - 1].out, fl.lb[l - 1].xsep, skip, g);
+    if (g < lt.coff[s1]) dev_backsubN<Tr, NB, false>(lt, fl.lb[l], fl.lb[l - 1].out, fl.lb[l - 1].xsep, skip, g);
   }
 }
 

@@ -226,15 +226,19 @@ struct FactorView {
     union { Tr v[RLH]; Vec w[NV]; } lh;
     Tr z[NB];
   };
+  // kRO: no thread writes lh or z during the kernel, so the loads may take the read-only path
+  // (one level per launch); the fused launches write a level's factor and z earlier in the
+  // same kernel and read them with plain loads.
+  template <bool kRO>
   SMNN_HD void load_raw(int j, int64_t g, Raw& r, bool with_h, bool with_z) const {
     const Vec* src = reinterpret_cast<const Vec*>(lh + rec(j, g));
     constexpr int NVL = (NT + V - 1) / V;   // vectors holding L
 #pragma unroll
     for (int q = 0; q < NV; ++q)
-      if (q < NVL || with_h) r.lh.w[q] = ld_ro(src + q);
+      if (q < NVL || with_h) r.lh.w[q] = kRO ? ld_ro(src + q) : src[q];
     if (with_z) {
 #pragma unroll
-      for (int e = 0; e < NB; ++e) r.z[e] = ld_ro(z + at(e, j, g));
+      for (int e = 0; e < NB; ++e) r.z[e] = kRO ? ld_ro(z + at(e, j, g)) : z[at(e, j, g)];
     }
   }
   static SMNN_HD void unpack_l(const Raw& r, Tr (&l)[NB][NB], Tr (&inv)[NB]) {
@@ -400,22 +404,58 @@ struct ReducedSource {
   const Tr* b_left;
   int64_t P;  // steps of this system at this level
 
+  // One-step-ahead staging, as CoefSource's: prime(k) issues the loads of step k's
+  // right-hand side (and, with stage_a, its diagonal block), commit(k) makes them current.
+  // Plain loads: in the fused launches the previous level wrote these in the same kernel.
+  bool stage_a = false;
+  struct Stage {
+    Tr b[NB], bn[NB];
+    Tr a[NT], an[NT];
+  };
+  Stage cur, nxt;
+  int64_t cur_t = -1;
+  SMNN_HD void prime(int64_t k) {
+    const bool more = k + 1 < P;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      nxt.b[i] = b_right[k * NB + i];
+      nxt.bn[i] = more ? b_left[(k + 1) * NB + i] : Tr(0);
+    }
+    if (stage_a) {
+#pragma unroll
+      for (int e = 0; e < NT; ++e) {
+        nxt.a[e] = a_right[k * NT + e];
+        nxt.an[e] = more ? a_left[(k + 1) * NT + e] : Tr(0);
+      }
+    }
+  }
+  SMNN_HD void commit(int64_t k) {
+    cur = nxt;
+    cur_t = k;
+  }
+
   SMNN_HD void A(int64_t k, Tr (&a)[NB][NB]) const {
-    const bool nxt = k + 1 < P;
+    const bool nxt_ = k + 1 < P;
+    const bool st = stage_a && k == cur_t;
 #pragma unroll
     for (int i = 0; i < NB; ++i)
 #pragma unroll
       for (int j = 0; j <= i; ++j) {
-        Tr v = a_right[k * NT + tri(i, j)];
-        if (nxt) v += a_left[(k + 1) * NT + tri(i, j)];
+        Tr v = st ? cur.a[tri(i, j)] + cur.an[tri(i, j)] : a_right[k * NT + tri(i, j)];
+        if (!st && nxt_) v += a_left[(k + 1) * NT + tri(i, j)];
         a[i][j] = v;
         a[j][i] = v;
       }
   }
   SMNN_HD void b(int64_t k, Tr (&v)[NB]) const {
-    const bool nxt = k + 1 < P;
+    if (k == cur_t) {
 #pragma unroll
-    for (int i = 0; i < NB; ++i) v[i] = b_right[k * NB + i] + (nxt ? b_left[(k + 1) * NB + i] : Tr(0));
+      for (int i = 0; i < NB; ++i) v[i] = cur.b[i] + cur.bn[i];
+      return;
+    }
+    const bool nxt_ = k + 1 < P;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) v[i] = b_right[k * NB + i] + (nxt_ ? b_left[(k + 1) * NB + i] : Tr(0));
   }
   struct ERaw {
     Tr v[NB * NB];
@@ -433,8 +473,6 @@ struct ReducedSource {
       for (int j = 0; j < NB; ++j) e[i][j] = r.v[i * NB + j];
   }
   SMNN_HD void E(int64_t k, Tr (&e)[NB][NB]) const { e_from(load_e(k), e); }
-  SMNN_HD void prime(int64_t) {}
-  SMNN_HD void commit(int64_t) {}
 };
 
 // ----------------------------------------------------------------------------- chunk sweeps
@@ -443,7 +481,7 @@ struct ReducedSource {
 // and store L_t, H_t and the separator's reduced blocks; otherwise read the stored factor and
 // only carry the right-hand side.  src.b is called for first, first+1, ..., last in order.
 // Returns 0, or 1 + the step index of the first bad pivot.
-template <class Tr, int NB, bool kFactor, class Src>
+template <class Tr, int NB, bool kFactor, bool kRO, class Src>
 SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
                            const FactorView<Tr, NB>& fac, int64_t g, const ChunkOut<Tr, NB>& out) {
   constexpr int NT = NB * (NB + 1) / 2;
@@ -469,7 +507,7 @@ SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
   Raw cur;
   ERaw ecur;
   if (!kFactor && first < last) {
-    fac.load_raw(0, g, cur, has_left, false);
+    fac.template load_raw<kRO>(0, g, cur, has_left, false);
     ecur = src.load_e(first);
   }
   for (int64_t t = first; t < last; ++t) {
@@ -481,7 +519,7 @@ SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
     ERaw enxt;
     const bool more = !kFactor && t + 1 < last;
     if (more) {
-      fac.load_raw(j + 1, g, nxt, has_left, false);
+      fac.template load_raw<kRO>(j + 1, g, nxt, has_left, false);
       enxt = src.load_e(t + 1);
     }
     if (kFactor) {
@@ -617,7 +655,7 @@ SMNN_HD bool solve_top(const ChunkOut<Tr, NB>& out, int64_t g, Tr* x) {
 // separator).  emit(t, x, emit.fetch(t)) receives every step of the chunk, separator
 // included; the stored data of step t-1 (and emit's prefetch) are loaded while step t is
 // computed.
-template <class Tr, int NB, class Src, class Emit>
+template <class Tr, int NB, bool kRO, class Src, class Emit>
 SMNN_HD void backsub_chunk(const Src& src, int64_t first, int64_t last, bool has_left,
                            const FactorView<Tr, NB>& fac, int64_t g, const Tr* x_right,
                            const Tr* x_left, Emit& emit) {
@@ -635,7 +673,7 @@ SMNN_HD void backsub_chunk(const Src& src, int64_t first, int64_t last, bool has
   Raw cur;
   ERaw ecur;
   Pre pcur;
-  fac.load_raw(int(last - 1 - first), g, cur, has_left, true);
+  fac.template load_raw<kRO>(int(last - 1 - first), g, cur, has_left, true);
   ecur = src.load_e(last - 1);
   pcur = emit.fetch(last - 1);
   for (int64_t t = last - 1; t >= first; --t) {
@@ -644,7 +682,7 @@ SMNN_HD void backsub_chunk(const Src& src, int64_t first, int64_t last, bool has
     ERaw enxt;
     Pre pnxt;
     if (more) {
-      fac.load_raw(int(t - 1 - first), g, nxt, has_left, true);
+      fac.template load_raw<kRO>(int(t - 1 - first), g, nxt, has_left, true);
       enxt = src.load_e(t - 1);
       pnxt = emit.fetch(t - 1);
     }
