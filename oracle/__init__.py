@@ -10,10 +10,13 @@ dense Cholesky, or by Householder QR; Eq. 14 / App. A.3 chain rule for the gradi
 and which pins tie it to the paper.  This module only compiles that file and marshals
 numpy arrays into it.
 
-Array conventions (one "system" = one (sequence, dimension) pair, V = Q = 1):
-  uniform batch:  c [B, D, T, R+1], d [B, D, T], s [B, T], u [B, D, T_init, R_init+1]
-  ragged batch:   c [sum_i T_i, R+1], d [sum_i T_i], s [sum_b T_b], u [S, T_init, R_init+1]
+Array conventions (one "system" = one (sequence, dimension) pair of V variables with Q
+governing equations per step; nb = V(R+1) unknowns per step, variable-major):
+  uniform batch:  c [B, D, T, Q*nb], d [B, D, T, Q], s [B, T], u [B, D, T_init, V*(R_init+1)]
+  ragged batch:   c [sum_i T_i, Q*nb], d [sum_i T_i, Q], s [sum_b T_b], u [S, T_init, V*(R_init+1)]
                   with ``seq_T`` giving T_b per sequence; system i = b*D + dd.
+  With V = Q = 1 the trailing unit dimensions may be left out (c [..., R+1], d [B, D, T]).
+  Solutions y have the layout of c with nb values per step.
 """
 from __future__ import annotations
 
@@ -41,8 +44,8 @@ def build(force: bool = False) -> str:
 
 class _Params(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int32), ("R_init", ctypes.c_int32), ("T_init", ctypes.c_int32),
-                ("pad_", ctypes.c_int32), ("w_gov", ctypes.c_double), ("w_init", ctypes.c_double),
-                ("w_smooth", ctypes.c_double)]
+                ("V", ctypes.c_int32), ("Q", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("w_gov", ctypes.c_double), ("w_init", ctypes.c_double), ("w_smooth", ctypes.c_double)]
 
 
 @dataclass(frozen=True)
@@ -54,9 +57,16 @@ class Params:
     w_gov: float = 1.0
     w_init: float = 1.0
     w_smooth: float = 1.0
+    V: int = 1
+    Q: int = 1
+
+    @property
+    def nb(self) -> int:
+        return self.V * (self.R + 1)
 
     def c(self) -> _Params:
-        return _Params(self.R, self.R_init, self.T_init, 0, self.w_gov, self.w_init, self.w_smooth)
+        return _Params(self.R, self.R_init, self.T_init, self.V, self.Q, 0, self.w_gov, self.w_init,
+                       self.w_smooth)
 
 
 _P = ctypes.POINTER
@@ -115,8 +125,14 @@ class _Layout:
     soff: np.ndarray    # [S] offset of each system's step sizes in s
 
 
+def _y_like(p: Params, c, seq_T) -> np.ndarray:
+    """Solution array: c's leading (step) dimensions with nb values per step."""
+    lead = c.shape[:3] if seq_T is None else c.shape[:1]
+    return np.zeros(lead + (p.nb,))
+
+
 def _layout(c, D: int | None, seq_T) -> _Layout:
-    if seq_T is None:  # uniform: c [B, D, T, nb]
+    if seq_T is None:  # uniform: c [B, D, T, ...]
         B, Dd, T = c.shape[0], c.shape[1], c.shape[2]
         S = B * Dd
         T_sys = np.full(S, T, np.int64)
@@ -146,7 +162,7 @@ def dense_system(p: Params, c, d, s, u):
     """Explicit (A, b, w) of one system: c [T, R+1], d [T], s [T], u [T_init, R_init+1]."""
     c, d, s, u = _f64(c), _f64(d), _f64(s), _f64(u)
     T = c.shape[0]
-    m, n = num_rows(p, T), T * (p.R + 1)
+    m, n = num_rows(p, T), T * p.nb
     A = np.zeros((m, n)); b = np.zeros(m); w = np.zeros(m)
     _load().orc_dense_system(ctypes.byref(p.c()), T, _ptr(c), _ptr(d), _ptr(s), _ptr(u),
                              _ptr(A), _ptr(b), _ptr(w))
@@ -157,7 +173,7 @@ def normal_band(p: Params, c, d, s, u):
     """Lower band of M (rows i, offsets i-j = 0..kd) and beta of one system."""
     c, d, s, u = _f64(c), _f64(d), _f64(s), _f64(u)
     T = c.shape[0]
-    n = T * (p.R + 1)
+    n = T * p.nb
     kd = int(_load().orc_band_width(ctypes.byref(p.c())))
     band = np.zeros((n, kd + 1)); beta = np.zeros(n)
     _load().orc_normal_band(ctypes.byref(p.c()), T, _ptr(c), _ptr(d), _ptr(s), _ptr(u),
@@ -181,7 +197,7 @@ def solve(p: Params, c, d, s, u, *, D: int | None = None, seq_T=None, mode: str 
     (dense Cholesky of M) or 'qr' (Householder QR of W^{1/2} A).  Returns (y, info)."""
     c, d, s, u = _f64(c), _f64(d), _f64(s), _f64(u)
     L = _layout(c, D, seq_T)
-    y = np.zeros_like(c)
+    y = _y_like(p, c, seq_T)
     info = np.zeros(L.S, np.int32)
     args = (ctypes.byref(p.c()), L.S, _ptr(L.T_sys, ctypes.c_int64), _ptr(L.off, ctypes.c_int64),
             _ptr(L.soff, ctypes.c_int64), _ptr(c), _ptr(d), _ptr(s), _ptr(u), _ptr(y),
@@ -204,8 +220,8 @@ def gradient(p: Params, c, d, s, u, gy, *, D: int | None = None, seq_T=None, nth
     the importance weights being shared by every system of the batch (summed in order)."""
     c, d, s, u, gy = _f64(c), _f64(d), _f64(s), _f64(u), _f64(gy)
     L = _layout(c, D, seq_T)
-    y = np.zeros_like(c); gc = np.zeros_like(c); gd = np.zeros_like(d)
-    gs = np.zeros_like(s); gu = np.zeros_like(u); gs_sys = np.zeros_like(d)
+    y = _y_like(p, c, seq_T); gc = np.zeros_like(c); gd = np.zeros_like(d)
+    gs = np.zeros_like(s); gu = np.zeros_like(u); gs_sys = np.zeros(int(L.T_sys.sum()))
     gw_sys = np.zeros((L.S, 3))
     info = np.zeros(L.S, np.int32)
     rc = _load().orc_grad_batch(ctypes.byref(p.c()), L.S, _ptr(L.T_sys, ctypes.c_int64),

@@ -6,20 +6,23 @@
  * and the benchmark's CPU-baseline leg load it. The CUDA library never links,
  * loads or calls it, and it shares no code, header or table with that library.
  *
- * What it computes, for one system (one sequence/dimension pair, V = Q = 1):
+ * What it computes, for one system (one sequence/dimension pair) of V variables with
+ * Q governing equations per step (Sec. 3.1; V = Q = 1 is the scalar case):
  *
  *   1. The rows of A, b and the diagonal weight matrix W, written out one
  *      constraint at a time exactly as Sec. 3.1 states them:
- *        Eq. 4  governing row per step t:        sum_r c_{t,r} y_{t,r} = d_t
- *        Eq. 5  initial-value rows, t <= T_init, r <= R_init:  y_{t,r} = u_{t,r}
- *        Eq. 6  forward smoothness, t < T, r <= R:
- *                   y_{t+1,r} = sum_{r'>=r} s_t^{r'-r}/(r'-r)! y_{t,r'}
- *        Eq. 7  backward smoothness, t < T, r <= R:
- *                   y_{t,r}   = sum_{r'>=r} (-s_t)^{r'-r}/(r'-r)! y_{t+1,r'}
+ *        Eq. 4  governing rows per step t, q < Q:
+ *                   sum_{v,r} c_{t,q,v,r} y_{t,v,r} = d_{t,q}
+ *        Eq. 5  initial-value rows, t <= T_init, v < V, r <= R_init:  y_{t,v,r} = u_{t,v,r}
+ *        Eq. 6  forward smoothness, t < T, v < V, r <= R:
+ *                   y_{t+1,v,r} = sum_{r'>=r} s_t^{r'-r}/(r'-r)! y_{t,v,r'}
+ *        Eq. 7  backward smoothness, t < T, v < V, r <= R:
+ *                   y_{t,v,r}   = sum_{r'>=r} (-s_t)^{r'-r}/(r'-r)! y_{t+1,v,r'}
  *      Row order and signs follow App. A.1 (A_gov, A_init, A_smooth_forward
  *      = [A+_t, -I], A_smooth_backward = [-I, A-_t]); b is d, u, then zeros;
  *      the weights are w_gov^2, w_init^2 and (w_smooth s_t^r)^2 (App. A.1).
- *      Unknown y_{t,r} sits at column t*(R+1)+r (Sec. 3.2, 0-based here).
+ *      Unknown y_{t,v,r} sits at column t*V(R+1) + v(R+1) + r (Sec. 3.2, 0-based
+ *      here); the step size s_t is shared by the V variables.
  *   2. y = (A^T W A)^{-1} A^T W b (Eq. 9), by forming M = A^T W A and
  *      beta = A^T W b from the rows and factoring M with a textbook scalar
  *      band Cholesky (half-bandwidth 2(R+1)-1), or densely (Cholesky, or
@@ -55,12 +58,14 @@
 #endif
 
 #define ORC_MAX_R 7
-#define ORC_MAX_NZ (ORC_MAX_R + 2)
+#define ORC_MAX_NZ 16   /* nonzeros of a row: V(R+1) for a governing row, <= R+2 otherwise */
 
 typedef struct {
   int32_t R;       /* highest derivative order; R+1 unknowns per step   */
   int32_t R_init;  /* initial values given for orders 0..R_init          */
   int32_t T_init;  /* initial values given for steps 1..T_init           */
+  int32_t V;       /* variables per step (Sec. 3.1), >= 1                */
+  int32_t Q;       /* governing equations per step, >= 1                 */
   int32_t pad_;
   double w_gov, w_init, w_smooth; /* importance weights (unsquared)      */
 } orc_params;
@@ -91,42 +96,54 @@ static double orc_powi(double x, int k) {
   return p;
 }
 
-/* m of Eq. 8 with V = Q = 1. */
+/* Unknowns per step. */
+static int orc_nb(const orc_params* p) { return p->V * (p->R + 1); }
+
+static int orc_params_ok(const orc_params* p) {
+  return p->R >= 0 && p->R <= ORC_MAX_R && p->R_init >= 0 && p->R_init <= p->R && p->T_init >= 1 &&
+         p->V >= 1 && p->Q >= 1 && orc_nb(p) <= ORC_MAX_NZ;
+}
+
+/* m of Eq. 8. */
 int64_t orc_num_rows(const orc_params* p, int64_t T) {
-  return T + (int64_t)p->T_init * (p->R_init + 1) + 2 * (T - 1) * (int64_t)(p->R + 1);
+  return T * p->Q + (int64_t)p->T_init * p->V * (p->R_init + 1) + 2 * (T - 1) * (int64_t)orc_nb(p);
 }
 
 /* Rows of A, b, W for one system of T steps.
- * c: [T][R+1], d: [T], s: [T] (s[T-1] unused), u: [T_init][R_init+1]. */
+ * c: [T][Q][V(R+1)], d: [T][Q], s: [T] (s[T-1] unused), u: [T_init][V][R_init+1]. */
 void orc_build_rows(const orc_params* p, int64_t T, const double* c, const double* d,
                     const double* s, const double* u, orc_row* rows) {
-  const int nb = p->R + 1;
+  const int nb = orc_nb(p), r1 = p->R + 1;
   int64_t k = 0;
   memset(rows, 0, sizeof(orc_row) * (size_t)orc_num_rows(p, T));
 
-  /* Eq. 4: sum_r c_{t,r} y_{t,r} = d_t, weight w_gov^2. */
-  for (int64_t t = 0; t < T; ++t, ++k) {
-    orc_row* w = &rows[k];
-    w->kind = ROW_GOV; w->t = (int32_t)t; w->r = -1; w->nnz = nb;
-    for (int r = 0; r < nb; ++r) {
-      w->col[r] = t * nb + r;
-      w->val[r] = c[t * nb + r];
+  /* Eq. 4: sum_{v,r} c_{t,q,v,r} y_{t,v,r} = d_{t,q}, weight w_gov^2. */
+  for (int64_t t = 0; t < T; ++t) {
+    for (int q = 0; q < p->Q; ++q, ++k) {
+      orc_row* w = &rows[k];
+      w->kind = ROW_GOV; w->t = (int32_t)t; w->r = q; w->nnz = nb;
+      for (int a = 0; a < nb; ++a) {
+        w->col[a] = t * nb + a;
+        w->val[a] = c[(t * p->Q + q) * nb + a];
+      }
+      w->b = d[t * p->Q + q];
+      w->w = p->w_gov * p->w_gov;
+      w->dw_dimp = 2.0 * p->w_gov;
     }
-    w->b = d[t];
-    w->w = p->w_gov * p->w_gov;
-    w->dw_dimp = 2.0 * p->w_gov;
   }
 
-  /* Eq. 5: y_{t,r} = u_{t,r} for t < T_init, r <= R_init, weight w_init^2. */
+  /* Eq. 5: y_{t,v,r} = u_{t,v,r} for t < T_init, r <= R_init, weight w_init^2. */
   for (int64_t t = 0; t < p->T_init; ++t) {
-    for (int r = 0; r <= p->R_init; ++r, ++k) {
-      orc_row* w = &rows[k];
-      w->kind = ROW_INIT; w->t = (int32_t)t; w->r = r; w->nnz = 1;
-      w->col[0] = t * nb + r;
-      w->val[0] = 1.0;
-      w->b = u[t * (p->R_init + 1) + r];
-      w->w = p->w_init * p->w_init;
-      w->dw_dimp = 2.0 * p->w_init;
+    for (int v = 0; v < p->V; ++v) {
+      for (int r = 0; r <= p->R_init; ++r, ++k) {
+        orc_row* w = &rows[k];
+        w->kind = ROW_INIT; w->t = (int32_t)t; w->r = v * (p->R_init + 1) + r; w->nnz = 1;
+        w->col[0] = t * nb + v * r1 + r;
+        w->val[0] = 1.0;
+        w->b = u[(t * p->V + v) * (p->R_init + 1) + r];
+        w->w = p->w_init * p->w_init;
+        w->dw_dimp = 2.0 * p->w_init;
+      }
     }
   }
 
@@ -134,17 +151,18 @@ void orc_build_rows(const orc_params* p, int64_t T, const double* c, const doubl
    * (App. A.1: block t is A+_t, block t+1 is -I); weight (w_smooth s_t^r)^2. */
   for (int64_t t = 0; t + 1 < T; ++t) {
     const double st = s[t];
-    for (int r = 0; r < nb; ++r, ++k) {
+    for (int v = 0; v < p->V; ++v)
+    for (int r = 0; r < r1; ++r, ++k) {
       orc_row* w = &rows[k];
       w->kind = ROW_FWD; w->t = (int32_t)t; w->r = r; w->nnz = 0;
-      for (int rp = r; rp < nb; ++rp) {
+      for (int rp = r; rp < r1; ++rp) {
         const int q = rp - r;
-        w->col[w->nnz] = t * nb + rp;
+        w->col[w->nnz] = t * nb + v * r1 + rp;
         w->val[w->nnz] = orc_powi(st, q) / orc_factorial(q);
         w->dval_ds[w->nnz] = q > 0 ? orc_powi(st, q - 1) / orc_factorial(q - 1) : 0.0;
         w->nnz++;
       }
-      w->col[w->nnz] = (t + 1) * nb + r;
+      w->col[w->nnz] = (t + 1) * nb + v * r1 + r;
       w->val[w->nnz] = -1.0;
       w->dval_ds[w->nnz] = 0.0;
       w->nnz++;
@@ -159,16 +177,17 @@ void orc_build_rows(const orc_params* p, int64_t T, const double* c, const doubl
    * (App. A.1: block t is -I, block t+1 is A-_t); same weight as Eq. 6. */
   for (int64_t t = 0; t + 1 < T; ++t) {
     const double st = s[t];
-    for (int r = 0; r < nb; ++r, ++k) {
+    for (int v = 0; v < p->V; ++v)
+    for (int r = 0; r < r1; ++r, ++k) {
       orc_row* w = &rows[k];
       w->kind = ROW_BWD; w->t = (int32_t)t; w->r = r; w->nnz = 0;
-      w->col[w->nnz] = t * nb + r;
+      w->col[w->nnz] = t * nb + v * r1 + r;
       w->val[w->nnz] = -1.0;
       w->dval_ds[w->nnz] = 0.0;
       w->nnz++;
-      for (int rp = r; rp < nb; ++rp) {
+      for (int rp = r; rp < r1; ++rp) {
         const int q = rp - r;
-        w->col[w->nnz] = (t + 1) * nb + rp;
+        w->col[w->nnz] = (t + 1) * nb + v * r1 + rp;
         w->val[w->nnz] = orc_powi(-st, q) / orc_factorial(q);
         /* d/ds (-s)^q/q! = -(-s)^{q-1}/(q-1)! */
         w->dval_ds[w->nnz] = q > 0 ? -orc_powi(-st, q - 1) / orc_factorial(q - 1) : 0.0;
@@ -189,7 +208,7 @@ void orc_build_rows(const orc_params* p, int64_t T, const double* c, const doubl
 /* Explicit A [m][n], b [m], w [m] (the diagonal of W). */
 void orc_dense_system(const orc_params* p, int64_t T, const double* c, const double* d,
                       const double* s, const double* u, double* A, double* b, double* w) {
-  const int64_t m = orc_num_rows(p, T), n = T * (p->R + 1);
+  const int64_t m = orc_num_rows(p, T), n = T * orc_nb(p);
   orc_row* rows = (orc_row*)malloc(sizeof(orc_row) * (size_t)m);
   orc_build_rows(p, T, c, d, s, u, rows);
   memset(A, 0, sizeof(double) * (size_t)(m * n));
@@ -222,7 +241,7 @@ static int orc_dense_cholesky(int64_t n, double* a) {
 /* y = (A^T W A)^{-1} A^T W b with a dense Cholesky of M (Eq. 9). */
 int orc_solve_dense_normal(const orc_params* p, int64_t T, const double* c, const double* d,
                            const double* s, const double* u, double* y) {
-  const int64_t m = orc_num_rows(p, T), n = T * (p->R + 1);
+  const int64_t m = orc_num_rows(p, T), n = T * orc_nb(p);
   double* A = (double*)malloc(sizeof(double) * (size_t)(m * n));
   double* b = (double*)malloc(sizeof(double) * (size_t)m);
   double* w = (double*)malloc(sizeof(double) * (size_t)m);
@@ -259,7 +278,7 @@ int orc_solve_dense_normal(const orc_params* p, int64_t T, const double* c, cons
  * forming the normal equations (the brute-force least-squares definition). */
 int orc_solve_dense_qr(const orc_params* p, int64_t T, const double* c, const double* d,
                        const double* s, const double* u, double* y) {
-  const int64_t m = orc_num_rows(p, T), n = T * (p->R + 1);
+  const int64_t m = orc_num_rows(p, T), n = T * orc_nb(p);
   double* A = (double*)malloc(sizeof(double) * (size_t)(m * n));
   double* b = (double*)malloc(sizeof(double) * (size_t)m);
   double* w = (double*)malloc(sizeof(double) * (size_t)m);
@@ -309,7 +328,7 @@ int orc_solve_dense_qr(const orc_params* p, int64_t T, const double* c, const do
  * inside one row of A (a backward smoothness row spans y_{t,r}..y_{t+1,R}).
  * ------------------------------------------------------------------------- */
 
-int orc_band_width(const orc_params* p) { return 2 * (p->R + 1) - 1; }
+int orc_band_width(const orc_params* p) { return 2 * orc_nb(p) - 1; }
 
 /* M = A^T W A and beta = A^T W b accumulated row by row. */
 static void orc_normal_band_rows(const orc_row* rows, int64_t m, int64_t n, int kd,
@@ -369,7 +388,7 @@ void orc_band_solve(int64_t n, int kd, const double* l, double* x) {
 /* Band M and beta of one system (for comparison with a library band solver). */
 void orc_normal_band(const orc_params* p, int64_t T, const double* c, const double* d,
                      const double* s, const double* u, double* band, double* beta) {
-  const int64_t m = orc_num_rows(p, T), n = T * (p->R + 1);
+  const int64_t m = orc_num_rows(p, T), n = T * orc_nb(p);
   orc_row* rows = (orc_row*)malloc(sizeof(orc_row) * (size_t)m);
   orc_build_rows(p, T, c, d, s, u, rows);
   orc_normal_band_rows(rows, m, n, orc_band_width(p), band, beta);
@@ -379,7 +398,7 @@ void orc_normal_band(const orc_params* p, int64_t T, const double* c, const doub
 /* Solve one system in band mode; returns 0 or the failing unknown's index+1. */
 static int orc_solve_one_band(const orc_params* p, int64_t T, const double* c, const double* d,
                               const double* s, const double* u, double* y) {
-  const int64_t m = orc_num_rows(p, T), n = T * (p->R + 1);
+  const int64_t m = orc_num_rows(p, T), n = T * orc_nb(p);
   const int kd = orc_band_width(p);
   orc_row* rows = (orc_row*)malloc(sizeof(orc_row) * (size_t)m);
   double* band = (double*)malloc(sizeof(double) * (size_t)(n * (kd + 1)));
@@ -397,7 +416,7 @@ static int orc_solve_one_band(const orc_params* p, int64_t T, const double* c, c
 static int orc_grad_one(const orc_params* p, int64_t T, const double* c, const double* d,
                         const double* s, const double* u, const double* gy, double* y,
                         double* gc, double* gd, double* gs, double* gu, double* gw) {
-  const int nb = p->R + 1;
+  const int nb = orc_nb(p);
   const int64_t m = orc_num_rows(p, T), n = T * nb;
   const int kd = orc_band_width(p);
   orc_row* rows = (orc_row*)malloc(sizeof(orc_row) * (size_t)m);
@@ -406,10 +425,10 @@ static int orc_grad_one(const orc_params* p, int64_t T, const double* c, const d
   orc_build_rows(p, T, c, d, s, u, rows);
   orc_normal_band_rows(rows, m, n, kd, band, y);
   const int info = orc_band_cholesky(n, kd, band);
-  memset(gc, 0, sizeof(double) * (size_t)n);
-  memset(gd, 0, sizeof(double) * (size_t)T);
+  memset(gc, 0, sizeof(double) * (size_t)(n * p->Q));
+  memset(gd, 0, sizeof(double) * (size_t)(T * p->Q));
   memset(gs, 0, sizeof(double) * (size_t)T);
-  memset(gu, 0, sizeof(double) * (size_t)(p->T_init * (p->R_init + 1)));
+  memset(gu, 0, sizeof(double) * (size_t)(p->T_init * p->V * (p->R_init + 1)));
   gw[0] = gw[1] = gw[2] = 0.0;
   if (info == 0) {
     orc_band_solve(n, kd, band, y);                   /* y = M^{-1} beta    */
@@ -428,16 +447,17 @@ static int orc_grad_one(const orc_params* p, int64_t T, const double* c, const d
       /* theta = the row's importance weight: da = db = 0, dw = dw_dimp (App. A.1's W). */
       gw[w->kind == ROW_GOV ? 0 : (w->kind == ROW_INIT ? 1 : 2)] += ag * w->dw_dimp * e;
       if (w->kind == ROW_GOV) {
-        /* theta = c_{t,r}: da = unit vector at column (t,r); dw = db = 0.
-         * theta = d_t:     db = 1. */
+        /* theta = c_{t,q,a}: da = unit vector at column (t,a); dw = db = 0.
+         * theta = d_{t,q}:   db = 1. */
+        const int64_t gq = (int64_t)w->t * p->Q + w->r;
         for (int j = 0; j < w->nnz; ++j) {
           const int64_t col = w->col[j];
-          gc[col] += g[col] * w->w * e - ag * w->w * y[col];
+          gc[gq * nb + (col - (int64_t)w->t * nb)] += g[col] * w->w * e - ag * w->w * y[col];
         }
-        gd[w->t] += ag * w->w;
+        gd[gq] += ag * w->w;
       } else if (w->kind == ROW_INIT) {
-        /* theta = u_{t,r}: db = 1. */
-        gu[w->t * (p->R_init + 1) + w->r] += ag * w->w;
+        /* theta = u_{t,v,r}: db = 1 (w->r = v (R_init+1) + r). */
+        gu[(int64_t)w->t * p->V * (p->R_init + 1) + w->r] += ag * w->w;
       } else {
         /* theta = s_t: da = dval_ds, dw = dw_ds, db = 0. */
         gs[w->t] += dag * w->w * e + ag * w->dw_ds * e - ag * w->w * day;
@@ -460,15 +480,15 @@ static int orc_grad_one(const orc_params* p, int64_t T, const double* c, const d
 int orc_solve_batch(const orc_params* p, int64_t S, const int64_t* T_sys, const int64_t* off,
                     const int64_t* soff, const double* c, const double* d, const double* s,
                     const double* u, double* y, int32_t* info, int nthreads) {
-  const int nb = p->R + 1;
-  const int nu = p->T_init * (p->R_init + 1);
-  if (p->R < 0 || p->R > ORC_MAX_R || p->R_init < 0 || p->R_init > p->R || p->T_init < 1) return -1;
+  const int nb = orc_nb(p), nq = p->Q;
+  const int nu = p->T_init * p->V * (p->R_init + 1);
+  if (!orc_params_ok(p)) return -1;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
   for (int64_t i = 0; i < S; ++i) {
-    const int r = orc_solve_one_band(p, T_sys[i], c + off[i] * nb, d + off[i], s + soff[i],
+    const int r = orc_solve_one_band(p, T_sys[i], c + off[i] * nq * nb, d + off[i] * nq, s + soff[i],
                                      u + i * nu, y + off[i] * nb);
     info[i] = r == 0 ? 0 : (int32_t)((r - 1) / nb + 1);
   }
@@ -480,17 +500,17 @@ int orc_grad_batch(const orc_params* p, int64_t S, const int64_t* T_sys, const i
                    const double* u, const double* gy, double* y, double* gc, double* gd,
                    double* gs, double* gu, double* gs_sys, double* gw_sys, int32_t* info,
                    int nthreads) {
-  const int nb = p->R + 1;
-  const int nu = p->T_init * (p->R_init + 1);
-  if (p->R < 0 || p->R > ORC_MAX_R || p->R_init < 0 || p->R_init > p->R || p->T_init < 1) return -1;
+  const int nb = orc_nb(p), nq = p->Q;
+  const int nu = p->T_init * p->V * (p->R_init + 1);
+  if (!orc_params_ok(p)) return -1;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
   for (int64_t i = 0; i < S; ++i) {
-    const int r = orc_grad_one(p, T_sys[i], c + off[i] * nb, d + off[i], s + soff[i], u + i * nu,
-                               gy + off[i] * nb, y + off[i] * nb, gc + off[i] * nb, gd + off[i],
-                               gs_sys + off[i], gu + i * nu, gw_sys + 3 * i);
+    const int r = orc_grad_one(p, T_sys[i], c + off[i] * nq * nb, d + off[i] * nq, s + soff[i],
+                               u + i * nu, gy + off[i] * nb, y + off[i] * nb, gc + off[i] * nq * nb,
+                               gd + off[i] * nq, gs_sys + off[i], gu + i * nu, gw_sys + 3 * i);
     info[i] = r == 0 ? 0 : (int32_t)((r - 1) / nb + 1);
   }
   /* chain rule for the shared step sizes: sum the systems' shares in order */
@@ -505,12 +525,13 @@ int orc_grad_batch(const orc_params* p, int64_t S, const int64_t* T_sys, const i
 int orc_solve_dense_batch(const orc_params* p, int64_t S, const int64_t* T_sys, const int64_t* off,
                           const int64_t* soff, const double* c, const double* d, const double* s,
                           const double* u, double* y, int32_t* info, int mode) {
-  const int nb = p->R + 1;
-  const int nu = p->T_init * (p->R_init + 1);
+  const int nb = orc_nb(p), nq = p->Q;
+  const int nu = p->T_init * p->V * (p->R_init + 1);
+  if (!orc_params_ok(p)) return -1;
   for (int64_t i = 0; i < S; ++i) {
     const int r = mode == 0
-        ? orc_solve_dense_normal(p, T_sys[i], c + off[i] * nb, d + off[i], s + soff[i], u + i * nu, y + off[i] * nb)
-        : orc_solve_dense_qr(p, T_sys[i], c + off[i] * nb, d + off[i], s + soff[i], u + i * nu, y + off[i] * nb);
+        ? orc_solve_dense_normal(p, T_sys[i], c + off[i] * nq * nb, d + off[i] * nq, s + soff[i], u + i * nu, y + off[i] * nb)
+        : orc_solve_dense_qr(p, T_sys[i], c + off[i] * nq * nb, d + off[i] * nq, s + soff[i], u + i * nu, y + off[i] * nb);
     info[i] = r == 0 ? 0 : (int32_t)((r - 1) / nb + 1);
   }
   return 0;

@@ -31,7 +31,7 @@ import numpy as np
 
 __all__ = ["Problem", "config1", "config2", "config2_slice", "config3", "config3b", "config4",
            "config5", "random_problem", "upstream_gradient", "mse_target", "CONFIGS",
-           "table5_odes", "table5_batch", "ODE_T", "ODE_H"]
+           "table5_odes", "table5_batch", "ODE_T", "ODE_H", "random_coupled_problem"]
 
 
 @dataclass
@@ -57,6 +57,8 @@ class Problem:
     w_init: float = 1.0
     w_smooth: float = 1.0
     meta: dict = field(default_factory=dict)
+    V: int = 1   # variables per step (Sec. 3.1); c then holds Q*V*(R+1) values per step,
+    Q: int = 1   # d holds Q, u holds V*(R_init+1) per initial step (variable-major)
 
     @property
     def S(self) -> int:
@@ -265,3 +267,26 @@ def table5_batch(R: int, R_init: int, T: int = ODE_T, h: float = ODE_H) -> tuple
         u[b, 0, 0, :] = cse["u"]
     s = np.full((B, T), h)
     return Problem(f"App. B.1 ODEs R={R}", R, R_init, 1, B, 1, T, c, d, s, u), cases
+
+
+def random_coupled_problem(seed: int = 0, B: int = 2, D: int = 2, T: int = 64, R: int = 1,
+                           V: int = 2, Q: int = 2, R_init: int | None = None, T_init: int = 1,
+                           s_lo: float = 0.01, s_hi: float = 0.1, w=(1.0, 1.0, 1.0)) -> Problem:
+    """Uniform batch of coupled systems (Sec. 3.1 with V variables and Q governing equations
+    per step): c [B, D, T, Q*V*(R+1)] ~ N(0,1) with the coefficient of each equation's own
+    variable's highest derivative (variable q mod V) set to 1 + |N(0,1)|, d [B, D, T, Q] ~ N(0,1),
+    s ~ U[s_lo, s_hi] per (sequence, step), u [B, D, T_init, V*(R_init+1)] ~ N(0,1).
+    Draw order: c, d, s, u."""
+    if R_init is None:
+        R_init = max(R - 1, 0)
+    nb = V * (R + 1)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = rng.standard_normal((B, D, T, Q, nb))
+    for q in range(Q):
+        k = (q % V) * (R + 1) + R
+        c[..., q, k] = 1.0 + np.abs(c[..., q, k])
+    d = rng.standard_normal((B, D, T, Q))
+    s = rng.uniform(s_lo, s_hi, (B, T))
+    u = rng.standard_normal((B, D, T_init, V * (R_init + 1)))
+    return Problem(f"coupled V={V} Q={Q}", R, R_init, T_init, B, D, T, c.reshape(B, D, T, Q * nb),
+                   d, s, u, w_gov=w[0], w_init=w[1], w_smooth=w[2], V=V, Q=Q)

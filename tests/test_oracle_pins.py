@@ -455,3 +455,117 @@ def test_table5_higher_order_odes_below_paper_bound():
         R = 4 if cse["name"] == "ThirdOrder" else cse["R"]
         y = _solve_ode(cse["coeffs"], cse["rhs"], cse["u"], R)
         assert max(_rel_mse(y[:, r], cse["exact"][r]) for r in range(3)) < 1e-6, cse["name"]
+
+
+# --------------------------------------------------------------------------- coupled systems
+
+def coupled_params(prob):
+    return O.Params(prob.R, prob.R_init, prob.T_init, prob.w_gov, prob.w_init, prob.w_smooth,
+                    V=prob.V, Q=prob.Q)
+
+
+@pytest.mark.parametrize("R,R_init,T_init,V,Q,T", [(1, 0, 1, 2, 1, 5), (2, 1, 2, 3, 2, 7),
+                                                  (1, 1, 1, 2, 3, 4)])
+def test_coupled_row_count_is_eq8(R, R_init, T_init, V, Q, T):
+    """Eq. 8: m = TQ + T_init V (R_init+1) + 2(T-1) V (R+1) and n = T V (R+1)."""
+    p = O.Params(R, R_init, T_init, V=V, Q=Q)
+    assert O.num_rows(p, T) == T * Q + T_init * V * (R_init + 1) + 2 * (T - 1) * V * (R + 1)
+    prob = W.random_coupled_problem(1, 1, 1, T, R, V, Q, R_init=R_init, T_init=T_init)
+    A, b, w = O.dense_system(p, prob.c[0, 0], prob.d[0, 0], prob.s[0], prob.u[0, 0])
+    assert A.shape == (O.num_rows(p, T), T * V * (R + 1))
+
+
+@pytest.mark.parametrize("R,V,Q,T", [(1, 2, 2, 9), (2, 3, 1, 8), (2, 2, 3, 6), (1, 2, 1, 11)])
+def test_coupled_normal_equations_match_qr(R, V, Q, T):
+    """Brute force: the band normal-equation solve equals dense Householder QR on W^{1/2}A."""
+    prob = W.random_coupled_problem(2, 2, 2, T, R, V, Q, s_lo=0.05, s_hi=0.3)
+    p = coupled_params(prob)
+    yb, ib = O.solve(p, prob.c, prob.d, prob.s, prob.u)
+    yq, iq = O.solve(p, prob.c, prob.d, prob.s, prob.u, mode="qr")
+    assert (ib == 0).all() and (iq == 0).all()
+    assert yb.shape == (2, 2, T, V * (R + 1))
+    np.testing.assert_allclose(yb, yq, rtol=1e-8, atol=1e-9 * np.abs(yq).max())
+
+
+def test_coupled_decoupled_equations_equal_independent_solves():
+    """V = Q = 2 with equation q involving only variable q: the solution is that of two
+    separate V = 1 systems with the same step sizes and each variable's own rows."""
+    R, T = 2, 13
+    prob = W.random_coupled_problem(3, 1, 1, T, R, V=2, Q=2, s_lo=0.05, s_hi=0.3)
+    nb1 = R + 1
+    c = prob.c.reshape(1, 1, T, 2, 2, nb1).copy()
+    c[:, :, :, 0, 1, :] = 0.0   # equation 0: variable 0 only
+    c[:, :, :, 1, 0, :] = 0.0   # equation 1: variable 1 only
+    p = coupled_params(prob)
+    y, info = O.solve(p, c.reshape(1, 1, T, -1), prob.d, prob.s, prob.u)
+    assert info[0] == 0
+    ui = prob.u.reshape(1, 1, prob.T_init, 2, prob.R_init + 1)
+    for v in range(2):
+        pv = O.Params(R, prob.R_init, prob.T_init)
+        yv, iv = O.solve(pv, c[:, :, :, v, v, :], prob.d[..., v], prob.s, ui[:, :, :, v, :])
+        np.testing.assert_allclose(y[..., v * nb1:(v + 1) * nb1], yv, rtol=1e-11, atol=1e-12)
+
+
+def test_coupled_polynomial_trajectories_recovered_exactly():
+    """Each variable a polynomial of degree <= R, coupled governing equations consistent with
+    it, initial values taken from it: A y = b exactly, so the solve returns it (Eq. 6-7 rows
+    vanish on polynomials of degree <= R)."""
+    R, V, Q, T = 2, 2, 3, 17
+    prob = W.random_coupled_problem(4, 1, 1, T, R, V, Q, s_lo=0.05, s_hi=0.2)
+    tau = np.concatenate([[0.0], np.cumsum(prob.s[0, :-1])])
+    coef = np.random.Generator(np.random.PCG64(5)).standard_normal((V, R + 1))
+    y = np.zeros((T, V * (R + 1)))
+    for v in range(V):
+        poly = np.polynomial.Polynomial(coef[v])
+        for r in range(R + 1):
+            y[:, v * (R + 1) + r] = poly.deriv(r)(tau) if r else poly(tau)
+    c = prob.c[0, 0].reshape(T, Q, V * (R + 1))
+    d = np.einsum("tqa,ta->tq", c, y)
+    u = y[:prob.T_init].reshape(prob.T_init, V, R + 1)[:, :, :prob.R_init + 1].reshape(prob.T_init, -1)
+    p = coupled_params(prob)
+    ys, info = O.solve(p, prob.c[0, 0][None, None], d[None, None], prob.s, u[None, None])
+    assert info[0] == 0
+    np.testing.assert_allclose(ys[0, 0], y, rtol=1e-8, atol=1e-9 * np.abs(y).max())
+
+
+def test_coupled_gradients_match_finite_differences():
+    """dl/d{c, d, s, u, w} for l = <gy, y> on a coupled system against central differences."""
+    R, V, Q, T = 1, 2, 2, 6
+    prob = W.random_coupled_problem(6, 1, 1, T, R, V, Q, T_init=2, s_lo=0.1, s_hi=0.4,
+                                    w=(0.9, 1.2, 1.1))
+    p = coupled_params(prob)
+    c, d, s, u = (a.copy() for a in (prob.c[0, 0], prob.d[0, 0], prob.s[0], prob.u[0, 0]))
+    gy = np.random.Generator(np.random.PCG64(7)).standard_normal((T, V * (R + 1)))
+    y, gc, gd, gs, gu, gw, info = O.gradient(p, c[None, None], d[None, None], s[None], u[None, None],
+                                             gy[None, None], weights=True)
+    assert info[0] == 0
+
+    def loss(pp, c_, d_, s_, u_):
+        yy, _ = O.solve(pp, c_[None, None], d_[None, None], s_[None], u_[None, None], mode="dense")
+        return float(np.sum(gy * yy[0, 0]))
+
+    def fd(arr, idx, h):
+        old = arr[idx]
+        arr[idx] = old + h; lp = loss(p, c, d, s, u)
+        arr[idx] = old - h; lm = loss(p, c, d, s, u)
+        arr[idx] = old
+        return (lp - lm) / (2 * h)
+
+    checks = []
+    for idx in np.ndindex(*c.shape):
+        checks.append((gc[0, 0][idx], fd(c, idx, 1e-6)))
+    for idx in np.ndindex(*d.shape):
+        checks.append((gd[0, 0][idx], fd(d, idx, 1e-6)))
+    for t in range(T - 1):
+        checks.append((gs[0, t], fd(s, (t,), 1e-7)))
+    for idx in np.ndindex(*u.shape):
+        checks.append((gu[0, 0][idx], fd(u, idx, 1e-6)))
+    wv = [p.w_gov, p.w_init, p.w_smooth]
+    for k in range(3):
+        wp = list(wv); wp[k] += 1e-6
+        wm = list(wv); wm[k] -= 1e-6
+        lp = loss(O.Params(R, p.R_init, p.T_init, *wp, V=V, Q=Q), c, d, s, u)
+        lm = loss(O.Params(R, p.R_init, p.T_init, *wm, V=V, Q=Q), c, d, s, u)
+        checks.append((gw[k], (lp - lm) / 2e-6))
+    an = np.array([a for a, _ in checks]); nu = np.array([b for _, b in checks])
+    assert np.abs(an - nu).max() <= 1e-6 * max(1.0, np.abs(nu).max())
