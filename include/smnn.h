@@ -110,6 +110,14 @@ typedef struct smnn_desc {
   int64_t T;              /* steps per sequence (uniform batch; ignored if seq_T)   */
   const int64_t* seq_T;   /* HOST pointer to B step counts (ragged), or NULL; read  */
                           /* only during smnn_plan_create                           */
+  int32_t V;              /* variables per step (Sec. 3.1; 0 means 1): a step has   */
+                          /* n_b = V(R+1) unknowns, variable-major; V(R+1) <= 4     */
+  int32_t Q;              /* governing equations per step (0 means 1), 1..2; with V */
+                          /* and Q the per-step layouts become c [..][Q][V(R+1)],  */
+                          /* d [..][Q], u [..][T_init][V][R_init+1], y [..][V(R+1)] */
+                          /* (gradients likewise).  Built shapes: V = Q = 1 with    */
+                          /* R = 1..3, and V = 2, R = 1, Q = 1 or 2; other valid    */
+                          /* shapes return SMNN_ERR_UNSUPPORTED at plan creation.   */
 } smnn_desc;
 
 typedef struct smnn_plan_s* smnn_plan;
@@ -145,9 +153,10 @@ smnn_status smnn_plan_get_stats(smnn_plan plan, smnn_plan_stats* stats);
 smnn_status smnn_workspace_size(smnn_plan plan, size_t* workspace_bytes, size_t* factor_bytes);
 
 /* App. A.2: materialise M_t (lower triangle packed row by row: M_00, M_10, M_11,
- * M_20, ..., (R+1)(R+2)/2 values), N_t (block (t+1,t), (R+1)^2 values row-major,
- * zero for the last step of a system) and beta_t (R+1 values) for every step, laid
- * out per step like y.  workspace: as for smnn_factor_solve.  Testing and inspection
+ * M_20, ..., n_b(n_b+1)/2 values), N_t (block (t+1,t), n_b^2 values row-major,
+ * zero for the last step of a system) and beta_t (n_b values) for every step, laid
+ * out per step like y; n_b = V(R+1) (for V > 1 the smoothness part of M_t and N_t is
+ * block diagonal over the variables, the governing part sum_q w_gov^2 c_q c_q^T).  workspace: as for smnn_factor_solve.  Testing and inspection
  * aid; the solver forms these blocks in registers. */
 smnn_status smnn_assemble(smnn_plan plan, const void* c, const void* d, const void* s,
                           const void* u, void* M, void* N, void* beta, void* workspace,
@@ -164,7 +173,8 @@ smnn_status smnn_factor_solve(smnn_plan plan, const void* c, const void* d, cons
 
 /* Backward pass (Alg. 2 and Eq. 14): g = M^{-1} dl/dy with the same factor (refined
  * like the forward pass), then the parameter gradients, fused per step as the chain
- * rule through App. A.2's assembly:
+ * rule through App. A.2's assembly (per governing equation q when Q > 1; per variable
+ * v for the initial values and the smoothness rows when V > 1):
  *   gd_t = w_gov^2 c_t.g_t,   gc_t = w_gov^2 [(d_t - c_t.y_t) g_t - (c_t.g_t) y_t],
  *   gu_{t,r} = w_init^2 g_{t,r},
  *   gs_t = -w_smooth^2 d/ds_t sum_r s_t^{2r} (f+_r e+_r + f-_r e-_r), summed over the

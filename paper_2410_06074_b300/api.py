@@ -33,13 +33,18 @@ class SolveConfig:
     # it after the last sweep gets info = -1 (refinement that stagnates is never silent)
     refine_tol: float = 1e-7
     factor_budget_bytes: int = 16 << 30   # store the factor for backward if it fits
+    # coupled systems (Sec. 3.1): V variables and Q governing equations per step; c then holds
+    # Q*V*(R+1) values per step (equation-major), d Q, u V*(R_init+1) per initial step, and
+    # y V*(R+1) (variable-major); V*(R+1) <= 4, Q <= 2
+    V: int = 1
+    Q: int = 1
 
 
 def get_plan(shape_key, cfg: SolveConfig, tuned: bool = True) -> B.Plan:
     """shape_key: (R, B, D, T) for uniform batches or (R, B, D, seq_T tuple) for ragged.
     With tuned=True, ALGO_AUTO and chunk=0, the autotuner's table may pick the algorithm and
     the level-0 chunk length for this shape bucket."""
-    if tuned and cfg.algo == B.ALGO_AUTO and cfg.chunk == 0:
+    if tuned and cfg.algo == B.ALGO_AUTO and cfg.chunk == 0 and cfg.V == 1 and cfg.Q == 1:
         from . import autotune
         R, Bn, D, T = shape_key
         S = Bn * D
@@ -57,24 +62,30 @@ def get_plan(shape_key, cfg: SolveConfig, tuned: bool = True) -> B.Plan:
                       precision=cfg.precision, algo=cfg.algo, max_refine=cfg.max_refine,
                       adjoint_refine=cfg.adjoint_refine,
                       chunk=cfg.chunk, w_gov=cfg.w_gov, w_init=cfg.w_init, w_smooth=cfg.w_smooth,
-                      refine_tol=cfg.refine_tol)
+                      refine_tol=cfg.refine_tol, V=cfg.V, Q=cfg.Q)
         _PLANS[key] = plan
     return plan
 
 
-def _shape_key(c, s, D=None, seq_T=None):
+def _shape_key(c, s, D=None, seq_T=None, cfg: SolveConfig | None = None):
+    vq = 1 if cfg is None else cfg.V * cfg.Q   # c holds Q V (R+1) values per step
     if seq_T is None:
-        Bn, Dn, T, nb = c.shape
-        return (nb - 1, Bn, Dn, T)
+        Bn, Dn, T, k = c.shape
+        return (k // vq - 1, Bn, Dn, T)
     seq_T = tuple(int(x) for x in seq_T)
-    return (c.shape[-1] - 1, len(seq_T), int(D), seq_T)
+    return (c.shape[-1] // vq - 1, len(seq_T), int(D), seq_T)
+
+
+def _y_like(c, cfg: SolveConfig):
+    """Solution tensor: c's step dimensions with V (R+1) = c.shape[-1] / Q values per step."""
+    return c.new_empty(c.shape[:-1] + (c.shape[-1] // cfg.Q,))
 
 
 def solve(c, d, s, u, cfg: SolveConfig = SolveConfig(), *, D=None, seq_T=None, factor=None,
           workspace=None):
     """Forward solve only: returns (y, info).  ``factor``: optional buffer to keep the factor."""
-    plan = get_plan(_shape_key(c, s, D, seq_T), cfg)
-    y = torch.empty_like(c)
+    plan = get_plan(_shape_key(c, s, D, seq_T, cfg), cfg)
+    y = _y_like(c, cfg)
     info = torch.empty(plan.S, dtype=torch.int32, device=c.device)
     ws = plan.workspace(c.device) if workspace is None else workspace
     plan.factor_solve(c, d, s, u, y, info, ws, factor=factor)
@@ -85,7 +96,7 @@ def gradients(c, d, s, u, y, gy, cfg: SolveConfig = SolveConfig(), *, D=None, se
               factor=None, workspace=None, weights: bool = False):
     """Backward only: returns (gc, gd, gs, gu, info) for dl/dy = gy; with weights=True,
     (gc, gd, gs, gu, gw, info), gw = dl/d(w_gov, w_init, w_smooth) (float64, 3 values)."""
-    plan = get_plan(_shape_key(c, s, D, seq_T), cfg)
+    plan = get_plan(_shape_key(c, s, D, seq_T, cfg), cfg)
     gc, gd, gs, gu = (torch.empty_like(t) for t in (c, d, s, u))
     info = torch.empty(plan.S, dtype=torch.int32, device=c.device)
     gw = torch.empty(3, dtype=torch.float64, device=c.device) if weights else None
@@ -110,7 +121,7 @@ class SmnnSolve(torch.autograd.Function):
         if weights is not None:
             wg, wi, wsm = (float(v) for v in weights.detach().double().cpu().tolist())
             cfg = replace(cfg, w_gov=wg, w_init=wi, w_smooth=wsm)
-        plan = get_plan(_shape_key(c, s, D, seq_T), cfg)
+        plan = get_plan(_shape_key(c, s, D, seq_T, cfg), cfg)
         factor = plan.factor_buffer(c.device) if plan.factor_bytes <= cfg.factor_budget_bytes else None
         y, info = solve(c, d, s, u, cfg, D=D, seq_T=seq_T, factor=factor)
         ctx.save_for_backward(c, d, s, u, y)

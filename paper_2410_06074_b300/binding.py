@@ -37,7 +37,7 @@ class Desc(ctypes.Structure):
                 ("w_init", ctypes.c_double), ("w_smooth", ctypes.c_double),
                 ("refine_tol", ctypes.c_double), ("num_seq", ctypes.c_int64),
                 ("dims_per_seq", ctypes.c_int64), ("T", ctypes.c_int64),
-                ("seq_T", ctypes.POINTER(ctypes.c_int64))]
+                ("seq_T", ctypes.POINTER(ctypes.c_int64)), ("V", ctypes.c_int32), ("Q", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -143,6 +143,8 @@ class Plan:
     w_init: float = 1.0
     w_smooth: float = 1.0
     refine_tol: float = 0.0
+    V: int = 1
+    Q: int = 1
     handle: ctypes.c_void_p = field(default=None, repr=False)
 
     def __post_init__(self):
@@ -152,7 +154,7 @@ class Plan:
             seq = (ctypes.c_int64 * len(self.seq_T))(*self.seq_T)
         d = Desc(self.R, self.R_init, self.T_init, self.precision, self.algo, self.max_refine,
                  self.chunk, self.adjoint_refine, self.w_gov, self.w_init, self.w_smooth, self.refine_tol, self.B,
-                 self.D, int(self.T or 0), ctypes.cast(seq, ctypes.POINTER(ctypes.c_int64)))
+                 self.D, int(self.T or 0), ctypes.cast(seq, ctypes.POINTER(ctypes.c_int64)), self.V, self.Q)
         h = ctypes.c_void_p()
         _check(lib.smnn_plan_create(ctypes.byref(d), ctypes.byref(h)), "smnn_plan_create")
         self.handle = h
@@ -177,6 +179,11 @@ class Plan:
     @property
     def S(self) -> int:
         return self.B * self.D
+
+    @property
+    def nb(self) -> int:
+        """Unknowns per step, V (R+1)."""
+        return self.V * (self.R + 1)
 
     @property
     def steps(self) -> int:

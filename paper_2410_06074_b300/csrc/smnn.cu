@@ -123,15 +123,15 @@ struct L0In {
   const Tr* s;    // [L][G]
 };
 
-template <class Tr, int NB>
-__device__ __forceinline__ CoefSource<Tr, NB> make_coef(const Problem0& p, const L0In<Tr>& in,
+template <class Tr, int NB, int R1 = NB, int Q = 1>
+__device__ __forceinline__ CoefSource<Tr, NB, R1, Q> make_coef(const Problem0& p, const L0In<Tr>& in,
                                                         const Tr* rhs, int64_t i, int64_t g,
                                                         int64_t first, int64_t T, int L, int64_t G) {
-  CoefSource<Tr, NB> src;
+  CoefSource<Tr, NB, R1, Q> src;
   src.c = in.c;
   src.d = in.d;
   src.s = in.s;
-  src.u = static_cast<const Tr*>(p.u) + i * int64_t(p.T_init) * (p.R_init + 1);
+  src.u = static_cast<const Tr*>(p.u) + i * int64_t(p.T_init) * (NB / R1) * (p.R_init + 1);
   src.rhs = rhs;
   src.T = T;
   src.first = first;
@@ -264,12 +264,12 @@ __global__ void __launch_bounds__(kThreads) k_gather_s(LevelTables lt, Problem0 
 
 // The per-chunk bodies of the level kernels (one thread = one chunk g of a level), shared by
 // the one-launch-per-level kernels and the fused per-CTA pass (k_pass).
-template <class Tr, int NB, bool kFactor, bool kRO>
+template <class Tr, int NB, bool kFactor, bool kRO, int R1 = NB, int Q = 1>
 __device__ __forceinline__ void dev_elim0(const LevelTables& lt, const LevelBufs<Tr, NB>& lb,
                                           const Problem0& p, const L0In<Tr>& in, const Tr* rhs,
                                           int32_t* info, int64_t g, bool top) {
   const ChunkPos cp = chunk_pos(lt, g);
-  CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, in, rhs, cp.i, g, cp.first, cp.T, lt.L, lt.G);
+  CoefSource<Tr, NB, R1, Q> src = make_coef<Tr, NB, R1, Q>(p, in, rhs, cp.i, g, cp.first, cp.T, lt.L, lt.G);
   int64_t fail = elim_chunk<Tr, NB, kFactor, kRO>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
   if (top) {
     if (!solve_top<Tr, NB>(lb.out, g, lb.xsep + g * NB) && kFactor && fail == 0) fail = cp.last + 1;
@@ -280,12 +280,12 @@ __device__ __forceinline__ void dev_elim0(const LevelTables& lt, const LevelBufs
 #ifndef SMNN_FACTOR_MIN_BLOCKS
 #define SMNN_FACTOR_MIN_BLOCKS 4   // factor pass: 4 CTAs per SM (128 registers) beat 3 (168)
 #endif
-template <class Tr, int NB, bool kFactor, bool kTop>
+template <class Tr, int NB, bool kFactor, bool kTop, int R1 = NB, int Q = 1>
 __global__ void __launch_bounds__(kThreads, kFactor ? SMNN_FACTOR_MIN_BLOCKS : 4) k_elim0(LevelTables lt, LevelBufs<Tr, NB> lb, Problem0 p,
                                                     L0In<Tr> in, const Tr* rhs, int32_t* info) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  dev_elim0<Tr, NB, kFactor, true>(lt, lb, p, in, rhs, info, g, kTop);
+  dev_elim0<Tr, NB, kFactor, true, R1, Q>(lt, lb, p, in, rhs, info, g, kTop);
 }
 
 template <class Tr, int NB, bool kFactor, bool kRO>
@@ -407,14 +407,14 @@ struct EmitY {
   }
 };
 
-template <class Tr, int NB, int kMode, bool kRO>
+template <class Tr, int NB, int kMode, bool kRO, int R1 = NB, int Q = 1>
 __device__ __forceinline__ void dev_backsub0(const LevelTables& lt, const LevelBufs<Tr, NB>& lb,
                                              const Problem0& p, const L0In<Tr>& in,
                                              const Level0Out<Tr>& o, const int32_t* info,
                                              const int32_t* skip, int64_t g) {
   const ChunkPos cp = chunk_pos(lt, g);
   if (skip && skip[cp.i]) return;
-  const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, in, nullptr, cp.i, g, cp.first, cp.T, lt.L, lt.G);
+  const CoefSource<Tr, NB, R1, Q> src = make_coef<Tr, NB, R1, Q>(p, in, nullptr, cp.i, g, cp.first, cp.T, lt.L, lt.G);
   EmitY<Tr, NB, kMode> emit{o, g, lt.G, cp.first, lt.L, info[cp.i] > 0, 0.f, 0.f};
   backsub_chunk<Tr, NB, kRO>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.xsep + g * NB,
                         cp.k > 0 ? lb.xsep + (g - 1) * NB : nullptr, emit);
@@ -424,13 +424,13 @@ __device__ __forceinline__ void dev_backsub0(const LevelTables& lt, const LevelB
   }
 }
 
-template <class Tr, int NB, int kMode>
+template <class Tr, int NB, int kMode, int R1 = NB, int Q = 1>
 __global__ void __launch_bounds__(kThreads, 4) k_backsub0(LevelTables lt, LevelBufs<Tr, NB> lb,
                                                        Problem0 p, L0In<Tr> in, Level0Out<Tr> o,
                                                        const int32_t* info, const int32_t* skip) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  dev_backsub0<Tr, NB, kMode, true>(lt, lb, p, in, o, info, skip, g);
+  dev_backsub0<Tr, NB, kMode, true, R1, Q>(lt, lb, p, in, o, info, skip, g);
 }
 
 // Per-system stop test of the refinement after a sweep: with d_k = ||dy_k|| (this sweep's
@@ -573,9 +573,10 @@ __device__ __forceinline__ void smooth_pair_residual(float s, N ws2, const N (&x
 // Level-0 source of a refinement sweep: blocks as CoefSource, right-hand side = the residual
 // r_t = rhs_t - (M x)_t evaluated on the fly in number type N (FP64 or float-float), so that
 // the residual never goes through memory.  b(t) must be called for consecutive t.
-template <class N, int NB>
+template <class N, int NB, int R1 = NB, int Q = 1>
 struct ResidualSource {
-  CoefSource<float, NB> cs;
+  static constexpr int V = NB / R1;
+  CoefSource<float, NB, R1, Q> cs;
   const float* xh;
   const float* xl;
   const float* rhs;     // explicit right-hand side (interleaved) or nullptr for beta
@@ -599,7 +600,7 @@ struct ResidualSource {
     }
   }
   // raw inputs of the next step, loaded one call ahead
-  float pc[NB], prh[NB], pd, ps;
+  float pc[Q * NB], prh[NB], pd[Q], ps;
   N px[NB];
 
   __device__ void prefetch(int64_t t) {
@@ -609,7 +610,10 @@ struct ResidualSource {
       pc[a] = ld_ro(cs.c + a * es + k);
       prh[a] = rhs ? ld_ro(rhs + a * es + k) : 0.f;
     }
-    pd = ld_ro(cs.d + k);
+#pragma unroll
+    for (int e = NB; e < Q * NB; ++e) pc[e] = ld_ro(cs.c + e * es + k);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) pd[q] = ld_ro(cs.d + q * es + k);
     if (t + 1 < cs.T) {
       ps = ld_ro(cs.s + k);
       load(t + 1, px);
@@ -623,48 +627,91 @@ struct ResidualSource {
     if (cs.first > 0) {
       N xp[NB], dummy[NB];
       load(cs.first - 1, xp);
-      smooth_pair_residual<N, NB>(cs.s[idx(cs.first - 1)], ws2, xp, xc, dummy, carry);
+      smooth_blocks(cs.s[idx(cs.first - 1)], xp, xc, dummy, carry, false);
     }
     prefetch(cs.first);
   }
+  // The smoothness rows of the pair (t, t+1), one R1 block per variable: ra receives their
+  // share of -(M x)_t; rb receives (add = false) or gains (add = true) that of -(M x)_{t+1}.
+  __device__ void smooth_blocks(float st, const N (&xa)[NB], const N (&xb)[NB], N (&ra)[NB],
+                                N (&rb)[NB], bool add) const {
+    if constexpr (V == 1) {
+      smooth_pair_residual<N, NB>(st, ws2, xa, xb, ra, rb);
+    } else {
+#pragma unroll
+      for (int b = 0; b < V; ++b) {
+        N xav[R1], xbv[R1], rav[R1], rbv[R1];
+#pragma unroll
+        for (int i = 0; i < R1; ++i) { xav[i] = xa[b * R1 + i]; xbv[i] = xb[b * R1 + i]; }
+        smooth_pair_residual<N, R1>(st, ws2, xav, xbv, rav, rbv);
+#pragma unroll
+        for (int i = 0; i < R1; ++i) {
+          ra[b * R1 + i] = rav[i];
+          rb[b * R1 + i] = add ? rb[b * R1 + i] + rbv[i] : rbv[i];
+        }
+      }
+    }
+  }
   __device__ void prime(int64_t) {}
   __device__ void commit(int64_t) {}
-  using ERaw = typename CoefSource<float, NB>::ERaw;
+  using ERaw = typename CoefSource<float, NB, R1, Q>::ERaw;
   __device__ ERaw load_e(int64_t t) const { return cs.load_e(t); }
   __device__ void e_from(ERaw r, float (&e)[NB][NB]) const { cs.e_from(r, e); }
   __device__ void A(int64_t t, float (&a)[NB][NB]) const { cs.A(t, a); }
   __device__ void E(int64_t t, float (&e)[NB][NB]) const { cs.E(t, e); }
   __device__ void b(int64_t t, float (&v)[NB]) {
-    float cv[NB], rh[NB];
+    float cv[Q * NB], rh[NB], dv_[Q];
     N xn[NB];
 #pragma unroll
-    for (int a = 0; a < NB; ++a) { cv[a] = pc[a]; rh[a] = prh[a]; xn[a] = px[a]; }
-    const float dt = pd, st = ps;
+    for (int a = 0; a < NB; ++a) { rh[a] = prh[a]; xn[a] = px[a]; }
+#pragma unroll
+    for (int e = 0; e < Q * NB; ++e) cv[e] = pc[e];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) dv_[q] = pd[q];
+    const float st = ps;
     if (t + 1 <= last) prefetch(t + 1);
     N r[NB];
-    N cx = Num<N>::zero();
+    // governing rows (Eq. 4): r -= w_gov^2 c_q (c_q.x - d_q) for each equation q
+    if constexpr (Q == 1) {
+      N cx = Num<N>::zero();
 #pragma unroll
-    for (int a = 0; a < NB; ++a) cx = cx + xc[a] * cv[a];
-    if (rhs) {
-      const N gres = -(wg2 * cx);
+      for (int a = 0; a < NB; ++a) cx = cx + xc[a] * cv[a];
+      if (rhs) {
+        const N gres = -(wg2 * cx);
 #pragma unroll
-      for (int a = 0; a < NB; ++a) r[a] = (gres * cv[a] + rh[a]) + carry[a];
+        for (int a = 0; a < NB; ++a) r[a] = (gres * cv[a] + rh[a]) + carry[a];
+      } else {
+        const N gres = wg2 * (cx - dv_[0]);
+#pragma unroll
+        for (int a = 0; a < NB; ++a) r[a] = carry[a] - gres * cv[a];
+      }
     } else {
-      const N gres = wg2 * (cx - dt);
 #pragma unroll
-      for (int a = 0; a < NB; ++a) r[a] = carry[a] - gres * cv[a];
+      for (int a = 0; a < NB; ++a) r[a] = rhs ? carry[a] + rh[a] : carry[a];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        N cx = Num<N>::zero();
+#pragma unroll
+        for (int a = 0; a < NB; ++a) cx = cx + xc[a] * cv[q * NB + a];
+        const N gres = rhs ? wg2 * cx : wg2 * (cx - dv_[q]);
+#pragma unroll
+        for (int a = 0; a < NB; ++a) r[a] = r[a] - gres * cv[q * NB + a];
+      }
     }
     if (t < cs.T_init) {
 #pragma unroll
-      for (int a = 0; a < NB; ++a)
-        if (a <= cs.R_init) {
-          const N dv = rhs ? -xc[a] : -(xc[a] - u[t * (cs.R_init + 1) + a]);
-          r[a] = r[a] + wi2 * dv;
-        }
+      for (int b = 0; b < V; ++b)
+#pragma unroll
+        for (int a = 0; a < R1; ++a)
+          if (a <= cs.R_init) {
+            const int k = b * R1 + a;
+            const N dv = rhs ? -xc[k] : -(xc[k] - u[(t * V + b) * (cs.R_init + 1) + a]);
+            r[k] = r[k] + wi2 * dv;
+          }
     }
     if (t + 1 < cs.T) {
       N ra[NB];
-      smooth_pair_residual<N, NB>(st, ws2, xc, xn, ra, carry);
+      smooth_blocks(st, xc, xn, ra, carry, false);
 #pragma unroll
       for (int a = 0; a < NB; ++a) { r[a] = r[a] + ra[a]; xc[a] = xn[a]; }
     }
@@ -674,7 +721,7 @@ struct ResidualSource {
 };
 
 // Level-0 replay of the stored FP32 factor on the refinement residual (fused, see above).
-template <class N, int NB, bool kRO>
+template <class N, int NB, bool kRO, int R1 = NB, int Q = 1>
 __device__ __forceinline__ void dev_elim0_res(const LevelTables& lt, const LevelBufs<float, NB>& lb,
                                               const Problem0& p, const L0In<float>& in,
                                               const float* x_hi, const float* x_lo,
@@ -682,8 +729,8 @@ __device__ __forceinline__ void dev_elim0_res(const LevelTables& lt, const Level
                                               bool top) {
   const ChunkPos cp = chunk_pos(lt, g);
   if (skip && skip[cp.i]) return;
-  ResidualSource<N, NB> src;
-  src.cs = make_coef<float, NB>(p, in, nullptr, cp.i, g, cp.first, cp.T, lt.L, lt.G);
+  ResidualSource<N, NB, R1, Q> src;
+  src.cs = make_coef<float, NB, R1, Q>(p, in, nullptr, cp.i, g, cp.first, cp.T, lt.L, lt.G);
   src.xh = x_hi;
   src.xl = x_lo;
   src.rhs = rhs;
@@ -698,14 +745,14 @@ __device__ __forceinline__ void dev_elim0_res(const LevelTables& lt, const Level
   if (top) solve_top<float, NB>(lb.out, g, lb.xsep + g * NB);
 }
 
-template <class N, int NB, bool kTop>
+template <class N, int NB, bool kTop, int R1 = NB, int Q = 1>
 __global__ void __launch_bounds__(kThreads) k_elim0_res(LevelTables lt, LevelBufs<float, NB> lb,
                                                         Problem0 p, L0In<float> in, const float* x_hi,
                                                         const float* x_lo, const float* rhs,
                                                         const int32_t* skip) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
-  dev_elim0_res<N, NB, true>(lt, lb, p, in, x_hi, x_lo, rhs, skip, g, kTop);
+  dev_elim0_res<N, NB, true, R1, Q>(lt, lb, p, in, x_hi, x_lo, rhs, skip, g, kTop);
 }
 
 // One whole solve pass in one launch, for plans whose systems fit a CTA at every level: the
@@ -714,7 +761,7 @@ __global__ void __launch_bounds__(kThreads) k_elim0_res(LevelTables lt, LevelBuf
 // back substitution down to level 0, with a block barrier between levels in place of a
 // launch.  The upper levels' few, short chunks run while the CTA's other warps wait, and
 // other CTAs of the SM, in other phases, keep its pipes and memory busy.
-template <class Tr, int NB, int kSrc, class N, int kMode>
+template <class Tr, int NB, int kSrc, class N, int kMode, int R1 = NB, int Q = 1>
 __global__ void __launch_bounds__(kThreads, 3) k_pass(const __grid_constant__ FusedLevels<Tr, NB> fl,
                                                       Problem0 p, L0In<Tr> in, const Tr* rhs,
                                                       const float* x_hi, const float* x_lo,
@@ -728,10 +775,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass(const __grid_constant__ Fu
     if (g < lt.coff[s1]) {
       if constexpr (kSrc == 2) {
         // x is accumulated by this launch's back substitution: plain loads
-        dev_elim0_res<N, NB, false>(lt, fl.lb[0], p, in, x_hi, x_lo, rhs, skip, g, nl == 1);
+        dev_elim0_res<N, NB, false, R1, Q>(lt, fl.lb[0], p, in, x_hi, x_lo, rhs, skip, g, nl == 1);
       } else {
         if (!(skip && skip[lt.csys[g]]))
-          dev_elim0<Tr, NB, kSrc == 0, false>(lt, fl.lb[0], p, in, rhs, info, g, nl == 1);
+          dev_elim0<Tr, NB, kSrc == 0, false, R1, Q>(lt, fl.lb[0], p, in, rhs, info, g, nl == 1);
       }
     }
   }
@@ -751,7 +798,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_pass(const __grid_constant__ Fu
   __syncthreads();
   const LevelTables& lt = fl.lt[0];
   const int64_t g = lt.coff[s0] + threadIdx.x;
-  if (g < lt.coff[s1]) dev_backsub0<Tr, NB, kMode, false>(lt, fl.lb[0], p, in, o, info, skip, g);
+  if (g < lt.coff[s1]) dev_backsub0<Tr, NB, kMode, false, R1, Q>(lt, fl.lb[0], p, in, o, info, skip, g);
 }
 
 // Levels from..top of a solve pass in one launch, for plans whose level-0 chunks exceed a CTA:
@@ -882,7 +929,7 @@ __device__ __forceinline__ float smooth_pair_grad_f32(float s, float ws2, const 
 //   dl/dw_gov = 2 w_gov sum_t (c_t.g_t)(d_t - c_t.y_t),  dl/dw_init = 2 w_init sum g (u - y),
 //   dl/dw_smooth = -2 w_smooth sum_pairs sum_r s^{2r} (f+_r e+_r + f-_r e-_r)
 // (the rows' g-values f and y-values e), written to part_w[3 g + k].
-template <class Tr, class N, int NB, bool kW>
+template <class Tr, class N, int NB, bool kW, int R1 = NB, int Q = 1>
 __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L0In<Tr> in,
                                                    const Tr* y_hi, const float* y_lo, const Tr* g_hi,
                                                    const float* g_lo, const int32_t* info, Tr* gc,
@@ -891,7 +938,8 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
   if (g >= lt.G) return;
   const ChunkPos cp = chunk_pos(lt, g);
   const int64_t G = lt.G, es = int64_t(lt.L) * G;
-  const int nu = p.T_init * (p.R_init + 1);
+  constexpr int V = NB / R1;
+  const int nu = p.T_init * V * (p.R_init + 1);
   const N wg2 = Num<N>::from_d(p.wg2), wi2 = Num<N>::from_d(p.wi2), ws2 = Num<N>::from_d(p.ws2);
   const bool failed = info[cp.i] > 0;
   N ya[NB], ga[NB];
@@ -905,37 +953,43 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
   const float wg2f = float(p.wg2), ws2f = float(p.ws2);
   double wgov = 0.0, winit = 0.0, wsm = 0.0;
   for (int64_t t = cp.first; t <= cp.last; ++t) {
-    N cy = Num<N>::zero(), cg = Num<N>::zero();
 #pragma unroll
-    for (int a = 0; a < NB; ++a) {
-      const N cv = ld_n<N>(in.c[a * es + k]);
-      cy = cy + cv * ya[a];
-      cg = cg + cv * ga[a];
-    }
-    const N e = ld_n<N>(in.d[k]) - cy;
-    if (kW) wgov += Num<N>::to_d(cg * e);
-    if constexpr (kF32) {
-      // e = d - c.y and c.g cancel and need N; the rest is FP32
-      const float ef = Num<N>::to_f(e), cgf = Num<N>::to_f(cg);
+    for (int q = 0; q < Q; ++q) {   // the governing rows (Eq. 4), one per equation q
+      N cy = Num<N>::zero(), cg = Num<N>::zero();
 #pragma unroll
-      for (int a = 0; a < NB; ++a)
-        gc[a * es + k] = failed ? nan_t<Tr>()
-                                : wg2f * fmaf(ef, Num<N>::to_f(ga[a]), -(cgf * Num<N>::to_f(ya[a])));
-      gd[k] = failed ? nan_t<Tr>() : wg2f * cgf;
-    } else {
+      for (int a = 0; a < NB; ++a) {
+        const N cv = ld_n<N>(in.c[(q * NB + a) * es + k]);
+        cy = cy + cv * ya[a];
+        cg = cg + cv * ga[a];
+      }
+      const N e = ld_n<N>(in.d[q * es + k]) - cy;
+      if (kW) wgov += Num<N>::to_d(cg * e);
+      if constexpr (kF32) {
+        // e = d - c.y and c.g cancel and need N; the rest is FP32
+        const float ef = Num<N>::to_f(e), cgf = Num<N>::to_f(cg);
 #pragma unroll
-      for (int a = 0; a < NB; ++a)
-        gc[a * es + k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * (e * ga[a] - cg * ya[a]));
-      gd[k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * cg);
+        for (int a = 0; a < NB; ++a)
+          gc[(q * NB + a) * es + k] = failed ? nan_t<Tr>()
+                                  : wg2f * fmaf(ef, Num<N>::to_f(ga[a]), -(cgf * Num<N>::to_f(ya[a])));
+        gd[q * es + k] = failed ? nan_t<Tr>() : wg2f * cgf;
+      } else {
+#pragma unroll
+        for (int a = 0; a < NB; ++a)
+          gc[(q * NB + a) * es + k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * (e * ga[a] - cg * ya[a]));
+        gd[q * es + k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * cg);
+      }
     }
     if (t < p.T_init) {
-      for (int a = 0; a <= p.R_init; ++a) {
-        gu[cp.i * nu + t * (p.R_init + 1) + a] = failed ? nan_t<Tr>() : st_n<Tr, N>(wi2 * ga[a]);
-        if (kW) {
-          const N du = ld_n<N>(static_cast<const Tr*>(p.u)[cp.i * nu + t * (p.R_init + 1) + a]) - ya[a];
-          winit += Num<N>::to_d(ga[a] * du);
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        for (int a = 0; a <= p.R_init; ++a) {
+          const int64_t iu = cp.i * nu + (t * V + v) * (p.R_init + 1) + a;
+          gu[iu] = failed ? nan_t<Tr>() : st_n<Tr, N>(wi2 * ga[v * R1 + a]);
+          if (kW) {
+            const N du = ld_n<N>(static_cast<const Tr*>(p.u)[iu]) - ya[v * R1 + a];
+            winit += Num<N>::to_d(ga[v * R1 + a] * du);
+          }
         }
-      }
     }
     N gsum = Num<N>::zero();
     const int64_t kn = t < cp.last ? k + G : g + 1;   // step t+1: next position or next chunk
@@ -946,9 +1000,24 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
         yb[a] = ld_pair<N>(y_hi, y_lo, a * es + kn);
         gb[a] = ld_pair<N>(g_hi, g_lo, a * es + kn);
       }
-      if constexpr (kF32)
-        gsum = Num<N>::from_f(smooth_pair_grad_f32<N, NB>(in.s[k], ws2f, ya, yb, ga, gb, kW ? &wsm : nullptr));
-      else gsum = smooth_pair_grad<N, NB, Tr>(in.s[k], ws2, ya, yb, ga, gb, kW ? &wsm : nullptr);
+      if constexpr (V == 1) {
+        if constexpr (kF32)
+          gsum = Num<N>::from_f(smooth_pair_grad_f32<N, NB>(in.s[k], ws2f, ya, yb, ga, gb, kW ? &wsm : nullptr));
+        else gsum = smooth_pair_grad<N, NB, Tr>(in.s[k], ws2, ya, yb, ga, gb, kW ? &wsm : nullptr);
+      } else {   // one R1 block of smoothness rows per variable, all on s_t
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          N yav[R1], ybv[R1], gav[R1], gbv[R1];
+#pragma unroll
+          for (int i = 0; i < R1; ++i) {
+            yav[i] = ya[v * R1 + i]; ybv[i] = yb[v * R1 + i];
+            gav[i] = ga[v * R1 + i]; gbv[i] = gb[v * R1 + i];
+          }
+          if constexpr (kF32)
+            gsum = gsum + Num<N>::from_f(smooth_pair_grad_f32<N, R1>(in.s[k], ws2f, yav, ybv, gav, gbv, kW ? &wsm : nullptr));
+          else gsum = gsum + smooth_pair_grad<N, R1, Tr>(in.s[k], ws2, yav, ybv, gav, gbv, kW ? &wsm : nullptr);
+        }
+      }
 #pragma unroll
       for (int a = 0; a < NB; ++a) { ya[a] = yb[a]; ga[a] = gb[a]; }
     }
@@ -1004,7 +1073,7 @@ __global__ void k_scatter_gs(GradTables gt, const int64_t* seq_soff, const int64
 }
 
 // ---- materialised assembly (App. A.2) ---------------------------------------------------
-template <class Tr, int NB>
+template <class Tr, int NB, int R1 = NB, int Q = 1>
 __global__ void __launch_bounds__(kThreads) k_assemble(LevelTables lt, Problem0 p, L0In<Tr> in, Tr* M,
                                                        Tr* N, Tr* beta) {
   constexpr int NT = NB * (NB + 1) / 2;
@@ -1012,7 +1081,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble(LevelTables lt, Problem0 
   if (g >= lt.G) return;
   const ChunkPos cp = chunk_pos(lt, g);
   const int64_t base = lt.base[cp.i];
-  const CoefSource<Tr, NB> src = make_coef<Tr, NB>(p, in, nullptr, cp.i, g, cp.first, cp.T, lt.L, lt.G);
+  const CoefSource<Tr, NB, R1, Q> src = make_coef<Tr, NB, R1, Q>(p, in, nullptr, cp.i, g, cp.first, cp.T, lt.L, lt.G);
   for (int64_t t = cp.first; t <= cp.last; ++t) {
     Tr a[NB][NB], e[NB][NB], v[NB];
     src.A(t, a);
@@ -1048,7 +1117,9 @@ struct Level {
 
 struct smnn_plan_s {
   smnn_desc desc{};
-  int NB = 0;
+  int NB = 0;       // unknowns per step, V (R+1)
+  int R1 = 0;       // R+1, the derivative orders of one variable
+  int V = 1, NQ = 1;  // variables, governing equations per step
   int device = 0;
   size_t esz = 4;
   int64_t S = 0, B = 0, D = 0, N0 = 0;
@@ -1207,8 +1278,8 @@ smnn_status build_plan_host(smnn_plan_s* pl) {
     const size_t GL = size_t(L0.G) * size_t(L0.L);
     // factor region: the staged inputs and the forward's float-float y, so that a backward
     // pass given the saved factor neither re-stages c, d, s nor re-refines y
-    pl->o_c = f; f += align_up(GL * NB * es);
-    pl->o_d = f; f += align_up(GL * es);
+    pl->o_c = f; f += align_up(GL * size_t(pl->NQ) * NB * es);
+    pl->o_d = f; f += align_up(GL * size_t(pl->NQ) * es);
     pl->o_s = f; f += align_up(GL * es);
     pl->o_fyh = f;
     if (es == 4) f += align_up(GL * NB * 4);
@@ -1225,8 +1296,8 @@ smnn_status build_plan_host(smnn_plan_s* pl) {
       pl->o_gh = take(GL * NB * 4);
       pl->o_gl = take(GL * NB * 4);
     }
-    pl->o_gc = take(GL * NB * es);
-    pl->o_gd = take(GL * es);
+    pl->o_gc = take(GL * size_t(pl->NQ) * NB * es);
+    pl->o_gd = take(GL * size_t(pl->NQ) * es);
     pl->o_part = take(size_t(L0.G) * 2 * sizeof(float));
     pl->o_prev = take(size_t(S) * sizeof(float));
     pl->o_skip = take(size_t(S) * sizeof(int32_t));
@@ -1362,7 +1433,7 @@ FusedLevels<Tr, NB> fused_levels(const smnn_plan_s* pl, char* fac, char* sol, in
 }
 
 // solve_pass of a fused plan: one k_pass launch, one CTA per entry of the CTA table.
-template <class Tr, int NB, class N>
+template <class Tr, int NB, class N, int R1 = NB, int Q = 1>
 smnn_status fused_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, bool factor,
                        char* fac, char* sol, const Level0Out<Tr>& out, int mode, int32_t* info,
                        cudaStream_t st, const ResIn* res, const int32_t* skip) {
@@ -1372,33 +1443,33 @@ smnn_status fused_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, 
   if constexpr (std::is_same<Tr, float>::value) {
     if (res) {
       if (mode != 2) return SMNN_ERR_INVALID_ARG;
-      SMNN_LAUNCH_AS("k_pass[res]", (k_pass<float, NB, 2, N, 2>), n, st, fl, p, in, res->rhs, res->xh,
+      SMNN_LAUNCH_AS("k_pass[res]", (k_pass<float, NB, 2, N, 2, R1, Q>), n, st, fl, p, in, res->rhs, res->xh,
                      res->xl, out, info, skip);
       return SMNN_OK;
     }
     if (mode == 1) {
-      if (factor) SMNN_LAUNCH_AS("k_pass[factor]", (k_pass<float, NB, 0, double, 1>), n, st, fl, p, in, rhs,
+      if (factor) SMNN_LAUNCH_AS("k_pass[factor]", (k_pass<float, NB, 0, double, 1, R1, Q>), n, st, fl, p, in, rhs,
                                  nullptr, nullptr, out, info, skip);
-      else SMNN_LAUNCH_AS("k_pass[rhs]", (k_pass<float, NB, 1, double, 1>), n, st, fl, p, in, rhs,
+      else SMNN_LAUNCH_AS("k_pass[rhs]", (k_pass<float, NB, 1, double, 1, R1, Q>), n, st, fl, p, in, rhs,
                           nullptr, nullptr, out, info, skip);
       return SMNN_OK;
     }
   }
   if (res || mode != 0) return SMNN_ERR_INVALID_ARG;
-  if (factor) SMNN_LAUNCH_AS("k_pass[factor]", (k_pass<Tr, NB, 0, double, 0>), n, st, fl, p, in, rhs,
+  if (factor) SMNN_LAUNCH_AS("k_pass[factor]", (k_pass<Tr, NB, 0, double, 0, R1, Q>), n, st, fl, p, in, rhs,
                              nullptr, nullptr, out, info, skip);
-  else SMNN_LAUNCH_AS("k_pass[rhs]", (k_pass<Tr, NB, 1, double, 0>), n, st, fl, p, in, rhs, nullptr,
+  else SMNN_LAUNCH_AS("k_pass[rhs]", (k_pass<Tr, NB, 1, double, 0, R1, Q>), n, st, fl, p, in, rhs, nullptr,
                       nullptr, out, info, skip);
   return SMNN_OK;
 }
 
-template <class Tr, int NB, class N = double>
+template <class Tr, int NB, class N = double, int R1 = NB, int Q = 1>
 smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, bool factor,
                        char* fac, char* sol, const Level0Out<Tr>& out, int mode, int32_t* info,
                        cudaStream_t st, const ResIn* res = nullptr, const int32_t* skip = nullptr) {
   const int nl = int(pl->lv.size());
   const L0In<Tr> in = l0_in<Tr>(pl, fac);
-  if (pl->fused) return fused_pass<Tr, NB, N>(pl, p, rhs, factor, fac, sol, out, mode, info, st, res, skip);
+  if (pl->fused) return fused_pass<Tr, NB, N, R1, Q>(pl, p, rhs, factor, fac, sol, out, mode, info, st, res, skip);
   for (int l = 0; l < nl; ++l) {
     const Level& L = pl->lv[l];
     const LevelTables lt = tables_of(L);
@@ -1406,8 +1477,8 @@ smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, 
     const bool top = l == nl - 1;
     if constexpr (std::is_same<Tr, float>::value) {
       if (l == 0 && res) {
-        if (top) SMNN_LAUNCH((k_elim0_res<N, NB, true>), L.G, st, lt, lb, p, in, res->xh, res->xl, res->rhs, skip);
-        else SMNN_LAUNCH((k_elim0_res<N, NB, false>), L.G, st, lt, lb, p, in, res->xh, res->xl, res->rhs, skip);
+        if (top) SMNN_LAUNCH((k_elim0_res<N, NB, true, R1, Q>), L.G, st, lt, lb, p, in, res->xh, res->xl, res->rhs, skip);
+        else SMNN_LAUNCH((k_elim0_res<N, NB, false, R1, Q>), L.G, st, lt, lb, p, in, res->xh, res->xl, res->rhs, skip);
         continue;
       }
     }
@@ -1419,10 +1490,10 @@ smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, 
       break;
     }
     if (l == 0) {
-      if (factor && top) SMNN_LAUNCH_AS("k_elim0[factor]", (k_elim0<Tr, NB, true, true>), L.G, st, lt, lb, p, in, rhs, info);
-      else if (factor) SMNN_LAUNCH_AS("k_elim0[factor]", (k_elim0<Tr, NB, true, false>), L.G, st, lt, lb, p, in, rhs, info);
-      else if (top) SMNN_LAUNCH((k_elim0<Tr, NB, false, true>), L.G, st, lt, lb, p, in, rhs, info);
-      else SMNN_LAUNCH((k_elim0<Tr, NB, false, false>), L.G, st, lt, lb, p, in, rhs, info);
+      if (factor && top) SMNN_LAUNCH_AS("k_elim0[factor]", (k_elim0<Tr, NB, true, true, R1, Q>), L.G, st, lt, lb, p, in, rhs, info);
+      else if (factor) SMNN_LAUNCH_AS("k_elim0[factor]", (k_elim0<Tr, NB, true, false, R1, Q>), L.G, st, lt, lb, p, in, rhs, info);
+      else if (top) SMNN_LAUNCH((k_elim0<Tr, NB, false, true, R1, Q>), L.G, st, lt, lb, p, in, rhs, info);
+      else SMNN_LAUNCH((k_elim0<Tr, NB, false, false, R1, Q>), L.G, st, lt, lb, p, in, rhs, info);
     } else {
       const ChunkOut<Tr, NB> prev = bufs_of<Tr, NB>(pl->lv[l - 1], fac, sol).out;
       if (factor && top) SMNN_LAUNCH_AS("k_elimN[factor]", (k_elimN<Tr, NB, true, true>), L.G, st, lt, lb, prev, pl->d_sys_T, info, nullptr);
@@ -1440,10 +1511,10 @@ smnn_status solve_pass(const smnn_plan_s* pl, const Problem0& p, const Tr* rhs, 
   const Level& L0 = pl->lv[0];
   const LevelBufs<Tr, NB> lb0 = bufs_of<Tr, NB>(L0, fac, sol);
   if (mode == 0) {
-    SMNN_LAUNCH((k_backsub0<Tr, NB, 0>), L0.G, st, tables_of(L0), lb0, p, in, out, info, skip);
+    SMNN_LAUNCH((k_backsub0<Tr, NB, 0, R1, Q>), L0.G, st, tables_of(L0), lb0, p, in, out, info, skip);
   } else if constexpr (std::is_same<Tr, float>::value) {
-    if (mode == 1) SMNN_LAUNCH((k_backsub0<Tr, NB, 1>), L0.G, st, tables_of(L0), lb0, p, in, out, info, skip);
-    else SMNN_LAUNCH((k_backsub0<Tr, NB, 2>), L0.G, st, tables_of(L0), lb0, p, in, out, info, skip);
+    if (mode == 1) SMNN_LAUNCH((k_backsub0<Tr, NB, 1, R1, Q>), L0.G, st, tables_of(L0), lb0, p, in, out, info, skip);
+    else SMNN_LAUNCH((k_backsub0<Tr, NB, 2, R1, Q>), L0.G, st, tables_of(L0), lb0, p, in, out, info, skip);
   }
   return SMNN_OK;
 }
@@ -1516,13 +1587,13 @@ smnn_status tile_copy(const smnn_plan_s* pl, const Ts* src, const float* src_lo,
   return cudaGetLastError() == cudaSuccess ? SMNN_OK : SMNN_ERR_CUDA;
 }
 
-template <class Tr, int NB>
+template <class Tr, int NB, int R1 = NB, int Q = 1>
 smnn_status gather_inputs(const smnn_plan_s* pl, const Problem0& p, const L0Bufs<Tr>& b,
                           const Tr* vec, Tr* vec_out, float* vec_lo, bool coefs, cudaStream_t st) {
   smnn_status rc = SMNN_OK;
   if (coefs) {
-    rc = tile_copy<Tr, Tr, NB, true>(pl, static_cast<const Tr*>(p.c), nullptr, b.c, nullptr, st);
-    if (rc == SMNN_OK) rc = tile_copy<Tr, Tr, 1, true>(pl, static_cast<const Tr*>(p.d), nullptr, b.d, nullptr, st);
+    rc = tile_copy<Tr, Tr, Q * NB, true>(pl, static_cast<const Tr*>(p.c), nullptr, b.c, nullptr, st);
+    if (rc == SMNN_OK) rc = tile_copy<Tr, Tr, Q, true>(pl, static_cast<const Tr*>(p.d), nullptr, b.d, nullptr, st);
     if (rc != SMNN_OK) return rc;
     SMNN_LAUNCH(k_gather_s<Tr>, l0_elems(pl), st, tables_of(pl->lv[0]), p, b.s);
   }
@@ -1535,7 +1606,7 @@ smnn_status gather_inputs(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
 // K refinement sweeps of x (float-float) against rhs (nullptr: beta).  With desc.refine_tol
 // > 0 each system stops as soon as its estimated error is <= refine_tol ||x|| (k_converge),
 // and systems still above it after the last sweep get info = -1.
-template <class N, int NB>
+template <class N, int NB, int R1 = NB, int Q = 1>
 smnn_status refine_sweeps(const smnn_plan_s* pl, const Problem0& p, char* fac, char* sol, float* xh,
                           float* xl, const float* rhs, int K, int32_t* info, cudaStream_t st) {
   const L0Bufs<float> b = l0_bufs<float>(pl, fac, sol);
@@ -1544,7 +1615,7 @@ smnn_status refine_sweeps(const smnn_plan_s* pl, const Problem0& p, char* fac, c
   for (int it = 0; it < K; ++it) {
     const ResIn ri{xh, xl, rhs};
     Level0Out<float> oa{nullptr, xh, xl, adaptive ? b.part : nullptr};
-    SMNN_TRY((solve_pass<float, NB, N>(pl, p, nullptr, false, fac, sol, oa, 2, info, st, &ri,
+    SMNN_TRY((solve_pass<float, NB, N, R1, Q>(pl, p, nullptr, false, fac, sol, oa, 2, info, st, &ri,
                                        adaptive ? b.skip : nullptr)));
     if (adaptive)
       SMNN_LAUNCH(k_converge, pl->S * 32, st, pl->S, pl->lv[0].d_coff, b.part, b.prev, b.skip,
@@ -1556,7 +1627,7 @@ smnn_status refine_sweeps(const smnn_plan_s* pl, const Problem0& p, char* fac, c
 // Forward solve with refinement in number type N (double: FP64 residual; ff: float-float).
 // The accumulator's low part lives in the factor region so that smnn_backward, given the same
 // factor buffer, starts from the refined y without refining it again.
-template <class N, int NB>
+template <class N, int NB, int R1 = NB, int Q = 1>
 smnn_status refine_forward(const smnn_plan_s* pl, const Problem0& p, char* fac, char* sol,
                            int32_t* info, cudaStream_t st) {
   const L0Bufs<float> b = l0_bufs<float>(pl, fac, sol);
@@ -1564,25 +1635,25 @@ smnn_status refine_forward(const smnn_plan_s* pl, const Problem0& p, char* fac, 
   float* yl = reinterpret_cast<float*>(fac + pl->o_fyl);
   const int K = pl->desc.max_refine;
   Level0Out<float> o{nullptr, yh, yl, nullptr};
-  SMNN_TRY((solve_pass<float, NB>(pl, p, nullptr, true, fac, sol, o, 1, info, st)));
-  return refine_sweeps<N, NB>(pl, p, fac, sol, yh, yl, nullptr, K, info, st);
+  SMNN_TRY((solve_pass<float, NB, double, R1, Q>(pl, p, nullptr, true, fac, sol, o, 1, info, st)));
+  return refine_sweeps<N, NB, R1, Q>(pl, p, fac, sol, yh, yl, nullptr, K, info, st);
 }
 
 // Adjoint: g = M^{-1} gy refined KA times (float-float accumulator).  y: with a saved factor
 // the forward's float-float y is reused (its low part was kept in the factor region);
 // otherwise y is refined once from the caller's FP32 y.  Returns the y pair used.
-template <class N, int NB>
+template <class N, int NB, int R1 = NB, int Q = 1>
 smnn_status refine_backward(const smnn_plan_s* pl, const Problem0& p, char* fac, char* sol,
                             bool recompute, const float* y, int32_t* info, cudaStream_t st,
                             const float** y_hi_used, const float** y_lo_used) {
   const L0Bufs<float> b = l0_bufs<float>(pl, fac, sol);
   const int KA = pl->desc.precision == SMNN_F32 ? 0 : pl->desc.adjoint_refine;
   Level0Out<float> og{nullptr, b.gh, b.gl, nullptr};
-  SMNN_TRY((solve_pass<float, NB>(pl, p, b.gy, recompute, fac, sol, og, 1, info, st)));
+  SMNN_TRY((solve_pass<float, NB, double, R1, Q>(pl, p, b.gy, recompute, fac, sol, og, 1, info, st)));
   *y_hi_used = b.yh;
   *y_lo_used = nullptr;
   const bool reuse = KA > 0 && !recompute && pl->desc.max_refine > 0;
-  if (!reuse) SMNN_TRY((gather_inputs<float, NB>(pl, p, b, y, b.yh, b.yl, false, st)));
+  if (!reuse) SMNN_TRY((gather_inputs<float, NB, R1, Q>(pl, p, b, y, b.yh, b.yl, false, st)));
   if (KA > 0) {
     if (reuse) {
       *y_hi_used = reinterpret_cast<const float*>(fac + pl->o_fyh);
@@ -1590,14 +1661,14 @@ smnn_status refine_backward(const smnn_plan_s* pl, const Problem0& p, char* fac,
     } else {
       const ResIn ri{b.yh, nullptr, nullptr};
       Level0Out<float> oy{nullptr, b.yh, b.yl, nullptr};
-      SMNN_TRY((solve_pass<float, NB, N>(pl, p, nullptr, false, fac, sol, oy, 2, info, st, &ri)));
+      SMNN_TRY((solve_pass<float, NB, N, R1, Q>(pl, p, nullptr, false, fac, sol, oy, 2, info, st, &ri)));
       *y_lo_used = b.yl;
     }
   }
-  return refine_sweeps<N, NB>(pl, p, fac, sol, b.gh, b.gl, b.gy, KA, info, st);
+  return refine_sweeps<N, NB, R1, Q>(pl, p, fac, sol, b.gh, b.gl, b.gy, KA, info, st);
 }
 
-template <class Tr, class N, int NB>
+template <class Tr, class N, int NB, int R1 = NB, int Q = 1>
 smnn_status gradients_out(const smnn_plan_s* pl, const Problem0& p, const L0Bufs<Tr>& b,
                           const Tr* yh, const float* yl, const Tr* gh, const float* gl,
                           int32_t* info, Tr* gc, Tr* gd, Tr* gs, Tr* gu, double* gw, cudaStream_t st) {
@@ -1605,7 +1676,7 @@ smnn_status gradients_out(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
   GradTables gt{pl->d_sq_b, pl->d_sq_k, L0.d_coff, pl->d_sys_T, pl->Q, L0.G, L0.L, int(pl->D)};
   const L0In<Tr> in{b.c, b.d, b.s};
   if (gw) {
-    SMNN_LAUNCH((k_grad<Tr, N, NB, true>), L0.G, st, tables_of(L0), p, in, yh, yl, gh, gl, info, b.gc,
+    SMNN_LAUNCH((k_grad<Tr, N, NB, true, R1, Q>), L0.G, st, tables_of(L0), p, in, yh, yl, gh, gl, info, b.gc,
                 b.gd, b.gs, gu, b.pw);
     if (cudaGetLastError() != cudaSuccess) return SMNN_ERR_CUDA;
     prof_begin("k_reduce_w", st);
@@ -1614,16 +1685,16 @@ smnn_status gradients_out(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (cudaGetLastError() != cudaSuccess) return SMNN_ERR_CUDA;
   } else {
-    SMNN_LAUNCH((k_grad<Tr, N, NB, false>), L0.G, st, tables_of(L0), p, in, yh, yl, gh, gl, info,
+    SMNN_LAUNCH((k_grad<Tr, N, NB, false, R1, Q>), L0.G, st, tables_of(L0), p, in, yh, yl, gh, gl, info,
                 b.gc, b.gd, b.gs, gu, nullptr);
   }
-  SMNN_TRY((tile_copy<Tr, Tr, NB, false>(pl, b.gc, nullptr, gc, nullptr, st)));
-  SMNN_TRY((tile_copy<Tr, Tr, 1, false>(pl, b.gd, nullptr, gd, nullptr, st)));
+  SMNN_TRY((tile_copy<Tr, Tr, Q * NB, false>(pl, b.gc, nullptr, gc, nullptr, st)));
+  SMNN_TRY((tile_copy<Tr, Tr, Q, false>(pl, b.gd, nullptr, gd, nullptr, st)));
   SMNN_LAUNCH(k_scatter_gs<Tr>, pl->Q * int64_t(L0.L), st, gt, pl->d_seq_soff, pl->d_seq_T, b.gs, gs);
   return SMNN_OK;
 }
 
-template <class Tr, int NB>
+template <class Tr, int NB, int R1 = NB, int Q = 1>
 smnn_status factor_solve_t(const smnn_plan_s* pl, const void* c, const void* d, const void* s,
                            const void* u, void* y, void* factor, int32_t* info, void* ws,
                            cudaStream_t st) {
@@ -1633,11 +1704,11 @@ smnn_status factor_solve_t(const smnn_plan_s* pl, const void* c, const void* d, 
   const L0Bufs<Tr> b = l0_bufs<Tr>(pl, fac, sol);
   const LevelTables lt0 = tables_of(pl->lv[0]);
   SMNN_LAUNCH(k_fill_i32, pl->S, st, info, pl->S, 0);
-  SMNN_TRY((gather_inputs<Tr, NB>(pl, p, b, nullptr, nullptr, nullptr, true, st)));
+  SMNN_TRY((gather_inputs<Tr, NB, R1, Q>(pl, p, b, nullptr, nullptr, nullptr, true, st)));
   if constexpr (std::is_same<Tr, float>::value) {
     if (pl->desc.precision == SMNN_F32_REFINED || pl->desc.precision == SMNN_F32_REFINED_DF) {
-      if (pl->desc.precision == SMNN_F32_REFINED) SMNN_TRY((refine_forward<double, NB>(pl, p, fac, sol, info, st)));
-      else SMNN_TRY((refine_forward<ff, NB>(pl, p, fac, sol, info, st)));
+      if (pl->desc.precision == SMNN_F32_REFINED) SMNN_TRY((refine_forward<double, NB, R1, Q>(pl, p, fac, sol, info, st)));
+      else SMNN_TRY((refine_forward<ff, NB, R1, Q>(pl, p, fac, sol, info, st)));
       return tile_copy<float, float, NB, false>(pl, reinterpret_cast<const float*>(fac + pl->o_fyh),
                                                 reinterpret_cast<const float*>(fac + pl->o_fyl),
                                                 static_cast<float*>(y), nullptr, st);
@@ -1645,11 +1716,11 @@ smnn_status factor_solve_t(const smnn_plan_s* pl, const void* c, const void* d, 
     }
   }
   Level0Out<Tr> o{b.x, nullptr, nullptr, nullptr};
-  SMNN_TRY((solve_pass<Tr, NB>(pl, p, nullptr, true, fac, sol, o, 0, info, st)));
+  SMNN_TRY((solve_pass<Tr, NB, double, R1, Q>(pl, p, nullptr, true, fac, sol, o, 0, info, st)));
   return tile_copy<Tr, Tr, NB, false>(pl, b.x, nullptr, static_cast<Tr*>(y), nullptr, st);
 }
 
-template <class Tr, int NB>
+template <class Tr, int NB, int R1 = NB, int Q = 1>
 smnn_status backward_t(const smnn_plan_s* pl, const void* c, const void* d, const void* s,
                        const void* u, const void* y, const void* factor, const void* gy, void* gc,
                        void* gd, void* gs, void* gu, void* gw, int32_t* info, void* ws,
@@ -1660,7 +1731,7 @@ smnn_status backward_t(const smnn_plan_s* pl, const void* c, const void* d, cons
   const L0Bufs<Tr> b = l0_bufs<Tr>(pl, fac, sol);
   SMNN_LAUNCH(k_fill_i32, pl->S, st, info, pl->S, 0);
   // with the saved factor, the forward's staged c, d, s are still in the factor region
-  SMNN_TRY((gather_inputs<Tr, NB>(pl, p, b, static_cast<const Tr*>(gy), b.gy, nullptr, factor == nullptr, st)));
+  SMNN_TRY((gather_inputs<Tr, NB, R1, Q>(pl, p, b, static_cast<const Tr*>(gy), b.gy, nullptr, factor == nullptr, st)));
   Tr* gco = static_cast<Tr*>(gc);
   Tr* gdo = static_cast<Tr*>(gd);
   Tr* gso = static_cast<Tr*>(gs);
@@ -1671,43 +1742,48 @@ smnn_status backward_t(const smnn_plan_s* pl, const void* c, const void* d, cons
     const float* yh = nullptr;
     const float* yl = nullptr;
     if (pl->desc.precision == SMNN_F32_REFINED_DF) {
-      SMNN_TRY((refine_backward<ff, NB>(pl, p, fac, sol, factor == nullptr, y32, info, st, &yh, &yl)));
-      return gradients_out<float, ff, NB>(pl, p, b, yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, gwo, st);
+      SMNN_TRY((refine_backward<ff, NB, R1, Q>(pl, p, fac, sol, factor == nullptr, y32, info, st, &yh, &yl)));
+      return gradients_out<float, ff, NB, R1, Q>(pl, p, b, yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, gwo, st);
     }
-    SMNN_TRY((refine_backward<double, NB>(pl, p, fac, sol, factor == nullptr, y32, info, st, &yh, &yl)));
-    return gradients_out<float, double, NB>(pl, p, b, yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, gwo, st);
+    SMNN_TRY((refine_backward<double, NB, R1, Q>(pl, p, fac, sol, factor == nullptr, y32, info, st, &yh, &yl)));
+    return gradients_out<float, double, NB, R1, Q>(pl, p, b, yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, gwo, st);
   } else {
     Level0Out<Tr> o{b.g, nullptr, nullptr, nullptr};
-    SMNN_TRY((solve_pass<Tr, NB>(pl, p, b.gy, factor == nullptr, fac, sol, o, 0, info, st)));
-    SMNN_TRY((gather_inputs<Tr, NB>(pl, p, b, static_cast<const Tr*>(y), b.x, nullptr, false, st)));
-    return gradients_out<Tr, double, NB>(pl, p, b, b.x, nullptr, b.g, nullptr, info, gco, gdo, gso, guo, gwo, st);
+    SMNN_TRY((solve_pass<Tr, NB, double, R1, Q>(pl, p, b.gy, factor == nullptr, fac, sol, o, 0, info, st)));
+    SMNN_TRY((gather_inputs<Tr, NB, R1, Q>(pl, p, b, static_cast<const Tr*>(y), b.x, nullptr, false, st)));
+    return gradients_out<Tr, double, NB, R1, Q>(pl, p, b, b.x, nullptr, b.g, nullptr, info, gco, gdo, gso, guo, gwo, st);
   }
 }
 
-template <class Tr, int NB>
+template <class Tr, int NB, int R1 = NB, int Q = 1>
 smnn_status assemble_t(const smnn_plan_s* pl, const void* c, const void* d, const void* s,
                        const void* u, void* M, void* N, void* beta, void* ws, cudaStream_t st) {
   const Problem0 p = problem0(pl, c, d, s, u);
   char* fac = static_cast<char*>(ws);
   char* sol = static_cast<char*>(ws) + pl->factor_bytes;
   const L0Bufs<Tr> b = l0_bufs<Tr>(pl, fac, sol);
-  SMNN_TRY((gather_inputs<Tr, NB>(pl, p, b, nullptr, nullptr, nullptr, true, st)));
+  SMNN_TRY((gather_inputs<Tr, NB, R1, Q>(pl, p, b, nullptr, nullptr, nullptr, true, st)));
   const L0In<Tr> in{b.c, b.d, b.s};
-  SMNN_LAUNCH((k_assemble<Tr, NB>), pl->lv[0].G, st, tables_of(pl->lv[0]), p, in, static_cast<Tr*>(M),
+  SMNN_LAUNCH((k_assemble<Tr, NB, R1, Q>), pl->lv[0].G, st, tables_of(pl->lv[0]), p, in, static_cast<Tr*>(M),
               static_cast<Tr*>(N), static_cast<Tr*>(beta));
   return SMNN_OK;
 }
 
 // Runs fn<Tr, NB>(...) for the plan's precision and block size.
+// Instantiated step shapes (n_b = V (R+1), R+1, Q): one variable with R = 1..3 and one
+// governing equation; and V = 2 variables of R = 1 with one or two equations per step.
+#define SMNN_SHAPE(pl, NB_, R1_, Q_, fn, ...)                                         \
+  if ((pl)->NB == NB_ && (pl)->R1 == R1_ && (pl)->NQ == Q_)                           \
+    return (pl)->desc.precision == SMNN_F64 ? fn<double, NB_, R1_, Q_>(__VA_ARGS__)   \
+                                            : fn<float, NB_, R1_, Q_>(__VA_ARGS__)
 #define SMNN_DISPATCH(pl, fn, ...)                                                    \
   do {                                                                                \
-    const bool f64 = (pl)->desc.precision == SMNN_F64;                                \
-    switch ((pl)->NB) {                                                               \
-      case 2: return f64 ? fn<double, 2>(__VA_ARGS__) : fn<float, 2>(__VA_ARGS__);    \
-      case 3: return f64 ? fn<double, 3>(__VA_ARGS__) : fn<float, 3>(__VA_ARGS__);    \
-      case 4: return f64 ? fn<double, 4>(__VA_ARGS__) : fn<float, 4>(__VA_ARGS__);    \
-      default: return SMNN_ERR_UNSUPPORTED;                                           \
-    }                                                                                 \
+    SMNN_SHAPE(pl, 2, 2, 1, fn, __VA_ARGS__);                                         \
+    SMNN_SHAPE(pl, 3, 3, 1, fn, __VA_ARGS__);                                         \
+    SMNN_SHAPE(pl, 4, 4, 1, fn, __VA_ARGS__);                                         \
+    SMNN_SHAPE(pl, 4, 2, 1, fn, __VA_ARGS__);                                         \
+    SMNN_SHAPE(pl, 4, 2, 2, fn, __VA_ARGS__);                                         \
+    return SMNN_ERR_UNSUPPORTED;                                                      \
   } while (0)
 
 inline bool aligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) % kAlign) == 0; }
@@ -1736,6 +1812,8 @@ smnn_status plan_init(const smnn_desc* desc, smnn_plan_s* pl) {
   if (!desc) return SMNN_ERR_INVALID_ARG;
   const smnn_desc& d = *desc;
   if (d.R < 1 || d.R > SMNN_MAX_R || d.R_init < 0 || d.R_init > d.R || d.T_init < 1) return SMNN_ERR_INVALID_ARG;
+  if (d.V < 0 || d.Q < 0 || d.Q > 2 || (d.V > 1 ? d.V : 1) * (d.R + 1) > SMNN_MAX_R + 1)
+    return SMNN_ERR_INVALID_ARG;
   if (d.precision < SMNN_F32_REFINED || d.precision > SMNN_F32_REFINED_DF) return SMNN_ERR_INVALID_ARG;
   if (d.algo < SMNN_ALGO_AUTO || d.algo > SMNN_ALGO_CR_FUSED) return SMNN_ERR_INVALID_ARG;
   if (d.max_refine < 0 || d.max_refine > 16 || d.adjoint_refine < 0 || d.adjoint_refine > 16 ||
@@ -1748,7 +1826,16 @@ smnn_status plan_init(const smnn_desc* desc, smnn_plan_s* pl) {
   if (!d.seq_T && (d.T < 1 || d.T < d.T_init)) return SMNN_ERR_INVALID_ARG;
   pl->desc = d;
   pl->desc.seq_T = nullptr;
-  pl->NB = d.R + 1;
+  pl->V = d.V == 0 ? 1 : d.V;
+  pl->NQ = d.Q == 0 ? 1 : d.Q;
+  pl->desc.V = pl->V;
+  pl->desc.Q = pl->NQ;
+  pl->R1 = d.R + 1;
+  pl->NB = pl->V * pl->R1;
+  // the instantiated step shapes (SMNN_DISPATCH): one variable and one equation, or
+  // V = 2 variables of R = 1 with one or two equations
+  const bool shape_ok = (pl->V == 1 && pl->NQ == 1) || (pl->V == 2 && pl->R1 == 2);
+  if (!shape_ok) return SMNN_ERR_UNSUPPORTED;
   pl->esz = d.precision == SMNN_F64 ? 8 : 4;
   pl->B = d.num_seq;
   pl->D = d.dims_per_seq;
@@ -1908,7 +1995,7 @@ smnn_status smnn_profile_read(smnn_kernel_time* out, int max, int* n) {
     if (cudaEventSynchronize(r.e1) != cudaSuccess) return SMNN_ERR_CUDA;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) return SMNN_ERR_CUDA;
-    // name: "(k_elim0<Tr, NB, true, true>)" -> "k_elim0"
+    // name: "(k_elim0<Tr, NB, true, ...>)" -> "k_elim0"
     const char* p = r.name;
     while (*p == '(') ++p;
     char nm[48] = {0};

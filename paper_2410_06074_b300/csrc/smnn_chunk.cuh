@@ -272,15 +272,21 @@ struct ChunkOut {
 // ----------------------------------------------------------------------------- sources
 
 // Level-0 blocks, assembled in registers from the paper's representation {c, d, u, s}
-// (App. A.2).  The per-step inputs sit in the chunk-interleaved layout of the factor:
-// element e of in-chunk position j of chunk g at [(e*L + j)*G + g]; steps of the previous
-// chunk (g-1, position L-1) are reached for t = first-1.
-template <class Tr, int NB>
+// (App. A.2).  A step holds NB = V R1 unknowns, V variables of R1 = R+1 derivative orders
+// (variable-major), and Q governing equations (Sec. 3.1): M_t's governing part is
+// sum_q w_gov^2 c_q c_q^T, its smoothness part and N_t are block diagonal over the V
+// variables (each the R1 x R1 form of App. A.2, one step size s_t for all), and the
+// initial rows act per variable.  V = Q = 1 is the scalar case.  The per-step inputs sit in
+// the chunk-interleaved layout of the factor: element e of in-chunk position j of chunk g
+// at [(e*L + j)*G + g] (c: Q*NB planes, equation-major; d: Q planes); steps of the
+// previous chunk (g-1, position L-1) are reached for t = first-1.
+template <class Tr, int NB, int R1 = NB, int Q = 1>
 struct CoefSource {
-  const Tr* c;     // [NB][L][G]
-  const Tr* d;     // [L][G]
+  static constexpr int V = NB / R1;
+  const Tr* c;     // [Q*NB][L][G]
+  const Tr* d;     // [Q][L][G]
   const Tr* s;     // [L][G]
-  const Tr* u;     // this system's initial values [T_init][R_init+1]
+  const Tr* u;     // this system's initial values [T_init][V][R_init+1]
   const Tr* rhs;   // explicit right-hand side [NB][L][G], or nullptr for beta_t
   int64_t T, first, g, G;
   int L;
@@ -296,19 +302,22 @@ struct CoefSource {
   // inputs, commit(t) makes them the ones A(t) and b(t) use.  Without a commit A and b load
   // directly.
   struct Stage {
-    Tr c[NB], rh[NB];
-    Tr d, s, sp;
+    Tr c[Q * NB], rh[NB];
+    Tr d[Q];
+    Tr s, sp;
   };
   Stage cur, nxt;
   int64_t cur_t = -1;
   SMNN_HD void prime(int64_t t) {
     const int64_t k = at(t);
 #pragma unroll
-    for (int r = 0; r < NB; ++r) {
-      nxt.c[r] = ld_ro(c + r * es() + k);
-      if (rhs) nxt.rh[r] = ld_ro(rhs + r * es() + k);
+    for (int e = 0; e < Q * NB; ++e) nxt.c[e] = ld_ro(c + e * es() + k);
+    if (rhs) {
+#pragma unroll
+      for (int r = 0; r < NB; ++r) nxt.rh[r] = ld_ro(rhs + r * es() + k);
     }
-    nxt.d = ld_ro(d + k);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) nxt.d[q] = ld_ro(d + q * es() + k);
     nxt.s = ld_ro(s + k);
     nxt.sp = t > 0 ? ld_ro(s + at(t - 1)) : Tr(0);
   }
@@ -320,38 +329,50 @@ struct CoefSource {
   SMNN_HD void A(int64_t t, Tr (&a)[NB][NB]) const {
     const int64_t k = at(t);
     const bool st = t == cur_t;
-    Tr cv[NB];
+    Tr cv[Q * NB];
 #pragma unroll
-    for (int r = 0; r < NB; ++r) cv[r] = st ? cur.c[r] : c[r * es() + k];
+    for (int e = 0; e < Q * NB; ++e) cv[e] = st ? cur.c[e] : c[e * es() + k];
 #pragma unroll
     for (int i = 0; i < NB; ++i)
 #pragma unroll
-      for (int j = 0; j < NB; ++j) a[i][j] = wg2 * cv[i] * cv[j];
+      for (int j = 0; j < NB; ++j) {
+        if (Q == 1) {
+          a[i][j] = wg2 * cv[i] * cv[j];
+        } else {
+          Tr acc = Tr(0);
+#pragma unroll
+          for (int q = 0; q < Q; ++q) acc += cv[q * NB + i] * cv[q * NB + j];
+          a[i][j] = wg2 * acc;
+        }
+      }
     if (t < T_init) {
 #pragma unroll
-      for (int r = 0; r < NB; ++r)
-        if (r <= R_init) a[r][r] += wi2;
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int r = 0; r < R1; ++r)
+          if (r <= R_init) a[v * R1 + r][v * R1 + r] += wi2;
     }
     if (t + 1 < T) add_smooth<false>(st ? cur.s : s[k], a);
     if (t > 0) add_smooth<true>(st ? cur.sp : s[at(t - 1)], a);
   }
 
   // w_s^2 ((S+- F^T F S+-) + S2) of the pair (t, t+1), seen from t (kMinus = false) or
-  // from t+1 (kMinus = true).
+  // from t+1 (kMinus = true), for each variable's R1 x R1 diagonal block.
   template <bool kMinus>
   SMNN_HD void add_smooth(Tr st, Tr (&a)[NB][NB]) const {
-    Tr pw[2 * NB - 1];
+    Tr pw[2 * R1 - 1];
     pw[0] = Tr(1);
 #pragma unroll
-    for (int k = 1; k < 2 * NB - 1; ++k) pw[k] = pw[k - 1] * st;
+    for (int k = 1; k < 2 * R1 - 1; ++k) pw[k] = pw[k - 1] * st;
 #pragma unroll
-    for (int i = 0; i < NB; ++i)
+    for (int i = 0; i < R1; ++i)
 #pragma unroll
-      for (int j = 0; j < NB; ++j) {
+      for (int j = 0; j < R1; ++j) {
         Tr v = Tr(ftf_coef(i, j)) * pw[i + j];
         if (kMinus && ((i + j) & 1)) v = -v;
         if (i == j) v += pw[2 * i];
-        a[i][j] += ws2 * v;
+#pragma unroll
+        for (int b = 0; b < V; ++b) a[b * R1 + i][b * R1 + j] += ws2 * v;
       }
   }
 
@@ -363,17 +384,31 @@ struct CoefSource {
       for (int r = 0; r < NB; ++r) v[r] = st ? cur.rh[r] : rhs[r * es() + k];
       return;
     }
-    const Tr dt = st ? cur.d : d[k];
+    if (Q == 1) {
+      const Tr dt = st ? cur.d[0] : d[k];
 #pragma unroll
-    for (int r = 0; r < NB; ++r) v[r] = wg2 * (st ? cur.c[r] : c[r * es() + k]) * dt;
+      for (int r = 0; r < NB; ++r) v[r] = wg2 * (st ? cur.c[r] : c[r * es() + k]) * dt;
+    } else {
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        Tr acc = Tr(0);
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          acc += (st ? cur.c[q * NB + r] : c[(q * NB + r) * es() + k]) * (st ? cur.d[q] : d[q * es() + k]);
+        v[r] = wg2 * acc;
+      }
+    }
     if (t < T_init) {
 #pragma unroll
-      for (int r = 0; r < NB; ++r)
-        if (r <= R_init) v[r] += wi2 * u[t * (R_init + 1) + r];
+      for (int b = 0; b < V; ++b)
+#pragma unroll
+        for (int r = 0; r < R1; ++r)
+          if (r <= R_init) v[b * R1 + r] += wi2 * u[(t * V + b) * (R_init + 1) + r];
     }
   }
 
-  // E_t = N_t = block (t+1, t), t < T-1; its raw data is the step size s_t
+  // E_t = N_t = block (t+1, t), t < T-1, block diagonal over the variables; its raw data
+  // is the step size s_t
   using ERaw = Tr;
   SMNN_HD ERaw load_e(int64_t t) const { return ld_ro(s + at(t)); }
   // s_t is staged with step t (as s) and with step t+1 (as its previous step size)
@@ -381,14 +416,17 @@ struct CoefSource {
     e_from(t + 1 == cur_t ? cur.sp : (t == cur_t ? cur.s : load_e(t)), e);
   }
   SMNN_HD void e_from(ERaw st, Tr (&e)[NB][NB]) const {
-    Tr pw[2 * NB - 1];
+    Tr pw[2 * R1 - 1];
     pw[0] = Tr(1);
 #pragma unroll
-    for (int k = 1; k < 2 * NB - 1; ++k) pw[k] = pw[k - 1] * st;
+    for (int k = 1; k < 2 * R1 - 1; ++k) pw[k] = pw[k - 1] * st;
 #pragma unroll
     for (int i = 0; i < NB; ++i)
 #pragma unroll
-      for (int j = 0; j < NB; ++j) e[i][j] = -ws2 * Tr(n_coef(i, j)) * pw[i + j];
+      for (int j = 0; j < NB; ++j) {
+        const int bi = i / R1, bj = j / R1, ii = i % R1, jj = j % R1;
+        e[i][j] = bi == bj ? -ws2 * Tr(n_coef(ii, jj)) * pw[ii + jj] : Tr(0);
+      }
   }
 };
 

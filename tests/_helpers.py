@@ -6,7 +6,8 @@ import oracle as O
 
 
 def oracle_params(prob):
-    return O.Params(prob.R, prob.R_init, prob.T_init, prob.w_gov, prob.w_init, prob.w_smooth)
+    return O.Params(prob.R, prob.R_init, prob.T_init, prob.w_gov, prob.w_init, prob.w_smooth,
+                    V=prob.V, Q=prob.Q)
 
 
 def dev(prob, dtype):
@@ -18,6 +19,8 @@ def dev(prob, dtype):
 
 def cfg_of(prob, precision, **kw):
     from paper_2410_06074_b300 import SolveConfig
+    kw.setdefault("V", prob.V)
+    kw.setdefault("Q", prob.Q)
     return SolveConfig(R_init=prob.R_init, T_init=prob.T_init, w_gov=prob.w_gov,
                        w_init=prob.w_init, w_smooth=prob.w_smooth, precision=precision, **kw)
 
@@ -42,7 +45,7 @@ def gpu_grad(prob, gy, precision, store_factor=True, **kw):
     dt = np_dtype(precision)
     c, d, s, u = dev(prob, dt)
     cfg = cfg_of(prob, precision, **kw)
-    plan = get_plan(_shape_key(c, s, prob.D, prob.seq_T), cfg)
+    plan = get_plan(_shape_key(c, s, prob.D, prob.seq_T, cfg), cfg)
     fac = plan.factor_buffer() if store_factor else None
     y, info = solve(c, d, s, u, cfg, D=prob.D, seq_T=prob.seq_T, factor=fac)
     gyt = torch.from_numpy(np.ascontiguousarray(gy, dt)).cuda()

@@ -72,3 +72,21 @@ def test_fused_pass_needs_every_system_within_one_cta():
     h = ctypes.c_void_p()
     assert B.lib.smnn_plan_create(ctypes.byref(d), ctypes.byref(h)) == B.SMNN_ERR_UNSUPPORTED
     assert not h.value
+
+
+@pytest.mark.parametrize("V,Q,R,ok", [(2, 1, 1, True), (2, 2, 1, True), (1, 2, 2, False), (2, 1, 2, False),
+                                      (4, 1, 1, False), (2, 3, 1, False), (0, 0, 2, True)])
+def test_coupled_descriptor_validation(V, Q, R, ok):
+    """V variables x (R+1) orders must fit a 4-wide block and Q <= 2; shapes outside the
+    instantiated ones (V(R+1) <= 4 with V = 1, or V = 2 with R = 1) are refused or reported
+    unsupported at plan creation, before any device call; 0 means 1 for both fields."""
+    from paper_2410_06074_b300 import binding as B
+    d = B.Desc(R, 0, 1, B.F32_REFINED, B.ALGO_CR, 2, 0, 0, 1.0, 1.0, 1.0, 0.0, 2, 2, 16, None, V, Q)
+    h = ctypes.c_void_p()
+    rc = B.lib.smnn_plan_create(ctypes.byref(d), ctypes.byref(h))
+    if ok:
+        assert rc in (B.SMNN_OK, B.SMNN_ERR_CUDA)   # CUDA: no device in this container
+        if h.value:
+            B.lib.smnn_plan_destroy(h)
+    else:
+        assert rc in (B.SMNN_ERR_INVALID_ARG, B.SMNN_ERR_UNSUPPORTED) and not h.value

@@ -398,3 +398,51 @@ def test_host_stream_steps_match_device_calls():
         ref = [y] + list(pk.gradients(c, d, s, u, y, g, cfg, factor=fac)[:4])
         for got, want in zip(o, ref):
             assert torch.equal(got, want.cpu())
+
+
+# ----------------------------------------------------------------------------- coupled systems
+
+@pytest.mark.parametrize("prec,tol", [("F64", 1e-9), ("F32_REFINED_DF", 1e-6), ("F32_REFINED", 1e-6)])
+@pytest.mark.parametrize("Q,T,algo,chunk", [(2, 1000, "AUTO", 0), (2, 777, "CR", 16), (2, 300, "CR_FUSED", 8),
+                                            (1, 400, "AUTO", 0)])
+def test_coupled_systems_match_oracle(Q, T, algo, chunk, prec, tol):
+    """V = 2 variables (R = 1: 4 unknowns per step) with Q governing equations per step
+    (Sec. 3.1, Eq. 4-7), forward and adjoint, against the oracle's coupled rows."""
+    import paper_2410_06074_b300 as pk
+    from smnn_workloads import random_coupled_problem
+    prob = random_coupled_problem(60 + Q, 3, 2, T, R=1, V=2, Q=Q, T_init=2, w=(0.9, 1.1, 1.2))
+    p = getattr(pk, prec)
+    gy = upstream_gradient(prob)[..., :4]
+    y, gc, gd, gs, gu, info, info2 = gpu_grad(prob, gy.astype(np.float64 if p == pk.F64 else np.float32), p,
+                                              algo=getattr(pk, "ALGO_" + algo), chunk=chunk)
+    r = rounded(prob, p)
+    g64 = gy.astype(np.float64 if p == pk.F64 else np.float32).astype(np.float64)
+    yo, gco, gdo, gso, guo, info_o = oracle_grad(r, g64)
+    assert (info == 0).all() and (info2 == 0).all() and (info_o == 0).all()
+    assert y.shape == (3, 2, T, 4)
+    assert rel_err_per_system(y, yo, prob).max() <= tol
+    for name, a, b in (("gc", gc, gco), ("gd", gd, gdo), ("gs", gs, gso), ("gu", gu, guo)):
+        assert rel_err(a, b) <= (1e-8 if p == pk.F64 else tol), (name, rel_err(a, b))
+
+
+def test_coupled_decoupled_equations_equal_independent_gpu_solves():
+    """On the GPU too: two variables whose equations do not couple them solve as two scalar
+    systems (FP64)."""
+    import paper_2410_06074_b300 as pk
+    from smnn_workloads import random_coupled_problem
+    R, T = 1, 500
+    prob = random_coupled_problem(70, 2, 1, T, R, V=2, Q=2)
+    c = prob.c.reshape(2, 1, T, 2, 2, R + 1).copy()
+    c[:, :, :, 0, 1, :] = 0.0
+    c[:, :, :, 1, 0, :] = 0.0
+    cp = Problem("decoupled", R, prob.R_init, 1, 2, 1, T, c.reshape(2, 1, T, -1), prob.d, prob.s,
+                 prob.u, V=2, Q=2)
+    y, info = gpu_solve(cp, pk.F64)
+    assert (info == 0).all()
+    ui = prob.u.reshape(2, 1, 1, 2, prob.R_init + 1)
+    for v in range(2):
+        one = Problem("one", R, prob.R_init, 1, 2, 1, T, np.ascontiguousarray(c[:, :, :, v, v, :]),
+                      np.ascontiguousarray(prob.d[..., v]), prob.s, np.ascontiguousarray(ui[:, :, :, v, :]))
+        yv, iv = gpu_solve(one, pk.F64)
+        assert (iv == 0).all()
+        np.testing.assert_allclose(y[..., v * (R + 1):(v + 1) * (R + 1)], yv, rtol=1e-10, atol=1e-12)
