@@ -336,23 +336,27 @@ def run_ours(args, ws, rank, local):
 
 def other_configs(args, ws, stream, flush):
     """Forward + adjoint time of the other large workloads (library defaults, saved factor,
-    L2 flushed between steps): config 4 (4096 ragged systems, T in [32, 65536], R = 2) and
-    config 3b (4 systems of 2^20 steps, R = 3) on SMNN_F32_REFINED_DF.  Secondary lines: their
-    accuracy against the oracle is covered by the full-size tests."""
+    L2 flushed between steps): config 4 (4096 ragged systems, T in [32, 65536], R = 2),
+    config 3b (4 systems of 2^20 steps, R = 3) and a coupled batch (4096 systems of 1024
+    steps with V = 2 variables, R = 1, Q = 2 equations per step) on SMNN_F32_REFINED_DF.
+    Secondary lines: their accuracy against the oracle is covered by the parity tests."""
     import torch
     import paper_2410_06074_b300 as pk
-    from smnn_workloads import config3b, config4
+    from smnn_workloads import config3b, config4, random_coupled_problem
     out = {}
-    for name, make in (("config4", config4), ("config3b", config3b)):
+    coupled = lambda: random_coupled_problem(0, 512, 8, 1024, R=1, V=2, Q=2)   # noqa: E731
+    for name, make in (("config4", config4), ("config3b", config3b), ("coupled_V2_Q2", coupled)):
         prob = make().cast(np.float32)
         seq_T = None if prob.seq_T is None else tuple(int(x) for x in prob.seq_T)
         dev = torch.device("cuda", torch.cuda.current_device())
         c, d, s, u = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (prob.c, prob.d, prob.s, prob.u))
-        gy = torch.from_numpy(upstream_gradient(prob).astype(np.float32)).to(dev)
-        cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=pk.F32_REFINED_DF)
-        plan = pk.get_plan(pk.api._shape_key(c, s, prob.D, seq_T), cfg)
+        nb = prob.V * (prob.R + 1)
+        gy = torch.from_numpy(np.ascontiguousarray(upstream_gradient(prob)[..., :nb]).astype(np.float32)).to(dev)
+        cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=pk.F32_REFINED_DF,
+                             V=prob.V, Q=prob.Q)
+        plan = pk.get_plan(pk.api._shape_key(c, s, prob.D, seq_T, cfg), cfg)
         wsb, fac = plan.workspace(dev), plan.factor_buffer(dev)
-        y = torch.empty_like(c)
+        y = pk.api._y_like(c, cfg)
         info, info_b = (torch.empty(plan.S, dtype=torch.int32, device=dev) for _ in range(2))
         g = [torch.empty_like(t) for t in (c, d, s, u)]
 

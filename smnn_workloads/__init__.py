@@ -288,5 +288,6 @@ def random_coupled_problem(seed: int = 0, B: int = 2, D: int = 2, T: int = 64, R
     d = rng.standard_normal((B, D, T, Q))
     s = rng.uniform(s_lo, s_hi, (B, T))
     u = rng.standard_normal((B, D, T_init, V * (R_init + 1)))
-    return Problem(f"coupled V={V} Q={Q}", R, R_init, T_init, B, D, T, c.reshape(B, D, T, Q * nb),
+    return Problem(f"coupled: B={B} D={D} T={T} V={V} R={R} Q={Q}", R, R_init, T_init, B, D, T,
+                   c.reshape(B, D, T, Q * nb),
                    d, s, u, w_gov=w[0], w_init=w[1], w_smooth=w[2], V=V, Q=Q)
