@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
     ap.add_argument("--chunk", type=int, default=0, help="level-0 chunk length (0: plan's table)")
     ap.add_argument("--no-other-configs", action="store_true",
-                    help="skip the secondary config-4 and config-3b timings")
+                    help="skip the secondary timings (config 4, config 3b, coupled batch, Lorenz training steps)")
     ap.add_argument("--algo", default="auto", choices=sorted(ALGOS),
                     help="reduction: auto (the plan's choice), seq, cr (a launch per level), "
                          "fused (a launch per solve pass)")
@@ -510,6 +510,64 @@ def accuracy(v, oracle_res, S):
             "gs": rel(v.gs, gso), "gu": rel(v.gu, guo)}
 
 
+# Sec. 5.2, Table 1: S-MNN time per optimisation step of the Lorenz discovery run on an
+# H100 80 GB, by (batch size, sequence length); context only (other hardware, and a whole
+# training script around the solver)
+LORENZ_PAPER_MS = {(512, 50): 7.4, (512, 5): 5.5, (512, 500): 32.2, (64, 50): 5.5, (4096, 50): 18.3}
+
+
+def lorenz_training_steps(args, ws, stream):
+    """Time per optimisation step of coefficient discovery on the Lorenz trajectory (the
+    Sec. 5.2 setting, synthetic RK4 data): B random windows of T samples drawn on the device,
+    degree-2 library, first-order layer solve (R = 1, FP32 + float-float refinement), MSE
+    loss, adjoint and Adam, the whole step captured in one CUDA graph and replayed.  The
+    eager (uncaptured) step is timed beside it.  No L2 flush: a training loop keeps its
+    trajectory (10,000 x 3 samples) and parameters resident."""
+    import torch
+    import paper_2410_06074_b300 as pk
+    from paper_2410_06074_b300 import binding as Bd
+    from paper_2410_06074_b300.discovery import Discovery, GraphedTrainStep, library_terms
+    from smnn_workloads import LORENZ, lorenz_trajectory
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tr = lorenz_trajectory()
+    traj = torch.from_numpy(tr).to(dev)
+    terms = library_terms(3, 2)
+    scale = Discovery.feature_scale(traj.cpu(), terms)
+    cfg = pk.SolveConfig(R_init=0, T_init=1, precision=pk.F32_REFINED_DF)
+    reps = max(50, 4 * args.steps)
+    out = {}
+    for (Bn, T), paper_ms in LORENZ_PAPER_MS.items():
+        row = {"batch": Bn, "T": T, "paper_ms_h100": paper_ms}
+        for graphed in (True, False):
+            torch.manual_seed(0)
+            model = Discovery(3, 2, LORENZ["dt"], scale=scale, cfg=cfg, device=dev)
+            n0 = Bd.launch_count()
+            st = GraphedTrainStep(model, traj, Bn, T, lr=1e-2, warmup=max(args.warmup, 3),
+                                  graphed=graphed)
+            per_step = (Bd.launch_count() - n0) // (max(args.warmup, 3) + (1 if graphed else 0))
+            for _ in range(3):
+                st.step()
+            torch.cuda.synchronize()
+            barrier(ws)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                st.step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = max_over_ranks(e0.elapsed_time(e1), ws) / reps
+            key = "graph" if graphed else "eager"
+            row[key + "_ms_per_step"] = ms
+            if graphed:
+                row["solver_launches_per_step"] = per_step
+                row["flagged_solves_last_step"] = int(st.bad)
+                row["loss_after"] = float(st.loss)
+                row["sequence_steps_per_s"] = ws * Bn * T / (ms / 1e3)
+            del st, model
+        out[f"B{Bn}_T{T}"] = row
+    return out
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
@@ -535,6 +593,7 @@ def main():
     r = results[head]
     e2e, roof, whole = e2e_and_roofline(prob, variants[head], r, ws, args, stream, flush)
     others = None if args.no_other_configs else other_configs(args, ws, stream, flush)
+    lorenz = None if args.no_other_configs else lorenz_training_steps(args, ws, stream)
     prec_txt = {"F32_REFINED_DF": "FP32 factor + float-float residual refinement",
                 "F32_REFINED": "FP32 factor + FP64 residual refinement"}[head]
     out = {
@@ -568,6 +627,8 @@ def main():
     }
     if others is not None:
         out["other_configs"] = others
+    if lorenz is not None:
+        out["lorenz_training_step"] = lorenz
     if cpu is not None:
         out["cpu_baseline"] = cpu
     if rank == 0:

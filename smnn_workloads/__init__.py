@@ -31,7 +31,8 @@ import numpy as np
 
 __all__ = ["Problem", "config1", "config2", "config2_slice", "config3", "config3b", "config4",
            "config5", "random_problem", "upstream_gradient", "mse_target", "CONFIGS",
-           "table5_odes", "table5_batch", "ODE_T", "ODE_H", "random_coupled_problem"]
+           "table5_odes", "table5_batch", "ODE_T", "ODE_H", "random_coupled_problem",
+           "LORENZ", "lorenz_trajectory", "lorenz_chunks"]
 
 
 @dataclass
@@ -291,3 +292,47 @@ def random_coupled_problem(seed: int = 0, B: int = 2, D: int = 2, T: int = 64, R
     return Problem(f"coupled: B={B} D={D} T={T} V={V} R={R} Q={Q}", R, R_init, T_init, B, D, T,
                    c.reshape(B, D, T, Q * nb),
                    d, s, u, w_gov=w[0], w_init=w[1], w_smooth=w[2], V=V, Q=Q)
+
+
+# ----------------------------------------------------------------------------- Lorenz data
+
+# Sec. 5.2: the standard Lorenz parameters, start (1, 1, 1), 10,000 samples 0.01 apart
+LORENZ = dict(sigma=10.0, rho=28.0, beta=8.0 / 3.0, x0=(1.0, 1.0, 1.0), n_steps=10000, dt=0.01)
+
+
+def lorenz_trajectory(n_steps: int = LORENZ["n_steps"], dt: float = LORENZ["dt"],
+                      x0=LORENZ["x0"], sigma: float = LORENZ["sigma"], rho: float = LORENZ["rho"],
+                      beta: float = LORENZ["beta"], substeps: int = 10) -> np.ndarray:
+    """The Lorenz trajectory of Sec. 5.2 as [n_steps, 3] float64 samples dt apart (row 0 = x0).
+
+    dx/dt = sigma (y - x), dy/dt = x (rho - z) - y, dz/dt = x y - beta z, integrated by the
+    classical fourth-order Runge-Kutta method with ``substeps`` equal sub-steps per sample
+    (a fixed-step stand-in for the adaptive integrator the paper names; deterministic, no
+    random numbers)."""
+    h = dt / substeps
+    x, y, z = (float(v) for v in x0)
+    out = np.empty((n_steps, 3))
+    out[0] = (x, y, z)
+
+    def f(x, y, z):
+        return sigma * (y - x), x * (rho - z) - y, x * y - beta * z
+
+    for i in range(1, n_steps):
+        for _ in range(substeps):
+            a1, b1, c1 = f(x, y, z)
+            a2, b2, c2 = f(x + 0.5 * h * a1, y + 0.5 * h * b1, z + 0.5 * h * c1)
+            a3, b3, c3 = f(x + 0.5 * h * a2, y + 0.5 * h * b2, z + 0.5 * h * c2)
+            a4, b4, c4 = f(x + h * a3, y + h * b3, z + h * c3)
+            x += h / 6.0 * (a1 + 2.0 * a2 + 2.0 * a3 + a4)
+            y += h / 6.0 * (b1 + 2.0 * b2 + 2.0 * b3 + b4)
+            z += h / 6.0 * (c1 + 2.0 * c2 + 2.0 * c3 + c4)
+        out[i] = (x, y, z)
+    return out
+
+
+def lorenz_chunks(traj: np.ndarray, B: int, T: int, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """B random windows of T consecutive samples of ``traj`` (App. B.2's batches): returns
+    (starts [B] int64, chunks [B, T, n]).  Start indices ~ U{0, ..., len(traj) - T}."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    starts = rng.integers(0, traj.shape[0] - T + 1, B).astype(np.int64)
+    return starts, traj[starts[:, None] + np.arange(T)[None, :]]
