@@ -51,6 +51,9 @@ extern "C" {
 
 /* Largest derivative order the kernels are compiled for (R+1 <= 4 unknowns/step). */
 #define SMNN_MAX_R 3
+/* Largest block n_b = V(R+1) and equation count Q of a coupled step (smnn_desc.V, .Q). */
+#define SMNN_MAX_NB 6
+#define SMNN_MAX_Q 3
 
 typedef enum {
   SMNN_OK = 0,
@@ -111,12 +114,13 @@ typedef struct smnn_desc {
   const int64_t* seq_T;   /* HOST pointer to B step counts (ragged), or NULL; read  */
                           /* only during smnn_plan_create                           */
   int32_t V;              /* variables per step (Sec. 3.1; 0 means 1): a step has   */
-                          /* n_b = V(R+1) unknowns, variable-major; V(R+1) <= 4     */
-  int32_t Q;              /* governing equations per step (0 means 1), 1..2; with V */
-                          /* and Q the per-step layouts become c [..][Q][V(R+1)],  */
-                          /* d [..][Q], u [..][T_init][V][R_init+1], y [..][V(R+1)] */
-                          /* (gradients likewise).  Built shapes: V = Q = 1 with    */
-                          /* R = 1..3, and V = 2, R = 1, Q = 1 or 2; other valid    */
+                          /* n_b = V(R+1) <= SMNN_MAX_NB unknowns, variable-major   */
+  int32_t Q;              /* governing equations per step (0 means 1), 1..MAX_Q;   */
+                          /* with V and Q the per-step layouts become              */
+                          /* c [..][Q][V(R+1)], d [..][Q], u [..][T_init][V][R_init+1], */
+                          /* y [..][V(R+1)] (gradients likewise).  Built shapes:   */
+                          /* V = Q = 1 with R = 1..3; V = 2, R = 1, Q = 1 or 2;    */
+                          /* V = 3, R = 1, Q = 3; V = 2, R = 2, Q = 2.  Other valid */
                           /* shapes return SMNN_ERR_UNSUPPORTED at plan creation.   */
 } smnn_desc;
 

@@ -35,7 +35,8 @@ class SolveConfig:
     factor_budget_bytes: int = 16 << 30   # store the factor for backward if it fits
     # coupled systems (Sec. 3.1): V variables and Q governing equations per step; c then holds
     # Q*V*(R+1) values per step (equation-major), d Q, u V*(R_init+1) per initial step, and
-    # y V*(R+1) (variable-major); V*(R+1) <= 4, Q <= 2
+    # y V*(R+1) (variable-major); built: V = Q = 1; V = 2, R = 1, Q <= 2; V = 3, R = 1, Q = 3;
+    # V = 2, R = 2, Q = 2
     V: int = 1
     Q: int = 1
 

@@ -281,7 +281,7 @@ __device__ __forceinline__ void dev_elim0(const LevelTables& lt, const LevelBufs
 #define SMNN_FACTOR_MIN_BLOCKS 4   // factor pass: 4 CTAs per SM (128 registers) beat 3 (168)
 #endif
 template <class Tr, int NB, bool kFactor, bool kTop, int R1 = NB, int Q = 1>
-__global__ void __launch_bounds__(kThreads, kFactor ? SMNN_FACTOR_MIN_BLOCKS : 4) k_elim0(LevelTables lt, LevelBufs<Tr, NB> lb, Problem0 p,
+__global__ void __launch_bounds__(kThreads, NB <= 4 ? (kFactor ? SMNN_FACTOR_MIN_BLOCKS : 4) : 1) k_elim0(LevelTables lt, LevelBufs<Tr, NB> lb, Problem0 p,
                                                     L0In<Tr> in, const Tr* rhs, int32_t* info) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
@@ -425,7 +425,7 @@ __device__ __forceinline__ void dev_backsub0(const LevelTables& lt, const LevelB
 }
 
 template <class Tr, int NB, int kMode, int R1 = NB, int Q = 1>
-__global__ void __launch_bounds__(kThreads, 4) k_backsub0(LevelTables lt, LevelBufs<Tr, NB> lb,
+__global__ void __launch_bounds__(kThreads, NB <= 4 ? 4 : 1) k_backsub0(LevelTables lt, LevelBufs<Tr, NB> lb,
                                                        Problem0 p, L0In<Tr> in, Level0Out<Tr> o,
                                                        const int32_t* info, const int32_t* skip) {
   const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -762,7 +762,7 @@ __global__ void __launch_bounds__(kThreads) k_elim0_res(LevelTables lt, LevelBuf
 // launch.  The upper levels' few, short chunks run while the CTA's other warps wait, and
 // other CTAs of the SM, in other phases, keep its pipes and memory busy.
 template <class Tr, int NB, int kSrc, class N, int kMode, int R1 = NB, int Q = 1>
-__global__ void __launch_bounds__(kThreads, 3) k_pass(const __grid_constant__ FusedLevels<Tr, NB> fl,
+__global__ void __launch_bounds__(kThreads, NB <= 4 ? 3 : 1) k_pass(const __grid_constant__ FusedLevels<Tr, NB> fl,
                                                       Problem0 p, L0In<Tr> in, const Tr* rhs,
                                                       const float* x_hi, const float* x_lo,
                                                       Level0Out<Tr> o, int32_t* info,
@@ -1769,20 +1769,23 @@ smnn_status assemble_t(const smnn_plan_s* pl, const void* c, const void* d, cons
   return SMNN_OK;
 }
 
-// Runs fn<Tr, NB>(...) for the plan's precision and block size.
-// Instantiated step shapes (n_b = V (R+1), R+1, Q): one variable with R = 1..3 and one
-// governing equation; and V = 2 variables of R = 1 with one or two equations per step.
-#define SMNN_SHAPE(pl, NB_, R1_, Q_, fn, ...)                                         \
+// The instantiated step shapes (n_b = V (R+1), R+1, Q): one variable with R = 1..3 and one
+// governing equation; V = 2 variables of R = 1 with one or two equations per step; V = 3
+// variables of R = 1 with three equations (a first-order system in three states); V = 2
+// variables of R = 2 with two equations (two coupled second-order equations).
+#define SMNN_SHAPES(X, ...)                                                           \
+  X(2, 2, 1, __VA_ARGS__) X(3, 3, 1, __VA_ARGS__) X(4, 4, 1, __VA_ARGS__)             \
+  X(4, 2, 1, __VA_ARGS__) X(4, 2, 2, __VA_ARGS__) X(6, 2, 3, __VA_ARGS__)             \
+  X(6, 3, 2, __VA_ARGS__)
+#define SMNN_SHAPE_IS(NB_, R1_, Q_, pl) ((pl)->NB == NB_ && (pl)->R1 == R1_ && (pl)->NQ == Q_) ||
+// Runs fn<Tr, NB, R1, Q>(...) for the plan's precision and step shape.
+#define SMNN_SHAPE_CASE(NB_, R1_, Q_, pl, fn, ...)                                    \
   if ((pl)->NB == NB_ && (pl)->R1 == R1_ && (pl)->NQ == Q_)                           \
     return (pl)->desc.precision == SMNN_F64 ? fn<double, NB_, R1_, Q_>(__VA_ARGS__)   \
-                                            : fn<float, NB_, R1_, Q_>(__VA_ARGS__)
+                                            : fn<float, NB_, R1_, Q_>(__VA_ARGS__);
 #define SMNN_DISPATCH(pl, fn, ...)                                                    \
   do {                                                                                \
-    SMNN_SHAPE(pl, 2, 2, 1, fn, __VA_ARGS__);                                         \
-    SMNN_SHAPE(pl, 3, 3, 1, fn, __VA_ARGS__);                                         \
-    SMNN_SHAPE(pl, 4, 4, 1, fn, __VA_ARGS__);                                         \
-    SMNN_SHAPE(pl, 4, 2, 1, fn, __VA_ARGS__);                                         \
-    SMNN_SHAPE(pl, 4, 2, 2, fn, __VA_ARGS__);                                         \
+    SMNN_SHAPES(SMNN_SHAPE_CASE, pl, fn, __VA_ARGS__)                                 \
     return SMNN_ERR_UNSUPPORTED;                                                      \
   } while (0)
 
@@ -1812,7 +1815,7 @@ smnn_status plan_init(const smnn_desc* desc, smnn_plan_s* pl) {
   if (!desc) return SMNN_ERR_INVALID_ARG;
   const smnn_desc& d = *desc;
   if (d.R < 1 || d.R > SMNN_MAX_R || d.R_init < 0 || d.R_init > d.R || d.T_init < 1) return SMNN_ERR_INVALID_ARG;
-  if (d.V < 0 || d.Q < 0 || d.Q > 2 || (d.V > 1 ? d.V : 1) * (d.R + 1) > SMNN_MAX_R + 1)
+  if (d.V < 0 || d.Q < 0 || d.Q > SMNN_MAX_Q || (d.V > 1 ? d.V : 1) * (d.R + 1) > SMNN_MAX_NB)
     return SMNN_ERR_INVALID_ARG;
   if (d.precision < SMNN_F32_REFINED || d.precision > SMNN_F32_REFINED_DF) return SMNN_ERR_INVALID_ARG;
   if (d.algo < SMNN_ALGO_AUTO || d.algo > SMNN_ALGO_CR_FUSED) return SMNN_ERR_INVALID_ARG;
@@ -1832,9 +1835,8 @@ smnn_status plan_init(const smnn_desc* desc, smnn_plan_s* pl) {
   pl->desc.Q = pl->NQ;
   pl->R1 = d.R + 1;
   pl->NB = pl->V * pl->R1;
-  // the instantiated step shapes (SMNN_DISPATCH): one variable and one equation, or
-  // V = 2 variables of R = 1 with one or two equations
-  const bool shape_ok = (pl->V == 1 && pl->NQ == 1) || (pl->V == 2 && pl->R1 == 2);
+  // only the instantiated step shapes (SMNN_SHAPES)
+  const bool shape_ok = SMNN_SHAPES(SMNN_SHAPE_IS, pl) false;
   if (!shape_ok) return SMNN_ERR_UNSUPPORTED;
   pl->esz = d.precision == SMNN_F64 ? 8 : 4;
   pl->B = d.num_seq;

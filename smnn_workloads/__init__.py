@@ -272,12 +272,20 @@ def table5_batch(R: int, R_init: int, T: int = ODE_T, h: float = ODE_H) -> tuple
 
 def random_coupled_problem(seed: int = 0, B: int = 2, D: int = 2, T: int = 64, R: int = 1,
                            V: int = 2, Q: int = 2, R_init: int | None = None, T_init: int = 1,
-                           s_lo: float = 0.01, s_hi: float = 0.1, w=(1.0, 1.0, 1.0)) -> Problem:
+                           s_lo: float = 0.01, s_hi: float = 0.1, w=(1.0, 1.0, 1.0),
+                           lead_cross: float | None = None) -> Problem:
     """Uniform batch of coupled systems (Sec. 3.1 with V variables and Q governing equations
     per step): c [B, D, T, Q*V*(R+1)] ~ N(0,1) with the coefficient of each equation's own
     variable's highest derivative (variable q mod V) set to 1 + |N(0,1)|, d [B, D, T, Q] ~ N(0,1),
     s ~ U[s_lo, s_hi] per (sequence, step), u [B, D, T_init, V*(R_init+1)] ~ N(0,1).
-    Draw order: c, d, s, u."""
+    Draw order: c, d, s, u.
+
+    ``lead_cross``: if set, an equation's coefficients on the OTHER variables' highest
+    derivatives become lead_cross * tanh(N) (same draws), so that with
+    lead_cross <= 1 / (V - 1) the highest derivatives are pinned by a diagonally dominant
+    block; left unset, those coefficients are plain N(0,1) and a step's block can come
+    arbitrarily close to singular (the highest derivatives then rest on smoothness rows of
+    weight s^{2R} alone)."""
     if R_init is None:
         R_init = max(R - 1, 0)
     nb = V * (R + 1)
@@ -286,6 +294,11 @@ def random_coupled_problem(seed: int = 0, B: int = 2, D: int = 2, T: int = 64, R
     for q in range(Q):
         k = (q % V) * (R + 1) + R
         c[..., q, k] = 1.0 + np.abs(c[..., q, k])
+        if lead_cross is not None:
+            for v in range(V):
+                if v != q % V:
+                    kv = v * (R + 1) + R
+                    c[..., q, kv] = lead_cross * np.tanh(c[..., q, kv])
     d = rng.standard_normal((B, D, T, Q))
     s = rng.uniform(s_lo, s_hi, (B, T))
     u = rng.standard_normal((B, D, T_init, V * (R_init + 1)))

@@ -425,6 +425,34 @@ def test_coupled_systems_match_oracle(Q, T, algo, chunk, prec, tol):
         assert rel_err(a, b) <= (1e-8 if p == pk.F64 else tol), (name, rel_err(a, b))
 
 
+@pytest.mark.parametrize("prec,tol", [("F64", 1e-9), ("F32_REFINED_DF", 1e-6)])
+@pytest.mark.parametrize("V,R,Q", [(3, 1, 3), (2, 2, 2)])
+@pytest.mark.parametrize("T,algo,chunk", [(1000, "AUTO", 0), (333, "CR", 8), (200, "CR_FUSED", 8),
+                                          (150, "SEQ", 0)])
+def test_coupled_six_wide_blocks_match_oracle(V, R, Q, T, algo, chunk, prec, tol):
+    """Steps of n_b = V(R+1) = 6 unknowns: three first-order variables with three equations,
+    and two second-order variables with two equations (Sec. 3.1), forward and adjoint,
+    against the oracle's coupled rows.  The highest-derivative block of each step is made
+    diagonally dominant (lead_cross), so that the FP32 factor's refinement converges."""
+    import paper_2410_06074_b300 as pk
+    from smnn_workloads import random_coupled_problem
+    prob = random_coupled_problem(80 + V, 3, 2, T, R=R, V=V, Q=Q, T_init=2, w=(1.1, 0.9, 1.05),
+                                  lead_cross=0.5 / (V - 1))
+    p = getattr(pk, prec)
+    nb = V * (R + 1)
+    gy = upstream_gradient(prob)[..., :nb]
+    wdt = np.float64 if p == pk.F64 else np.float32
+    y, gc, gd, gs, gu, info, info2 = gpu_grad(prob, gy.astype(wdt), p,
+                                              algo=getattr(pk, "ALGO_" + algo), chunk=chunk)
+    r = rounded(prob, p)
+    yo, gco, gdo, gso, guo, info_o = oracle_grad(r, gy.astype(wdt).astype(np.float64))
+    assert (info == 0).all() and (info2 == 0).all() and (info_o == 0).all()
+    assert y.shape == (3, 2, T, nb)
+    assert rel_err_per_system(y, yo, prob).max() <= tol
+    for name, a, b in (("gc", gc, gco), ("gd", gd, gdo), ("gs", gs, gso), ("gu", gu, guo)):
+        assert rel_err(a, b) <= (1e-8 if p == pk.F64 else tol), (name, rel_err(a, b))
+
+
 def test_coupled_decoupled_equations_equal_independent_gpu_solves():
     """On the GPU too: two variables whose equations do not couple them solve as two scalar
     systems (FP64)."""
