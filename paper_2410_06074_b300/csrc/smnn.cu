@@ -745,8 +745,11 @@ __device__ __forceinline__ void dev_elim0_res(const LevelTables& lt, const Level
   if (top) solve_top<float, NB>(lb.out, g, lb.xsep + g * NB);
 }
 
+#ifndef SMNN_RES_MIN_BLOCKS
+#define SMNN_RES_MIN_BLOCKS 4   // refinement sweep, n_b <= 3: 4 CTAs per SM (128 registers, no spills)
+#endif
 template <class N, int NB, bool kTop, int R1 = NB, int Q = 1>
-__global__ void __launch_bounds__(kThreads) k_elim0_res(LevelTables lt, LevelBufs<float, NB> lb,
+__global__ void __launch_bounds__(kThreads, NB <= 3 ? SMNN_RES_MIN_BLOCKS : 1) k_elim0_res(LevelTables lt, LevelBufs<float, NB> lb,
                                                         Problem0 p, L0In<float> in, const float* x_hi,
                                                         const float* x_lo, const float* rhs,
                                                         const int32_t* skip) {
