@@ -428,7 +428,11 @@ template <class Tr, int NB, int kMode, int R1 = NB, int Q = 1>
 __global__ void __launch_bounds__(kThreads, NB <= 4 ? 4 : 1) k_backsub0(LevelTables lt, LevelBufs<Tr, NB> lb,
                                                        Problem0 p, L0In<Tr> in, Level0Out<Tr> o,
                                                        const int32_t* info, const int32_t* skip) {
-  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  // CTAs take the chunks in the reverse of the elimination's order: the chunks the
+  // elimination launch touched last (whose factor records and z are most likely still in
+  // L2) are substituted first, and the next sweep's elimination, in forward order, again
+  // starts where this launch ended
+  const int64_t g = (gridDim.x - 1 - blockIdx.x) * int64_t(blockDim.x) + threadIdx.x;
   if (g >= lt.G) return;
   dev_backsub0<Tr, NB, kMode, true, R1, Q>(lt, lb, p, in, o, info, skip, g);
 }
