@@ -393,8 +393,8 @@ def e2e_and_roofline(prob, v, res, ws, args, stream, flush):
     d2h = sum(t.numel() * t.element_size() for t in host_out)
     # the public API's streaming host path: each step copies its inputs in and its results out;
     # step k+1's copy-in and step k-1's copy-out run on their own streams while step k
-    # computes (HostStream).  Every step's working set (inputs 120 MB, factor 300 MB, outputs)
-    # exceeds L2, so no flush is added between the steps.
+    # computes (HostStream, three rotating device buffer sets).  Every step's working set
+    # (inputs 120 MB, factor 300 MB, outputs) exceeds L2, so no flush is added between steps.
     pipe = pk.HostStream((prob.R, prob.B, prob.D, prob.T), v.cfg, device=v.c.device, dtype=v.c.dtype)
 
     def run_steps(n):

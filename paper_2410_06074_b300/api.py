@@ -212,9 +212,12 @@ class HostPipeline:
 class HostStream:
     """Forward + adjoint of successive uniform batches held in pinned host memory, with the
     transfers of neighbouring steps overlapped: step k's host->device copy (copy-in stream)
-    runs while step k-1 computes (compute stream), and step k-1's device->host copy (copy-out
-    stream) while step k computes.  Two device buffer sets alternate between the steps; events
-    order each set's reuse after the reads of the step that used it before.
+    runs while step k-1 computes (compute stream) and step k-2's device->host copy (copy-out
+    stream) drains.  ``n_sets`` device buffer sets rotate between the steps; events order each
+    set's reuse after the copy-out of the step that used it before.  With two sets, step k's
+    copy-in waits for step k-2's copy-out, so a pair of steps costs copy-in + compute +
+    copy-out; with three, the three engines run side by side and a step costs the largest of
+    the three.
 
     submit(c, d, s, u, gy, y, gc, gd, gs, gu): host tensors of one step (layouts of ``solve``
     and ``gradients``; outputs preallocated, pinned).  Returns (info, info_b, done): device
@@ -223,13 +226,15 @@ class HostStream:
     submitted step."""
 
     def __init__(self, shape_key, cfg: SolveConfig = SolveConfig(), device="cuda",
-                 dtype=torch.float32):
+                 dtype=torch.float32, n_sets: int = 3):
         R, B, D, T = shape_key
+        if n_sets < 1:
+            raise ValueError("n_sets >= 1")
         self.plan = get_plan((R, B, D, T), cfg)
         self.s_in, self.s_cmp, self.s_out = (torch.cuda.Stream(device=device) for _ in range(3))
         self.k = 0
         self.sets = []
-        for _ in range(2):
+        for _ in range(n_sets):
             f = lambda *sh: torch.empty(sh, dtype=dtype, device=device)
             b = dict(c=f(B, D, T, R + 1), d=f(B, D, T), s=f(B, T),
                      u=f(B, D, cfg.T_init, cfg.R_init + 1), gy=f(B, D, T, R + 1))
@@ -243,7 +248,7 @@ class HostStream:
         self.fac = self.plan.factor_buffer(device)
 
     def submit(self, c, d, s, u, gy, y, gc, gd, gs, gu):
-        b = self.sets[self.k % 2]
+        b = self.sets[self.k % len(self.sets)]
         self.k += 1
         main = torch.cuda.current_stream()
         self.s_in.wait_stream(main)

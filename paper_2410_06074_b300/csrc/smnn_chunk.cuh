@@ -180,6 +180,13 @@ SMNN_HD void trsm_l(const Tr (&l)[NB][NB], const Tr (&inv)[NB], const Tr (&b)[NB
 // chunks g) move consecutive records, each with RLH*sizeof(Tr)/16 vector accesses.  z holds
 // the forward-sweep vectors z_t of the current right-hand side, element e at
 // [(e*L + j)*G + g] (scalar, coalesced: a 16-byte record would add a third to its bytes).
+// Steps ahead at which the replay sweep warms L2 with the stored factor (0: no prefetch).
+// The back substitution, HBM-bound at ~84% of the copy rate, gained nothing from it.
+#ifndef SMNN_PREFETCH_STEPS
+#define SMNN_PREFETCH_STEPS 4
+#endif
+constexpr int kPrefetchSteps = SMNN_PREFETCH_STEPS;
+
 template <class Tr> struct Vec16;
 template <> struct Vec16<float> { using T = float4; };
 template <> struct Vec16<double> { using T = double2; };
@@ -229,6 +236,14 @@ struct FactorView {
   // kRO: no thread writes lh or z during the kernel, so the loads may take the read-only path
   // (one level per launch); the fused launches write a level's factor and z earlier in the
   // same kernel and read them with plain loads.
+  // Warm L2 with step j's record ahead of the sweep reaching it: a sweep walks its chunk one
+  // dependent step at a time, so a one-step-ahead load alone leaves most of the HBM latency
+  // exposed.
+  SMNN_HD void prefetch(int j, int64_t g) const {
+#if defined(__CUDA_ARCH__)
+    asm volatile("prefetch.L2 [%0];" ::"l"(lh + rec(j, g)));
+#endif
+  }
   template <bool kRO>
   SMNN_HD void load_raw(int j, int64_t g, Raw& r, bool with_h, bool with_z) const {
     const Vec* src = reinterpret_cast<const Vec*>(lh + rec(j, g));
@@ -559,6 +574,7 @@ SMNN_HD int64_t elim_chunk(Src& src, int64_t first, int64_t last, bool has_left,
     if (more) {
       fac.template load_raw<kRO>(j + 1, g, nxt, has_left, false);
       enxt = src.load_e(t + 1);
+      if (kPrefetchSteps > 0 && t + kPrefetchSteps < last) fac.prefetch(j + kPrefetchSteps, g);
     }
     if (kFactor) {
 #pragma unroll

@@ -370,14 +370,16 @@ def test_host_pipeline_matches_device_calls(n_parts):
         assert float((got.double() - want).norm() / want.norm()) <= 1e-6
 
 
-def test_host_stream_steps_match_device_calls():
-    """HostStream (three streams, two device buffer sets, the steps' transfers overlapped)
-    returns for every step exactly what the device calls return for that step's inputs."""
+@pytest.mark.parametrize("n_sets", [2, 3])
+def test_host_stream_steps_match_device_calls(n_sets):
+    """HostStream (three streams, n_sets rotating device buffer sets, the steps' transfers
+    overlapped) returns for every step exactly what the device calls return for that step's
+    inputs."""
     import torch
     import paper_2410_06074_b300 as pk
     cfg = pk.SolveConfig(R_init=1, T_init=1, precision=pk.F32_REFINED_DF)
     steps = []
-    for seed in (41, 42, 43):
+    for seed in (41, 42, 43, 44):
         prob = random_problem(seed, 6, 2, 257, 2).cast(np.float32)
         gy = upstream_gradient(prob, seed).astype(np.float32)
         host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -385,11 +387,11 @@ def test_host_stream_steps_match_device_calls():
         outs = [torch.empty(t.shape, dtype=t.dtype).pin_memory()
                 for t in (host[0], host[0], host[1], host[2], host[3])]
         steps.append((host, outs))
-    hs = pk.HostStream((2, 6, 2, 257), cfg)
+    hs = pk.HostStream((2, 6, 2, 257), cfg, n_sets=n_sets)
     flags = [hs.submit(*h, *o) for h, o in steps]
     hs.wait()
     torch.cuda.synchronize()
-    for info, info_b, _ in flags[-2:]:   # a set's flags are reused two steps later
+    for info, info_b, _ in flags[-n_sets:]:   # a set's flags are reused n_sets steps later
         assert (info.cpu() == 0).all() and (info_b.cpu() == 0).all()
     fac = pk.get_plan((2, 6, 2, 257), cfg).factor_buffer()   # the saved-factor path, as HostStream
     for h, o in steps:
