@@ -258,6 +258,12 @@ class Variant:
         self.forward()
         self.backward()
 
+    def graph(self):
+        """The same step recorded once by smnn_graph_create on this variant's buffers."""
+        return self.plan.graph(self.c, self.d, self.s, self.u, self.y, self.info, self.work,
+                               factor=self.factor, gy=self.gy, gc=self.gc, gd=self.gd, gs=self.gs,
+                               gu=self.gu, info_b=self.info_b)
+
 
 def timed(fn, steps, stream, flush):
     """Sum of per-step CUDA-event durations; a 256 MiB write flushes L2 between steps."""
@@ -326,9 +332,16 @@ def run_ours(args, ws, rank, local):
         prof = Bd.profile_read()
         ms = max_over_ranks(ms, ws) / args.steps
         fwd_ms = max_over_ranks(timed(v.forward, args.steps, stream, flush), ws) / args.steps
+        # the same step replayed from the library's own CUDA graph (smnn_graph_create)
+        gph = v.graph()
+        for _ in range(2):
+            gph.launch()
+        graph_ms = max_over_ranks(timed(gph.launch, args.steps, stream, flush), ws) / args.steps
+        gph.close()
         assert int((v.info != 0).sum()) == 0 and int((v.info_b != 0).sum()) == 0, f"{name}: solver failures"
         results[name] = {"ms_per_step": ms, "value": ws * steps_per_pass / (ms / 1e3),
                          "fwd_ms_per_step": fwd_ms, "fwd_value": ws * steps_per_pass / (fwd_ms / 1e3),
+                         "graph_ms_per_step": graph_ms,
                          "gpu_launches": launches, "clocks": clk.summary(), "profile": prof,
                          "ms_per_step_profiled": max_over_ranks(ms_prof, ws) / args.steps}
     return prob, p32, variants, results, stream, flush, dev
@@ -620,7 +633,7 @@ def main():
         "roofline": roof,
         "whole_step_hbm": whole,
         "variants": {n: {k: x[k] for k in ("value", "ms_per_step", "fwd_value", "fwd_ms_per_step",
-                                           "ms_per_step_profiled")}
+                                           "ms_per_step_profiled", "graph_ms_per_step")}
                      for n, x in results.items()},
         "kernels": {k: {"launches": x[0], "total_ms": x[1]} for k, x in sorted(r["profile"].items())},
         "kernels_note": "per-launch CUDA events on the launching stream over a second timed run "

@@ -201,6 +201,27 @@ smnn_status smnn_backward(smnn_plan plan, const void* c, const void* d, const vo
                           void* gc, void* gd, void* gs, void* gu, double* gw, int32_t* info,
                           void* workspace, void* stream);
 
+/* A captured step: smnn_factor_solve on (c, d, s, u) into (y, factor, info) and, when gy
+ * is not NULL, smnn_backward on dl/dy = gy into (gc, gd, gs, gu, gw, info_b), recorded once
+ * into a CUDA graph on fixed buffers and replayed by smnn_graph_launch as one launch in place
+ * of the step's ~40 kernel launches (Sec. 6 names launch overhead as what dominates batches
+ * of small systems).  Arguments keep their meaning, layout, alignment and NULL rules from
+ * smnn_factor_solve and smnn_backward; the buffers must stay allocated at the same
+ * addresses while the graph exists, and new inputs are written into them between launches.
+ * The capture runs on a private stream of the plan's device in thread-local capture mode
+ * and executes nothing; the plan must outlive the graph.  The profiler does not time graph
+ * launches; smnn_launch_count grows by the graph's kernel count at every launch.
+ * On failure *graph is NULL and nothing is left allocated. */
+typedef struct smnn_graph_s* smnn_graph;
+smnn_status smnn_graph_create(smnn_plan plan, const void* c, const void* d, const void* s,
+                              const void* u, void* y, void* factor, int32_t* info,
+                              const void* gy, void* gc, void* gd, void* gs, void* gu,
+                              double* gw, int32_t* info_b, void* workspace, smnn_graph* graph);
+/* Replays the step on `stream` (stream-ordered, asynchronous, on the plan's device). */
+smnn_status smnn_graph_launch(smnn_graph graph, void* stream);
+/* Frees the graph (NULL is a no-op); launches already issued are not affected. */
+smnn_status smnn_graph_destroy(smnn_graph graph);
+
 /* Per-kernel timing of this library's own launches, for benchmarks.  While enabled
  * (enable != 0), every kernel launch is bracketed by two CUDA events recorded on the
  * launch's stream; up to 65536 launches are kept, later ones are counted but not timed.

@@ -69,6 +69,9 @@ SYMBOLS = {
     "smnn_profile_read": (ctypes.c_int, [ctypes.POINTER(KernelTime), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
     "smnn_factor_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(Desc)] + [_VP] * 7),
+    "smnn_graph_create": (ctypes.c_int, [_VP] * 16 + [ctypes.POINTER(_VP)]),
+    "smnn_graph_launch": (ctypes.c_int, [_VP, _VP]),
+    "smnn_graph_destroy": (ctypes.c_int, [_VP]),
 }
 
 
@@ -108,6 +111,31 @@ def profile_read() -> dict:
     _check(lib.smnn_profile_read(buf, 64, ctypes.byref(n)), "smnn_profile_read")
     return {buf[k].name.decode(): (int(buf[k].launches), float(buf[k].total_ms))
             for k in range(min(n.value, 64))}
+
+
+class StepGraph:
+    """A step recorded by smnn_graph_create; launch(stream) replays it (one graph launch)."""
+
+    def __init__(self, plan, bufs):
+        self.plan, self.bufs = plan, bufs      # both must outlive the graph
+        h = ctypes.c_void_p()
+        _check(lib.smnn_graph_create(plan.handle, *[_p(t) for t in bufs], ctypes.byref(h)),
+               "smnn_graph_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(lib.smnn_graph_launch(self.handle, _stream(stream)), "smnn_graph_launch")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib.smnn_graph_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _check(status: int, where: str):
@@ -228,3 +256,10 @@ class Plan:
         _check(lib.smnn_backward(self.handle, _p(c), _p(d), _p(s), _p(u), _p(y), _p(factor),
                                  _p(gy), _p(gc), _p(gd), _p(gs), _p(gu), _p(gw), _p(info),
                                  _p(workspace), _stream(stream)), "smnn_backward")
+
+    def graph(self, c, d, s, u, y, info, workspace, factor=None, gy=None, gc=None, gd=None,
+              gs=None, gu=None, info_b=None, gw=None) -> "StepGraph":
+        """Record factor_solve (and, with gy, backward) on these buffers as one CUDA graph
+        (smnn_graph_create); the graph keeps references to the tensors."""
+        self._args_ok(c, d, s, u, y, info, workspace, factor, gy, gc, gd, gs, gu, info_b, gw)
+        return StepGraph(self, (c, d, s, u, y, factor, info, gy, gc, gd, gs, gu, gw, info_b, workspace))

@@ -44,13 +44,24 @@ struct Profiler {
 };
 Profiler g_prof;
 
+// Set while smnn_graph_create records a step on this thread: launches are then counted into
+// t_captured (the graph's kernel count) instead of g_launches, and not timed.
+thread_local bool t_capturing = false;
+thread_local uint64_t t_captured = 0;
+inline void count_launch() {
+  if (t_capturing) ++t_captured;
+  else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 inline void prof_begin(const char* name, cudaStream_t st) {
+  if (t_capturing) return;
   if (g_prof.on && g_prof.n < int(g_prof.rec.size())) {
     g_prof.rec[g_prof.n].name = name;
     cudaEventRecord(g_prof.rec[g_prof.n].e0, st);
   }
 }
 inline void prof_end(cudaStream_t st) {
+  if (t_capturing) return;
   if (g_prof.on && g_prof.n < int(g_prof.rec.size())) cudaEventRecord(g_prof.rec[g_prof.n++].e1, st);
 }
 
@@ -1394,7 +1405,7 @@ inline unsigned nblocks(int64_t n) { return unsigned((n + kThreads - 1) / kThrea
       prof_begin(label, st);                                                  \
       kern<<<nblocks(n), kThreads, 0, st>>>(__VA_ARGS__);                     \
       prof_end(st);                                                           \
-      g_launches.fetch_add(1, std::memory_order_relaxed);                     \
+      count_launch();                                                         \
       if (cudaGetLastError() != cudaSuccess) return SMNN_ERR_CUDA;            \
     }                                                                         \
   } while (0)
@@ -1590,7 +1601,7 @@ smnn_status tile_copy(const smnn_plan_s* pl, const Ts* src, const float* src_lo,
   prof_begin("k_tile", st);
   k_tile<Tr, Ts, K, kIn><<<blocks, kTileThreads, shm, st>>>(tables_of(L0), src, src_lo, dst, dst_lo);
   prof_end(st);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+  count_launch();
   return cudaGetLastError() == cudaSuccess ? SMNN_OK : SMNN_ERR_CUDA;
 }
 
@@ -1689,7 +1700,7 @@ smnn_status gradients_out(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
     prof_begin("k_reduce_w", st);
     k_reduce_w<<<1, 256, 0, st>>>(b.pw, L0.G, gw);
     prof_end(st);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    count_launch();
     if (cudaGetLastError() != cudaSuccess) return SMNN_ERR_CUDA;
   } else {
     SMNN_LAUNCH((k_grad<Tr, N, NB, false, R1, Q>), L0.G, st, tables_of(L0), p, in, yh, yl, gh, gl, info,
@@ -1760,6 +1771,16 @@ smnn_status backward_t(const smnn_plan_s* pl, const void* c, const void* d, cons
     SMNN_TRY((gather_inputs<Tr, NB, R1, Q>(pl, p, b, static_cast<const Tr*>(y), b.x, nullptr, false, st)));
     return gradients_out<Tr, double, NB, R1, Q>(pl, p, b, b.x, nullptr, b.g, nullptr, info, gco, gdo, gso, guo, gwo, st);
   }
+}
+
+// Forward then (with gy) backward of one step, as smnn_graph_create records it.
+template <class Tr, int NB, int R1 = NB, int Q = 1>
+smnn_status step_t(const smnn_plan_s* pl, const void* c, const void* d, const void* s, const void* u,
+                   void* y, void* factor, int32_t* info, const void* gy, void* gc, void* gd, void* gs,
+                   void* gu, void* gw, int32_t* info_b, void* ws, cudaStream_t st) {
+  SMNN_TRY((factor_solve_t<Tr, NB, R1, Q>(pl, c, d, s, u, y, factor, info, ws, st)));
+  if (!gy) return SMNN_OK;
+  return backward_t<Tr, NB, R1, Q>(pl, c, d, s, u, y, factor, gy, gc, gd, gs, gu, gw, info_b, ws, st);
 }
 
 template <class Tr, int NB, int R1 = NB, int Q = 1>
@@ -1962,6 +1983,93 @@ smnn_status smnn_backward(smnn_plan plan, const void* c, const void* d, const vo
   if (gw && (reinterpret_cast<uintptr_t>(gw) & 7)) return SMNN_ERR_INVALID_ARG;
   SMNN_DISPATCH(plan, backward_t, plan, c, d, s, u, y, factor, gy, gc, gd, gs, gu, gw, info,
                 workspace, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+struct smnn_graph_s {
+  cudaGraphExec_t exec = nullptr;
+  int device = 0;
+  uint64_t kernels = 0;   // kernel nodes recorded (added to the launch counter per launch)
+};
+
+namespace {
+smnn_status record_step(smnn_plan plan, const void* c, const void* d, const void* s, const void* u,
+                        void* y, void* factor, int32_t* info, const void* gy, void* gc, void* gd,
+                        void* gs, void* gu, double* gw, int32_t* info_b, void* workspace,
+                        cudaStream_t st) {
+  SMNN_DISPATCH(plan, step_t, plan, c, d, s, u, y, factor, info, gy, gc, gd, gs, gu, gw, info_b,
+                workspace, st);
+}
+}  // namespace
+
+extern "C" {
+
+smnn_status smnn_graph_create(smnn_plan plan, const void* c, const void* d, const void* s,
+                              const void* u, void* y, void* factor, int32_t* info, const void* gy,
+                              void* gc, void* gd, void* gs, void* gu, double* gw, int32_t* info_b,
+                              void* workspace, smnn_graph* graph) {
+  if (!graph) return SMNN_ERR_INVALID_ARG;
+  *graph = nullptr;
+  if (!plan || !c || !d || !s || !u || !y || !info) return SMNN_ERR_INVALID_ARG;
+  if (gy && (!gc || !gd || !gs || !gu || !info_b)) return SMNN_ERR_INVALID_ARG;
+  if (gw && (reinterpret_cast<uintptr_t>(gw) & 7)) return SMNN_ERR_INVALID_ARG;
+  if (!workspace || !aligned(workspace) || (factor && !aligned(factor))) return SMNN_ERR_WORKSPACE;
+  DeviceGuard dg(plan->device);
+  if (!dg.ok) return SMNN_ERR_CUDA;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return SMNN_ERR_CUDA;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaStreamDestroy(st);
+    return SMNN_ERR_CUDA;
+  }
+  t_capturing = true;
+  t_captured = 0;
+  const smnn_status rc = record_step(plan, c, d, s, u, y, factor, info, gy, gc, gd, gs, gu, gw,
+                                     info_b, workspace, st);
+  t_capturing = false;
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(st, &g);   // ends the capture on every path
+  cudaStreamDestroy(st);
+  if (rc != SMNN_OK || ec != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc != SMNN_OK ? rc : SMNN_ERR_CUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return SMNN_ERR_CUDA;
+  smnn_graph_s* h = new (std::nothrow) smnn_graph_s;
+  if (!h) {
+    cudaGraphExecDestroy(ex);
+    return SMNN_ERR_CUDA;
+  }
+  h->exec = ex;
+  h->device = plan->device;
+  h->kernels = t_captured;
+  *graph = h;
+  return SMNN_OK;
+}
+
+smnn_status smnn_graph_launch(smnn_graph graph, void* stream) {
+  if (!graph || !graph->exec) return SMNN_ERR_INVALID_ARG;
+  DeviceGuard dg(graph->device);
+  if (!dg.ok) return SMNN_ERR_CUDA;
+  if (cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) return SMNN_ERR_CUDA;
+  g_launches.fetch_add(graph->kernels, std::memory_order_relaxed);
+  return SMNN_OK;
+}
+
+smnn_status smnn_graph_destroy(smnn_graph graph) {
+  if (!graph) return SMNN_OK;
+  smnn_status rc = SMNN_OK;
+  {
+    DeviceGuard dg(graph->device);
+    if (!dg.ok || cudaGraphExecDestroy(graph->exec) != cudaSuccess) rc = SMNN_ERR_CUDA;
+  }
+  delete graph;
+  return rc;
 }
 
 const char* smnn_status_string(smnn_status status) {

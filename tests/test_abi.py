@@ -93,3 +93,15 @@ def test_coupled_descriptor_validation(V, Q, R, ok):
             B.lib.smnn_plan_destroy(h)
     else:
         assert rc in (B.SMNN_ERR_INVALID_ARG, B.SMNN_ERR_UNSUPPORTED) and not h.value
+
+
+def test_graph_calls_reject_null_arguments():
+    """smnn_graph_create checks its arguments before any device call (no GPU here) and
+    leaves *graph NULL; launching a NULL graph is refused; destroying NULL is a no-op."""
+    from paper_2410_06074_b300 import binding as B
+    h = ctypes.c_void_p(1234)
+    rc = B.lib.smnn_graph_create(None, *([None] * 15), ctypes.byref(h))
+    assert rc == B.SMNN_ERR_INVALID_ARG and not h.value
+    assert B.lib.smnn_graph_create(None, *([None] * 15), None) == B.SMNN_ERR_INVALID_ARG
+    assert B.lib.smnn_graph_launch(None, None) == B.SMNN_ERR_INVALID_ARG
+    assert B.lib.smnn_graph_destroy(None) == B.SMNN_OK

@@ -193,3 +193,49 @@ def test_cuda_graph_replay_matches_eager():
     torch.cuda.synchronize()
     for a, b in zip(eager, (y, gc, gd, gs, gu)):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("with_backward,store_factor", [(True, True), (True, False), (False, True)])
+def test_native_step_graph_matches_eager(with_backward, store_factor):
+    """smnn_graph_create records the step once; each smnn_graph_launch replays it on the
+    current contents of the same buffers, to the bits of the eager calls on those contents
+    (two different input sets in turn), and adds the graph's kernel count to the launch
+    counter."""
+    import torch
+    import paper_2410_06074_b300 as pk
+    from paper_2410_06074_b300 import binding as Bd
+    from smnn_workloads import random_problem
+    cfg = pk.SolveConfig(R_init=1, T_init=1, precision=pk.F32_REFINED_DF)
+    plan = pk.get_plan((2, 12, 3, 1500), cfg)
+    probs = [random_problem(seed, 12, 3, 1500, 2).cast(np.float32) for seed in (51, 52)]
+    host = [[torch.from_numpy(np.ascontiguousarray(a)).cuda()
+             for a in (p.c, p.d, p.s, p.u, upstream_gradient(p).astype(np.float32))] for p in probs]
+    c, d, s, u, gy = (torch.empty_like(t) for t in host[0])
+    ws = plan.workspace()
+    fac = plan.factor_buffer() if store_factor else None
+    y = torch.empty_like(c)
+    info, info_b = (torch.empty(plan.S, dtype=torch.int32, device="cuda") for _ in range(2))
+    gc, gd, gs, gu = (torch.empty_like(t) for t in (c, d, s, u))
+    bw = dict(gy=gy, gc=gc, gd=gd, gs=gs, gu=gu, info_b=info_b) if with_backward else {}
+    g = plan.graph(c, d, s, u, y, info, ws, factor=fac, **bw)
+    outs = (y, gc, gd, gs, gu) if with_backward else (y,)
+    for h in host:
+        for dst, src in zip((c, d, s, u, gy), h):
+            dst.copy_(src)
+        for t in outs:
+            t.fill_(float("nan"))
+        n0 = Bd.launch_count()
+        g.launch()
+        torch.cuda.synchronize()
+        n_graph = Bd.launch_count() - n0
+        got = [t.clone() for t in outs]
+        assert int((info != 0).sum()) == 0
+        n1 = Bd.launch_count()
+        plan.factor_solve(c, d, s, u, y, info, ws, factor=fac)
+        if with_backward:
+            plan.backward(c, d, s, u, y, gy, gc, gd, gs, gu, info_b, ws, factor=fac)
+        torch.cuda.synchronize()
+        assert n_graph == Bd.launch_count() - n1 > 0
+        for a, b in zip(got, outs):
+            assert torch.equal(a, b)
+    g.close()
