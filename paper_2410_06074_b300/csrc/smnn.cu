@@ -67,6 +67,7 @@ inline void prof_end(cudaStream_t st) {
 
 constexpr int kThreads = 128;
 constexpr int kTopMax = 8;         // a level with at most this many steps per system is one chunk
+constexpr int kPcrMax = 32;        // AUTO: a top level of at most this many steps is a warp PCR
 constexpr int kMaxLevels = 8;
 constexpr size_t kAlign = 256;
 
@@ -112,6 +113,8 @@ struct FusedLevels {
   const int64_t* T0;
   LevelTables lt[kMaxLevels];
   LevelBufs<Tr, NB> lb[kMaxLevels];
+  int pcr_m;              // >= 0: the top level is a warp PCR on groups of 2^pcr_m lanes
+  PcrView<Tr, NB> pcr;
 };
 
 struct Problem0 {  // level-0 inputs
@@ -828,14 +831,32 @@ __global__ void __launch_bounds__(kThreads) k_upper(const __grid_constant__ Fuse
                                                     int32_t* info, const int32_t* skip) {
   const int32_t s0 = fl.cta_sys[blockIdx.x], s1 = fl.cta_sys[blockIdx.x + 1];
   const int nl = fl.nl;
-  for (int l = fl.from; l < nl; ++l) {
+  const bool pcr = fl.pcr_m >= 0;
+  const int top = pcr ? nl - 1 : nl;   // levels below `top` run as chunk sweeps
+  for (int l = fl.from; l < top; ++l) {
     if (l > fl.from) __syncthreads();
     const LevelTables& lt = fl.lt[l];
     const int64_t g = lt.coff[s0] + threadIdx.x;
     if (g < lt.coff[s1])
       dev_elimN<Tr, NB, kFactor, false>(lt, fl.lb[l], fl.lb[l - 1].out, fl.T0, info, skip, g, l == nl - 1);
   }
-  for (int l = nl - 1; l >= fl.from; --l) {
+  if (pcr) {
+    // one group of 2^pcr_m lanes per system; every lane of the CTA takes part in the
+    // shuffles, lanes without a system or row carry identity rows
+    __syncthreads();
+    const LevelTables& lt = fl.lt[nl - 1];
+    const int W = 1 << fl.pcr_m;
+    const int64_t i = s0 + int64_t(threadIdx.x / W);
+    const int k = int(threadIdx.x % W);
+    const bool sys = i < s1 && !(skip && skip[i]);
+    const int64_t P = sys ? lt.P[i] : 0;
+    const int64_t base = sys ? lt.base[i] : 0;
+    const int fail = pcr_top<Tr, NB, kFactor>(fl.lb[nl - 2].out, base, int(P), k, fl.pcr_m, fl.pcr,
+                                              fl.lb[nl - 2].xsep, sys && k < P);
+    if (kFactor && fail && *reinterpret_cast<volatile int32_t*>(info + i) == 0)
+      record_fail(info + i, int32_t(min(int64_t(fail) * lt.stride0, fl.T0[i])));
+  }
+  for (int l = top - 1; l >= fl.from; --l) {
     __syncthreads();
     const LevelTables& lt = fl.lt[l];
     const int64_t g = lt.coff[s0] + threadIdx.x;
@@ -1155,6 +1176,8 @@ struct smnn_plan_s {
   std::vector<int32_t> cta_sys;        // fused: first system of each CTA, [n_cta + 1]
   int32_t* d_cta_sys = nullptr;
   int up = 0;                          // > 0: levels up..top in one launch (k_upper)
+  int pcr_m = -1;                      // >= 0: top level solved by warp PCR, 2^pcr_m lanes/system
+  size_t o_pcr = 0;                    //   its multipliers and final factors (factor region)
   std::vector<int32_t> up_sys;         //   first system of each of its CTAs
   int32_t* d_up_sys = nullptr;
   size_t factor_bytes = 0, solve_bytes = 0;
@@ -1177,8 +1200,12 @@ namespace {
 // (Alg. 3/4 as written).  CR/AUTO: level 0 takes chunks long enough to leave ~75k threads
 // (4..64 steps; desc.chunk overrides).  An upper level keeps >= 32k chunks while the level
 // is large (L = its steps / 32k, 4..32), else takes L = 16, until one chunk of <= kTopMax
-// steps per system remains.  Each level costs about L dependent steps of latency plus two
+// steps per system remains (AUTO: <= kPcrMax, solved by a warp PCR).  Each level costs about L dependent steps of latency plus two
 // launches, so the upper levels stay short while enough chunks remain.
+// AUTO plans of the FP32 paths solve their top level by warp PCR; in FP64 the PCR's register
+// blocks double and it lost to the sequential top chunk (4.43 vs 4.22 ms on config 2).
+bool uses_pcr(const smnn_desc& d) { return d.algo == SMNN_ALGO_AUTO && d.precision != SMNN_F64; }
+
 std::vector<int> plan_levels(const smnn_desc& d, const std::vector<int64_t>& T, int64_t total) {
   int64_t maxT = 1;
   for (int64_t t : T) maxT = std::max(maxT, t);
@@ -1190,7 +1217,8 @@ std::vector<int> plan_levels(const smnn_desc& d, const std::vector<int64_t>& T, 
   std::vector<int64_t> P = T;
   int64_t maxP = maxT, sumP = total;
   bool first = true;
-  while (maxP > kTopMax && int(Ls.size()) < kMaxLevels - 1) {
+  const int64_t top_max = uses_pcr(d) ? kPcrMax : kTopMax;
+  while (maxP > top_max && int(Ls.size()) < kMaxLevels - 1) {
     int L;
     if (first) {
       if (d.chunk > 0) {
@@ -1258,10 +1286,11 @@ smnn_status build_plan_host(smnn_plan_s* pl) {
       if (L.coff[i + 1] - L.coff[i] > kThreads) return false;
     return true;
   };
-  auto pack = [&](const Level& L, std::vector<int32_t>& cta) {
+  auto pack = [&](const Level& L, std::vector<int32_t>& cta, int64_t max_sys) {
     cta.assign(1, 0);
     for (int64_t i = 0; i < S; ++i)
-      if (L.coff[i + 1] - L.coff[cta.back()] > kThreads) cta.push_back(int32_t(i));
+      if (L.coff[i + 1] - L.coff[cta.back()] > kThreads || i - cta.back() >= max_sys)
+        cta.push_back(int32_t(i));
     cta.push_back(int32_t(S));
   };
   pl->fused = false;
@@ -1272,11 +1301,22 @@ smnn_status build_plan_host(smnn_plan_s* pl) {
   if (want_fused) {
     if (!fits(pl->lv[0])) return SMNN_ERR_UNSUPPORTED;
     pl->fused = true;
-    pack(pl->lv[0], pl->cta_sys);
+    pack(pl->lv[0], pl->cta_sys, S);
   } else if (d.algo == SMNN_ALGO_AUTO) {
     for (int l = 1; l < int(pl->lv.size()) && !pl->up; ++l)
       if (fits(pl->lv[l])) pl->up = l;
-    if (pl->up) pack(pl->lv[pl->up], pl->up_sys);
+    // the top level (one chunk of <= kPcrMax steps per system) as a warp PCR inside k_upper:
+    // 2^pcr_m lanes per system, so a CTA holds at most kThreads / 2^pcr_m systems
+    pl->pcr_m = -1;
+    if (pl->up && uses_pcr(d)) {
+      const int topP = pl->lv.back().L;
+      int m = 0;
+      while ((1 << m) < topP) ++m;
+      pl->pcr_m = m;
+      pack(pl->lv[pl->up], pl->up_sys, kThreads >> m);
+    } else if (pl->up) {
+      pack(pl->lv[pl->up], pl->up_sys, S);
+    }
   }
   size_t f = 0, s = 0;  // buffer layout
   for (auto& L : pl->lv) {
@@ -1290,6 +1330,11 @@ smnn_status build_plan_host(smnn_plan_s* pl) {
     L.o_br = s; s += align_up(size_t(L.G) * NB * es);
     L.o_bl = s; s += align_up(size_t(L.G) * NB * es);
     L.o_xs = s; s += align_up(size_t(L.G) * NB * es);
+  }
+  pl->o_pcr = f;
+  if (pl->pcr_m >= 0) {
+    const size_t PR = 2 * size_t(kPcrLevels) * NB * NB + size_t(NT);   // PcrView's record
+    f += align_up(PR * size_t(pl->lv.back().N) * es);
   }
   {
     const Level& L0 = pl->lv[0];
@@ -1447,6 +1492,8 @@ FusedLevels<Tr, NB> fused_levels(const smnn_plan_s* pl, char* fac, char* sol, in
     fl.lt[l] = tables_of(pl->lv[l]);
     fl.lb[l] = bufs_of<Tr, NB>(pl->lv[l], fac, sol);
   }
+  fl.pcr_m = from ? pl->pcr_m : -1;
+  fl.pcr = PcrView<Tr, NB>{reinterpret_cast<Tr*>(fac + pl->o_pcr), pl->lv.back().N};
   return fl;
 }
 

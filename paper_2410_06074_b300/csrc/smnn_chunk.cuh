@@ -705,6 +705,242 @@ SMNN_HD bool solve_top(const ChunkOut<Tr, NB>& out, int64_t g, Tr* x) {
   return ok;
 }
 
+// ----------------------------------------------------------------------------- warp PCR
+
+// The top level as a warp-shuffle parallel cyclic reduction.  A system's top level is the
+// block-tridiagonal SPD system of its P <= 32 remaining separators,
+//   C_k x_{k-1} + A_k x_k + D_k x_{k+1} = b_k   (D_k = C_{k+1}^T),
+// with A_k = a_right_k + a_left_{k+1}, C_k = e_coup_k and b_k = b_right_k + b_left_{k+1}
+// from the level below.  Lane k of a group of W lanes (W = 2^m >= P) holds row k.  At stride
+// h = 1, 2, ..., W/2 every row eliminates its couplings to rows k -+ h with those rows'
+// equations:
+//   al = -C_k A_{k-h}^{-1},  ga = -D_k A_{k+h}^{-1},
+//   A_k += al D_{k-h} + ga C_{k+h},  C_k <- al C_{k-h},  D_k <- ga D_{k+h},
+//   b_k += al b_{k-h} + ga b_{k+h}.
+// Each A_k stays a Schur complement of the SPD matrix, so SPD; after m strides no coupling
+// is left and x_k = A_k^{-1} b_k.  All rows work at every stride (no idle half, no back
+// substitution): m dependent stages of register algebra and shuffles instead of the 2P
+// dependent steps of a sequential sweep.  Rows k >= P are identity rows.
+constexpr int kPcrLevels = 5;    // strides 1..16: W <= 32
+
+// Stored PCR data, per top-level step, element e at [e * N + step] (the lanes of a group read
+// consecutive steps): stride level v's al (NB x NB, row-major) at e = 2 v NB^2, its ga at
+// e = (2 v + 1) NB^2, and the Cholesky factor of the final A_k (lower triangle packed by
+// tri(), inverse diagonal in place) at e = 2 kPcrLevels NB^2.
+template <class Tr, int NB>
+struct PcrView {
+  static constexpr int NT = NB * (NB + 1) / 2;
+  static constexpr int PR = 2 * kPcrLevels * NB * NB + NT;
+  Tr* p;
+  int64_t N;
+  SMNN_HD Tr& at(int e, int64_t step) const { return p[int64_t(e) * N + step]; }
+};
+
+template <class Tr, int NB>
+__device__ __forceinline__ void pcr_pack(const Tr (&l)[NB][NB], const Tr (&inv)[NB], Tr (&f)[NB * (NB + 1) / 2]) {
+#pragma unroll
+  for (int a = 0; a < NB; ++a)
+#pragma unroll
+    for (int b = 0; b <= a; ++b) f[tri(a, b)] = a == b ? inv[a] : l[a][b];
+}
+template <class Tr, int NB>
+__device__ __forceinline__ void pcr_unpack(const Tr (&f)[NB * (NB + 1) / 2], Tr (&l)[NB][NB], Tr (&inv)[NB]) {
+#pragma unroll
+  for (int a = 0; a < NB; ++a)
+#pragma unroll
+    for (int b = 0; b <= a; ++b) {
+      if (a == b) inv[a] = f[tri(a, b)]; else l[a][b] = f[tri(a, b)];
+    }
+}
+// out = -M A^{-1}, A given by its packed Cholesky factor (A symmetric: row r of out solves
+// A z = M_r^T)
+template <class Tr, int NB>
+__device__ __forceinline__ void pcr_mult(const Tr (&f)[NB * (NB + 1) / 2], const Tr (&m)[NB][NB], Tr (&out)[NB][NB]) {
+  Tr l[NB][NB], inv[NB];
+  pcr_unpack<Tr, NB>(f, l, inv);
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    Tr v[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) v[a] = m[r][a];
+    trsv_l<Tr, NB>(l, inv, v);
+    trsv_lt<Tr, NB>(l, inv, v);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) out[r][a] = -v[a];
+  }
+}
+template <class Tr, int N>
+__device__ __forceinline__ void shfl_up_n(const Tr (&v)[N], Tr (&o)[N], int h, int w) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) o[i] = __shfl_up_sync(0xffffffffu, v[i], h, w);
+}
+template <class Tr, int N>
+__device__ __forceinline__ void shfl_down_n(const Tr (&v)[N], Tr (&o)[N], int h, int w) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) o[i] = __shfl_down_sync(0xffffffffu, v[i], h, w);
+}
+
+// One system's top level on a group of W lanes; every lane of the warp calls it (the
+// shuffles are warp-wide), with `in` false for lanes whose row does not exist.  prev: the
+// level below's chunk outputs; base: the index of the system's first top-level step there
+// and in pv; k: the lane's row; m = log2 W.  Writes x_k to x[(base + k) NB ...] for rows that
+// exist.  kFactor: computes and stores al, ga and the final factor; returns 1 + k if a pivot
+// of row k was not positive, else 0.  Replay: applies the stored multipliers to b only.
+template <class Tr, int NB, bool kFactor>
+__device__ __forceinline__ int pcr_top(const ChunkOut<Tr, NB>& prev, int64_t base, int P, int k, int m,
+                                       const PcrView<Tr, NB>& pv, Tr* x, bool in) {
+  constexpr int NT = NB * (NB + 1) / 2;
+  constexpr int NN = NB * NB;
+  const int W = 1 << m;
+  const int64_t j = base + k;
+  Tr b[NB];
+#pragma unroll
+  for (int a = 0; a < NB; ++a)
+    b[a] = in ? prev.b_right[j * NB + a] + (k + 1 < P ? prev.b_left[(j + 1) * NB + a] : Tr(0)) : Tr(0);
+  int fail = 0;
+  Tr f[NT];
+  if (kFactor) {
+    Tr A[NB][NB], C[NB][NB], Dm[NB][NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a)
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        const int lo = a >= c ? tri(a, c) : tri(c, a);
+        A[a][c] = in ? prev.a_right[j * NT + lo] + (k + 1 < P ? prev.a_left[(j + 1) * NT + lo] : Tr(0))
+                     : Tr(a == c ? 1 : 0);
+        C[a][c] = in && k > 0 ? prev.e_coup[j * NN + a * NB + c] : Tr(0);
+        Dm[a][c] = in && k + 1 < P ? prev.e_coup[(j + 1) * NN + c * NB + a] : Tr(0);
+      }
+    for (int v = 0; v < m; ++v) {
+      const int h = 1 << v;
+      Tr l[NB][NB], inv[NB];
+#pragma unroll
+      for (int a = 0; a < NB; ++a)
+#pragma unroll
+        for (int c = 0; c < NB; ++c) l[a][c] = A[a][c];
+      if (!chol<Tr, NB>(l, inv) && in && fail == 0) fail = k + 1;
+      pcr_pack<Tr, NB>(l, inv, f);
+      Tr fu[NT], fd[NT], Du[NN], Cu[NN], Cd[NN], Dd[NN], bu[NB], bd[NB];
+      Tr Cf[NN], Df[NN];
+#pragma unroll
+      for (int a = 0; a < NB; ++a)
+#pragma unroll
+        for (int c = 0; c < NB; ++c) { Cf[a * NB + c] = C[a][c]; Df[a * NB + c] = Dm[a][c]; }
+      shfl_up_n<Tr, NT>(f, fu, h, W);
+      shfl_up_n<Tr, NN>(Df, Du, h, W);
+      shfl_up_n<Tr, NN>(Cf, Cu, h, W);
+      shfl_up_n<Tr, NB>(b, bu, h, W);
+      shfl_down_n<Tr, NT>(f, fd, h, W);
+      shfl_down_n<Tr, NN>(Cf, Cd, h, W);
+      shfl_down_n<Tr, NN>(Df, Dd, h, W);
+      shfl_down_n<Tr, NB>(b, bd, h, W);
+      Tr al[NB][NB], ga[NB][NB];
+      if (k >= h) pcr_mult<Tr, NB>(fu, C, al);
+      else {
+#pragma unroll
+        for (int a = 0; a < NN; ++a) al[a / NB][a % NB] = Tr(0);
+      }
+      if (k + h < W) pcr_mult<Tr, NB>(fd, Dm, ga);
+      else {
+#pragma unroll
+        for (int a = 0; a < NN; ++a) ga[a / NB][a % NB] = Tr(0);
+      }
+#pragma unroll
+      for (int a = 0; a < NB; ++a) {
+        Tr nb = b[a];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) nb += al[a][c] * bu[c] + ga[a][c] * bd[c];
+        b[a] = nb;
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          Tr na = A[a][c], nc = Tr(0), nd = Tr(0);
+#pragma unroll
+          for (int e = 0; e < NB; ++e) {
+            na += al[a][e] * Du[e * NB + c] + ga[a][e] * Cd[e * NB + c];
+            nc += al[a][e] * Cu[e * NB + c];
+            nd += ga[a][e] * Dd[e * NB + c];
+          }
+          A[a][c] = na;
+          C[a][c] = nc;
+          Dm[a][c] = nd;
+        }
+      }
+      if (in) {
+#pragma unroll
+        for (int a = 0; a < NN; ++a) {
+          pv.at(2 * v * NN + a, j) = al[a / NB][a % NB];
+          pv.at((2 * v + 1) * NN + a, j) = ga[a / NB][a % NB];
+        }
+      }
+    }
+    Tr l[NB][NB], inv[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a)
+#pragma unroll
+      for (int c = 0; c < NB; ++c) l[a][c] = A[a][c];
+    if (!chol<Tr, NB>(l, inv) && in && fail == 0) fail = k + 1;
+    pcr_pack<Tr, NB>(l, inv, f);
+    if (in) {
+#pragma unroll
+      for (int e = 0; e < NT; ++e) pv.at(2 * kPcrLevels * NN + e, j) = f[e];
+    }
+  } else {
+    // replay: every stored multiplier is loaded up front (they do not depend on b), so the
+    // m stages wait for memory once rather than once per stage; blocks wider than 4 keep
+    // per-stage loads (the registers would spill)
+    constexpr bool kHoist = NB <= 4;
+    Tr mu[kHoist ? kPcrLevels : 1][2][NN];
+    if (kHoist) {
+#pragma unroll
+      for (int v = 0; v < (kHoist ? kPcrLevels : 1); ++v)
+#pragma unroll
+        for (int a = 0; a < NN; ++a) {
+          const bool use = in && v < m;
+          mu[v][0][a] = use && k >= (1 << v) ? pv.at(2 * v * NN + a, j) : Tr(0);
+          mu[v][1][a] = use && k + (1 << v) < W ? pv.at((2 * v + 1) * NN + a, j) : Tr(0);
+        }
+    }
+    if (in) {
+#pragma unroll
+      for (int e = 0; e < NT; ++e) f[e] = pv.at(2 * kPcrLevels * NN + e, j);
+    }
+#pragma unroll
+    for (int v = 0; v < kPcrLevels; ++v) {
+      if (v < m) {
+        const int h = 1 << v;
+        Tr bu[NB], bd[NB];
+        shfl_up_n<Tr, NB>(b, bu, h, W);
+        shfl_down_n<Tr, NB>(b, bd, h, W);
+        if (in) {
+#pragma unroll
+          for (int a = 0; a < NB; ++a) {
+            Tr nb = b[a];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) {
+              if (kHoist) {
+                nb += mu[kHoist ? v : 0][0][a * NB + c] * bu[c] + mu[kHoist ? v : 0][1][a * NB + c] * bd[c];
+              } else {
+                if (k >= h) nb += pv.at(2 * v * NN + a * NB + c, j) * bu[c];
+                if (k + h < W) nb += pv.at((2 * v + 1) * NN + a * NB + c, j) * bd[c];
+              }
+            }
+            b[a] = nb;
+          }
+        }
+      }
+    }
+  }
+  if (in) {
+    Tr l[NB][NB], inv[NB];
+    pcr_unpack<Tr, NB>(f, l, inv);
+    trsv_l<Tr, NB>(l, inv, b);
+    trsv_lt<Tr, NB>(l, inv, b);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) x[j * NB + a] = b[a];
+  }
+  return fail;
+}
+
 // Back-substitute chunk g given its separators' values (x_left unused without a left
 // separator).  emit(t, x, emit.fetch(t)) receives every step of the chunk, separator
 // included; the stored data of step t-1 (and emit's prefetch) are loaded while step t is

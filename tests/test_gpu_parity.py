@@ -67,19 +67,29 @@ def test_refined_fp32_forward(T, algo, chunk, prec):
                                            ([1, 2, 3, 5, 64, 65, 1000, 3001], 2, 32),
                                            ([200, 17, 500], 2, 0)])
 def test_fused_pass_equals_per_level_launches(seq_T, D, chunk, prec):
-    """One launch per solve pass (a CTA runs every level of its systems), or one launch for
-    the levels whose systems fit a CTA, performs the same operations in the same order as
-    one launch per level: the outputs agree bit for bit, forward and adjoint."""
+    """One launch per solve pass (a CTA runs every level of its systems) performs the same
+    operations in the same order as one launch per level: the outputs agree bit for bit,
+    forward and adjoint.  ALGO_AUTO (one launch for the levels whose systems fit a CTA, its
+    top level a warp-shuffle PCR: another elimination order) agrees with the oracle within
+    the precision's tolerance."""
     pk = P()
     prob = ragged_problem(seq_T, D=D, seed=21)
     gy = upstream_gradient(prob)
     p = getattr(pk, prec)
     split = gpu_grad(prob, gy, p, algo=pk.ALGO_CR, chunk=chunk)
-    for algo in (pk.ALGO_CR_FUSED, pk.ALGO_AUTO):   # one launch per pass; per level below
-        fused = gpu_grad(prob, gy, p, algo=algo, chunk=chunk)   # a CTA's size
-        for a, b in zip(fused, split):
-            np.testing.assert_array_equal(a, b)
-        assert (fused[-2] == 0).all() and (fused[-1] == 0).all()
+    fused = gpu_grad(prob, gy, p, algo=pk.ALGO_CR_FUSED, chunk=chunk)
+    for a, b in zip(fused, split):
+        np.testing.assert_array_equal(a, b)
+    assert (fused[-2] == 0).all() and (fused[-1] == 0).all()
+    auto = gpu_grad(prob, gy, p, algo=pk.ALGO_AUTO, chunk=chunk)
+    assert (auto[-2] == 0).all() and (auto[-1] == 0).all()
+    tol = {"F64": TOL_F64, "F32": TOL_F32}.get(prec, TOL_REF)
+    wdt = np.float64 if p == pk.F64 else np.float32
+    yo, gco, gdo, gso, guo, _ = oracle_grad(rounded(prob, p), gy.astype(wdt).astype(np.float64))
+    assert rel_err_per_system(auto[0], yo, prob).max() <= tol
+    if prec != "F32":
+        for a, b in zip(auto[1:5], (gco, gdo, gso, guo)):
+            assert rel_err(a, b) <= (1e-8 if p == pk.F64 else tol)
 
 
 @pytest.mark.parametrize("T,chunk", [(1000, 0), (2500, 16)])
@@ -135,6 +145,27 @@ def test_ragged_batch(seq_T):
         yo, info_o = oracle_solve(rounded(prob, prec))
         assert (info == info_o).all()
         assert rel_err_per_system(y, yo, prob).max() <= tol
+
+
+@pytest.mark.parametrize("chunk,tops", [(8, [1, 2, 3, 5, 8, 13, 16, 17, 31, 32]),
+                                        (16, [1, 2, 3, 5, 8, 9, 13, 16])])
+def test_pcr_top_level_over_every_size(chunk, tops):
+    """ALGO_AUTO solves the top level (<= 32 separators per system) by a warp-shuffle
+    parallel cyclic reduction: systems whose top levels hold 1 to 32 (or 1 to 16)
+    separators share one plan (groups of 32, or 16 lanes with two systems per warp; rows
+    beyond a system's size idle), forward and adjoint against the oracle."""
+    pk = P()
+    prob = ragged_problem([chunk * p - (p % 3) for p in tops], D=2, seed=33)
+    gy = upstream_gradient(prob)
+    for prec, tol, gtol in ((pk.F64, TOL_F64, 1e-8), (pk.F32_REFINED_DF, TOL_REF, TOL_REF)):
+        wdt = np.float64 if prec == pk.F64 else np.float32
+        y, gc, gd, gs, gu, info, info2 = gpu_grad(prob, gy.astype(wdt), prec, algo=pk.ALGO_AUTO,
+                                                  chunk=chunk)
+        yo, gco, gdo, gso, guo, info_o = oracle_grad(rounded(prob, prec), gy.astype(wdt).astype(np.float64))
+        assert (info == 0).all() and (info2 == 0).all() and (info_o == 0).all()
+        assert rel_err_per_system(y, yo, prob).max() <= tol
+        for a, b in ((gc, gco), (gd, gdo), (gs, gso), (gu, guo)):
+            assert rel_err(a, b) <= gtol, rel_err(a, b)
 
 
 def test_exact_polynomial_recovery_on_gpu():
