@@ -1,12 +1,14 @@
 """Autotuner for the level structure of the chunked solve.
 
 For a batch shape (R, number of systems, steps per system) and precision it times the
-candidates -- one sequential block-Cholesky sweep per system (SMNN_ALGO_SEQ, Alg. 3/4 as
-written), the chunked cyclic reduction with level-0 chunks of 8, 16, 32 or 64 steps, and the
-same reduction in one launch per solve pass (SMNN_ALGO_CR_FUSED, where every system fits a
-CTA; the plan is refused otherwise) --
-on the caller's inputs, forward + adjoint, after checking that each candidate reproduces the
-default plan's solution (so no candidate is ever picked for speed alone).  Winners are kept in
+candidates -- the default plan, one sequential block-Cholesky sweep per system
+(SMNN_ALGO_SEQ, Alg. 3/4 as written), the chunked cyclic reduction with level-0 chunks of 8,
+16, 32 or 64 steps, and the same reduction in one launch per solve pass (SMNN_ALGO_CR_FUSED,
+where every system fits a CTA; the plan is refused otherwise) -- on the caller's inputs,
+forward + adjoint, each as replays of the library's CUDA graph of the step (device time, as
+a training loop runs it, without the host's launch overhead), after checking that each
+candidate reproduces the default plan's solution (so no candidate is ever picked for speed
+alone).  Winners are kept in
 ``autotune_table.json`` next to this file, keyed by R, precision and power-of-two buckets of the
 system count and the mean steps per system; ``api.get_plan`` consults the table whenever a
 ``SolveConfig`` asks for ``ALGO_AUTO`` with ``chunk = 0``.
@@ -27,7 +29,7 @@ TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_table
 _lock = threading.Lock()
 _table = None
 
-CANDIDATES = [(B.ALGO_SEQ, 0)] + [(B.ALGO_AUTO, L) for L in (8, 16, 32, 64)] + \
+CANDIDATES = [(B.ALGO_AUTO, 0), (B.ALGO_SEQ, 0)] + [(B.ALGO_AUTO, L) for L in (8, 16, 32, 64)] + \
     [(B.ALGO_CR_FUSED, L) for L in (16, 32, 64)]
 
 
@@ -69,7 +71,7 @@ def record(R: int, S: int, steps: int, precision: int, algo: int, chunk: int, ms
             os.replace(tmp, TABLE)
 
 
-def autotune(c, d, s, u, cfg, gy=None, *, D=None, seq_T=None, repeats: int = 3, tol: float = 1e-6,
+def autotune(c, d, s, u, cfg, gy=None, *, D=None, seq_T=None, repeats: int = 10, tol: float = 1e-6,
              save: bool = True, candidates=CANDIDATES):
     """Time every candidate on these inputs (forward + adjoint when gy is given), keep the
     fastest whose y matches the default plan's within tol (relative L2), record it, and return
@@ -99,18 +101,17 @@ def autotune(c, d, s, u, cfg, gy=None, *, D=None, seq_T=None, repeats: int = 3, 
             results[(algo, chunk)] = None
             continue
         g = [torch.empty_like(t) for t in (c, d, s, u)]
-
-        def step():
-            plan.factor_solve(c, d, s, u, y, info, ws, factor=fac)
-            if gy is not None:
-                plan.backward(c, d, s, u, y, gy, *g, info, ws, factor=fac)
-        step()
+        info_b = torch.empty_like(info)
+        bw = dict(gy=gy, gc=g[0], gd=g[1], gs=g[2], gu=g[3], info_b=info_b) if gy is not None else {}
+        graph = plan.graph(c, d, s, u, y, info, ws, factor=fac, **bw)
+        graph.launch()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record()
         for _ in range(repeats):
-            step()
+            graph.launch()
         ev[1].record()
         torch.cuda.synchronize()
+        graph.close()
         ms = ev[0].elapsed_time(ev[1]) / repeats
         results[(algo, chunk)] = ms
         if best is None or ms < best[2]:
