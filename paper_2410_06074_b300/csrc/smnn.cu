@@ -266,14 +266,16 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(LevelTables lt, const Ts*
 // systems of a sequence, so it is gathered per element)
 template <class Tr>
 __global__ void __launch_bounds__(kThreads) k_gather_s(LevelTables lt, Problem0 p, Tr* s) {
-  const int64_t n = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (n >= lt.G * lt.L) return;
-  const int64_t g = n % lt.G;
-  const int j = int(n / lt.G);
+  // one thread per chunk: its position is looked up once, then its steps are copied (the
+  // interleaved stores are coalesced across the threads of a warp)
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g >= lt.G) return;
   const ChunkPos cp = chunk_pos(lt, g);
-  const int64_t t = cp.first + j;
-  if (t > cp.last) return;
-  s[n] = static_cast<const Tr*>(p.s)[p.soff[cp.i] + t];
+  const Tr* src = static_cast<const Tr*>(p.s) + p.soff[cp.i] + cp.first;
+  const int len = int(cp.last - cp.first + 1);
+  Tr* dst = s + g;
+#pragma unroll 4
+  for (int j = 0; j < len; ++j) dst[int64_t(j) * lt.G] = src[j];
 }
 
 // The per-chunk bodies of the level kernels (one thread = one chunk g of a level), shared by
@@ -1605,7 +1607,6 @@ L0Bufs<Tr> l0_bufs(const smnn_plan_s* pl, char* fac, char* sol) {
                     reinterpret_cast<double*>(sol + pl->o_pw)};
 }
 
-inline int64_t l0_elems(const smnn_plan_s* pl) { return pl->lv[0].G * int64_t(pl->lv[0].L); }
 
 // Per-element transposes, used when a tile of kTileChunks chunks would not fit in shared
 // memory (long chunks, e.g. the sequential algorithm).
@@ -1660,7 +1661,7 @@ smnn_status gather_inputs(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
     rc = tile_copy<Tr, Tr, Q * NB, true>(pl, static_cast<const Tr*>(p.c), nullptr, b.c, nullptr, st);
     if (rc == SMNN_OK) rc = tile_copy<Tr, Tr, Q, true>(pl, static_cast<const Tr*>(p.d), nullptr, b.d, nullptr, st);
     if (rc != SMNN_OK) return rc;
-    SMNN_LAUNCH(k_gather_s<Tr>, l0_elems(pl), st, tables_of(pl->lv[0]), p, b.s);
+    SMNN_LAUNCH(k_gather_s<Tr>, pl->lv[0].G, st, tables_of(pl->lv[0]), p, b.s);
   }
   if (vec) rc = tile_copy<Tr, Tr, NB, true>(pl, vec, nullptr, vec_out, vec_lo, st);
   return rc;
