@@ -979,6 +979,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
   if (g >= lt.G) return;
   const ChunkPos cp = chunk_pos(lt, g);
   const int64_t G = lt.G, es = int64_t(lt.L) * G;
+  const int64_t ub = lt.base[cp.i];   // the system's first step in the caller's layout
   constexpr int V = NB / R1;
   const int nu = p.T_init * V * (p.R_init + 1);
   const N wg2 = Num<N>::from_d(p.wg2), wi2 = Num<N>::from_d(p.wi2), ws2 = Num<N>::from_d(p.ws2);
@@ -1010,14 +1011,14 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
         const float ef = Num<N>::to_f(e), cgf = Num<N>::to_f(cg);
 #pragma unroll
         for (int a = 0; a < NB; ++a)
-          gc[(q * NB + a) * es + k] = failed ? nan_t<Tr>()
+          gc[(ub + t) * (Q * NB) + q * NB + a] = failed ? nan_t<Tr>()
                                   : wg2f * fmaf(ef, Num<N>::to_f(ga[a]), -(cgf * Num<N>::to_f(ya[a])));
-        gd[q * es + k] = failed ? nan_t<Tr>() : wg2f * cgf;
+        gd[(ub + t) * Q + q] = failed ? nan_t<Tr>() : wg2f * cgf;
       } else {
 #pragma unroll
         for (int a = 0; a < NB; ++a)
-          gc[(q * NB + a) * es + k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * (e * ga[a] - cg * ya[a]));
-        gd[q * es + k] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * cg);
+          gc[(ub + t) * (Q * NB) + q * NB + a] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * (e * ga[a] - cg * ya[a]));
+        gd[(ub + t) * Q + q] = failed ? nan_t<Tr>() : st_n<Tr, N>(wg2 * cg);
       }
     }
     if (t < p.T_init) {
@@ -1190,7 +1191,7 @@ struct smnn_plan_s {
   size_t o_r = 0, o_gy = 0;            //   residual / explicit rhs, staged dl/dy
   size_t o_x = 0, o_g = 0;             //   plain solutions (FP64 and FP32 paths)
   size_t o_yh = 0, o_yl = 0, o_gh = 0, o_gl = 0;  // float-float accumulators (FP32 paths)
-  size_t o_gc = 0, o_gd = 0, o_gs = 0; //   gradients before the scatter
+  size_t o_gs = 0;                     //   per-system dl/ds before the sum over dimensions
   void* tables = nullptr;              // one device allocation for every index table
   std::vector<char> table_blob;        // the tables, packed on the host
   std::vector<std::function<void(char*)>> table_binds;  // set the device pointers for a base
@@ -1361,8 +1362,6 @@ smnn_status build_plan_host(smnn_plan_s* pl) {
       pl->o_gh = take(GL * NB * 4);
       pl->o_gl = take(GL * NB * 4);
     }
-    pl->o_gc = take(GL * size_t(pl->NQ) * NB * es);
-    pl->o_gd = take(GL * size_t(pl->NQ) * es);
     pl->o_part = take(size_t(L0.G) * 2 * sizeof(float));
     pl->o_prev = take(size_t(S) * sizeof(float));
     pl->o_skip = take(size_t(S) * sizeof(int32_t));
@@ -1590,7 +1589,7 @@ template <class Tr>
 struct L0Bufs {  // level-0 interleaved scratch of one call
   Tr* c; Tr* d; Tr* s; Tr* r; Tr* gy; Tr* x; Tr* g;
   float* yh; float* yl; float* gh; float* gl;
-  Tr* gc; Tr* gd; Tr* gs;
+  Tr* gs;
   float* part; float* prev; int32_t* skip;
   double* pw;   // [G0][3] the chunks' shares of dl/dw
 };
@@ -1601,8 +1600,8 @@ L0Bufs<Tr> l0_bufs(const smnn_plan_s* pl, char* fac, char* sol) {
   auto F = [&](size_t o) { return reinterpret_cast<float*>(sol + o); };
   auto PF = [&](size_t o) { return reinterpret_cast<Tr*>(fac + o); };
   return L0Bufs<Tr>{PF(pl->o_c), PF(pl->o_d), PF(pl->o_s), P(pl->o_r), P(pl->o_gy), P(pl->o_x),
-                    P(pl->o_g), F(pl->o_yh), F(pl->o_yl), F(pl->o_gh), F(pl->o_gl), P(pl->o_gc),
-                    P(pl->o_gd), P(pl->o_gs), F(pl->o_part), F(pl->o_prev),
+                    P(pl->o_g), F(pl->o_yh), F(pl->o_yl), F(pl->o_gh), F(pl->o_gl),
+                    P(pl->o_gs), F(pl->o_part), F(pl->o_prev),
                     reinterpret_cast<int32_t*>(sol + pl->o_skip),
                     reinterpret_cast<double*>(sol + pl->o_pw)};
 }
@@ -1742,8 +1741,8 @@ smnn_status gradients_out(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
   GradTables gt{pl->d_sq_b, pl->d_sq_k, L0.d_coff, pl->d_sys_T, pl->Q, L0.G, L0.L, int(pl->D)};
   const L0In<Tr> in{b.c, b.d, b.s};
   if (gw) {
-    SMNN_LAUNCH((k_grad<Tr, N, NB, true, R1, Q>), L0.G, st, tables_of(L0), p, in, yh, yl, gh, gl, info, b.gc,
-                b.gd, b.gs, gu, b.pw);
+    SMNN_LAUNCH((k_grad<Tr, N, NB, true, R1, Q>), L0.G, st, tables_of(L0), p, in, yh, yl, gh, gl, info, gc,
+                gd, b.gs, gu, b.pw);
     if (cudaGetLastError() != cudaSuccess) return SMNN_ERR_CUDA;
     prof_begin("k_reduce_w", st);
     k_reduce_w<<<1, 256, 0, st>>>(b.pw, L0.G, gw);
@@ -1752,10 +1751,8 @@ smnn_status gradients_out(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
     if (cudaGetLastError() != cudaSuccess) return SMNN_ERR_CUDA;
   } else {
     SMNN_LAUNCH((k_grad<Tr, N, NB, false, R1, Q>), L0.G, st, tables_of(L0), p, in, yh, yl, gh, gl, info,
-                b.gc, b.gd, b.gs, gu, nullptr);
+                gc, gd, b.gs, gu, nullptr);
   }
-  SMNN_TRY((tile_copy<Tr, Tr, Q * NB, false>(pl, b.gc, nullptr, gc, nullptr, st)));
-  SMNN_TRY((tile_copy<Tr, Tr, Q, false>(pl, b.gd, nullptr, gd, nullptr, st)));
   SMNN_LAUNCH(k_scatter_gs<Tr>, pl->Q * int64_t(L0.L), st, gt, pl->d_seq_soff, pl->d_seq_T, b.gs, gs);
   return SMNN_OK;
 }
