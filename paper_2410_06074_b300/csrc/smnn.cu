@@ -975,8 +975,18 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
                                                    const Tr* y_hi, const float* y_lo, const Tr* g_hi,
                                                    const float* g_lo, const int32_t* info, Tr* gc,
                                                    Tr* gd, Tr* gs, Tr* gu, double* part_w) {
-  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (g >= lt.G) return;
+  // FP32 outputs of up to 4 values per step are staged in shared memory over windows of
+  // kGW steps and written per chunk segment (a warp's stores then cover a few contiguous
+  // runs instead of 32 rows 32 steps apart); other shapes store straight from registers
+  constexpr bool kStage = std::is_same<Tr, float>::value && Q * NB <= 4;
+  constexpr int kGW = 8, KC = Q * NB, KT = kStage ? kGW * (KC + Q) + 1 : 1;   // padded row
+  __shared__ float tile[kStage ? kThreads : 1][KT];
+  __shared__ int64_t s_base[kStage ? kThreads : 1];
+  __shared__ int s_len[kStage ? kThreads : 1];
+  const int64_t g0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const bool live = g0 < lt.G;
+  if (!kStage && !live) return;
+  const int64_t g = live ? g0 : lt.G - 1;   // idle threads still meet the CTA's barriers
   const ChunkPos cp = chunk_pos(lt, g);
   const int64_t G = lt.G, es = int64_t(lt.L) * G;
   const int64_t ub = lt.base[cp.i];   // the system's first step in the caller's layout
@@ -994,7 +1004,17 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
   constexpr bool kF32 = std::is_same<Tr, float>::value;
   const float wg2f = float(p.wg2), ws2f = float(p.ws2);
   double wgov = 0.0, winit = 0.0, wsm = 0.0;
-  for (int64_t t = cp.first; t <= cp.last; ++t) {
+  const int len = live ? int(cp.last - cp.first + 1) : 0;
+  if (kStage) {
+    s_base[threadIdx.x] = lt.base[cp.i] + cp.first;
+    s_len[threadIdx.x] = len;
+  }
+  const int nwin = kStage ? (lt.L + kGW - 1) / kGW : 1;
+  int64_t t = cp.first;
+  for (int w = 0; w < nwin; ++w) {
+  const int jend = kStage ? min(len, (w + 1) * kGW) : len;
+  for (int j = kStage ? w * kGW : 0; j < jend; ++j, ++t) {
+    const int jw = j - (kStage ? w * kGW : 0);   // step within the window
 #pragma unroll
     for (int q = 0; q < Q; ++q) {   // the governing rows (Eq. 4), one per equation q
       N cy = Num<N>::zero(), cg = Num<N>::zero();
@@ -1010,10 +1030,14 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
         // e = d - c.y and c.g cancel and need N; the rest is FP32
         const float ef = Num<N>::to_f(e), cgf = Num<N>::to_f(cg);
 #pragma unroll
-        for (int a = 0; a < NB; ++a)
-          gc[(ub + t) * (Q * NB) + q * NB + a] = failed ? nan_t<Tr>()
-                                  : wg2f * fmaf(ef, Num<N>::to_f(ga[a]), -(cgf * Num<N>::to_f(ya[a])));
-        gd[(ub + t) * Q + q] = failed ? nan_t<Tr>() : wg2f * cgf;
+        for (int a = 0; a < NB; ++a) {
+          const float v = failed ? nan_t<float>() : wg2f * fmaf(ef, Num<N>::to_f(ga[a]), -(cgf * Num<N>::to_f(ya[a])));
+          if (kStage) tile[kStage ? threadIdx.x : 0][jw * KC + q * NB + a] = v;
+          else gc[(ub + t) * (Q * NB) + q * NB + a] = v;
+        }
+        const float vd = failed ? nan_t<float>() : wg2f * cgf;
+        if (kStage) tile[kStage ? threadIdx.x : 0][kGW * KC + jw * Q + q] = vd;
+        else gd[(ub + t) * Q + q] = vd;
       } else {
 #pragma unroll
         for (int a = 0; a < NB; ++a)
@@ -1066,7 +1090,20 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
     gs[k] = failed ? nan_t<Tr>() : st_n<Tr, N>(gsum);
     k += G;
   }
-  if (kW) {   // a failed system contributes nothing (its info flags it)
+  if (kStage) {   // write the window's rows of every chunk of the CTA
+    __syncthreads();
+    for (int f = threadIdx.x; f < kThreads * kGW * KC; f += kThreads) {
+      const int c = f / (kGW * KC), o = f % (kGW * KC);
+      if (w * kGW + o / KC < s_len[c]) gc[(s_base[c] + w * kGW) * KC + o] = tile[c][o];
+    }
+    for (int f = threadIdx.x; f < kThreads * kGW * Q; f += kThreads) {
+      const int c = f / (kGW * Q), o = f % (kGW * Q);
+      if (w * kGW + o / Q < s_len[c]) gd[(s_base[c] + w * kGW) * Q + o] = tile[c][kGW * KC + o];
+    }
+    __syncthreads();
+  }
+  }
+  if (kW && live) {   // a failed system contributes nothing (its info flags it)
     const double sw = failed ? 0.0 : 2.0;
     part_w[3 * g] = sw * sqrt(p.wg2) * wgov;
     part_w[3 * g + 1] = sw * sqrt(p.wi2) * winit;
