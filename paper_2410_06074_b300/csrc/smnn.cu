@@ -376,6 +376,9 @@ struct Level0Out {
   float* acc_hi;
   float* acc_lo;
   float* part;   // [G0][2] or nullptr
+  // mode 1: leave acc_lo unwritten (a refinement sweep follows and writes it); mode 2: the
+  // accumulator's low part has not been written yet and reads as zero
+  bool lo_skip = false;
 };
 
 template <class Tr, int NB, int kMode>
@@ -396,7 +399,7 @@ struct EmitY {
 #pragma unroll
       for (int a = 0; a < NB; ++a) {
         p.hi[a] = o.acc_hi[a * es + n];
-        p.lo[a] = o.acc_lo[a * es + n];
+        p.lo[a] = o.lo_skip ? 0.f : o.acc_lo[a * es + n];
       }
     }
     return p;
@@ -413,7 +416,7 @@ struct EmitY {
         acc = acc + float(v[a]);
         if (failed) acc = ff{nan_t<float>(), nan_t<float>()};
         o.acc_hi[a * es + n] = acc.hi;
-        o.acc_lo[a * es + n] = acc.lo;
+        if (kMode == 2 || !o.lo_skip) o.acc_lo[a * es + n] = acc.lo;
         if (kMode == 2 && o.part) {
           dd = fmaf(float(v[a]), float(v[a]), dd);
           yy = fmaf(acc.hi, acc.hi, yy);
@@ -1710,13 +1713,15 @@ smnn_status gather_inputs(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
 // and systems still above it after the last sweep get info = -1.
 template <class N, int NB, int R1 = NB, int Q = 1>
 smnn_status refine_sweeps(const smnn_plan_s* pl, const Problem0& p, char* fac, char* sol, float* xh,
-                          float* xl, const float* rhs, int K, int32_t* info, cudaStream_t st) {
+                          float* xl, const float* rhs, int K, int32_t* info, cudaStream_t st,
+                          bool lo_fresh = false) {
   const L0Bufs<float> b = l0_bufs<float>(pl, fac, sol);
   const bool adaptive = pl->desc.refine_tol > 0;
   if (adaptive) SMNN_LAUNCH(k_fill_i32, pl->S, st, b.skip, pl->S, 0);
   for (int it = 0; it < K; ++it) {
-    const ResIn ri{xh, xl, rhs};
-    Level0Out<float> oa{nullptr, xh, xl, adaptive ? b.part : nullptr};
+    const bool fresh = lo_fresh && it == 0;   // xl not yet written: reads as zero
+    const ResIn ri{xh, fresh ? nullptr : xl, rhs};
+    Level0Out<float> oa{nullptr, xh, xl, adaptive ? b.part : nullptr, fresh};
     SMNN_TRY((solve_pass<float, NB, N, R1, Q>(pl, p, nullptr, false, fac, sol, oa, 2, info, st, &ri,
                                        adaptive ? b.skip : nullptr)));
     if (adaptive)
@@ -1736,9 +1741,9 @@ smnn_status refine_forward(const smnn_plan_s* pl, const Problem0& p, char* fac, 
   float* yh = reinterpret_cast<float*>(fac + pl->o_fyh);
   float* yl = reinterpret_cast<float*>(fac + pl->o_fyl);
   const int K = pl->desc.max_refine;
-  Level0Out<float> o{nullptr, yh, yl, nullptr};
+  Level0Out<float> o{nullptr, yh, yl, nullptr, K > 0};   // the first sweep writes yl
   SMNN_TRY((solve_pass<float, NB, double, R1, Q>(pl, p, nullptr, true, fac, sol, o, 1, info, st)));
-  return refine_sweeps<N, NB, R1, Q>(pl, p, fac, sol, yh, yl, nullptr, K, info, st);
+  return refine_sweeps<N, NB, R1, Q>(pl, p, fac, sol, yh, yl, nullptr, K, info, st, K > 0);
 }
 
 // Adjoint: g = M^{-1} gy refined KA times (float-float accumulator).  y: with a saved factor
@@ -1750,7 +1755,7 @@ smnn_status refine_backward(const smnn_plan_s* pl, const Problem0& p, char* fac,
                             const float** y_hi_used, const float** y_lo_used) {
   const L0Bufs<float> b = l0_bufs<float>(pl, fac, sol);
   const int KA = pl->desc.precision == SMNN_F32 ? 0 : pl->desc.adjoint_refine;
-  Level0Out<float> og{nullptr, b.gh, b.gl, nullptr};
+  Level0Out<float> og{nullptr, b.gh, b.gl, nullptr, KA > 0};   // the first sweep writes gl
   SMNN_TRY((solve_pass<float, NB, double, R1, Q>(pl, p, b.gy, recompute, fac, sol, og, 1, info, st)));
   *y_hi_used = b.yh;
   *y_lo_used = nullptr;
@@ -1767,7 +1772,7 @@ smnn_status refine_backward(const smnn_plan_s* pl, const Problem0& p, char* fac,
       *y_lo_used = b.yl;
     }
   }
-  return refine_sweeps<N, NB, R1, Q>(pl, p, fac, sol, b.gh, b.gl, b.gy, KA, info, st);
+  return refine_sweeps<N, NB, R1, Q>(pl, p, fac, sol, b.gh, b.gl, b.gy, KA, info, st, KA > 0);
 }
 
 template <class Tr, class N, int NB, int R1 = NB, int Q = 1>
