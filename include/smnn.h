@@ -122,6 +122,11 @@ typedef struct smnn_desc {
                           /* V = Q = 1 with R = 1..3; V = 2, R = 1, Q = 1 or 2;    */
                           /* V = 3, R = 1, Q = 3; V = 2, R = 2, Q = 2.  Other valid */
                           /* shapes return SMNN_ERR_UNSUPPORTED at plan creation.   */
+  int32_t per_level_launches; /* 0 (default): refined FP32 solves of AUTO plans with   */
+                          /* two levels and at most 32 level-0 chunks per system run  */
+                          /* one warp per system, one launch per pass boundary;      */
+                          /* nonzero: one launch per level, pass and stop test there */
+                          /* too (the same arithmetic; for comparison and testing)   */
 } smnn_desc;
 
 typedef struct smnn_plan_s* smnn_plan;
@@ -266,6 +271,15 @@ smnn_status smnn_profile_read(smnn_kernel_time* out, int max, int* n);
 smnn_status smnn_factor_solve_noalloc(const smnn_desc* desc, const void* c, const void* d,
                                       const void* s, const void* u, void* y, int32_t* info,
                                       void* stream);
+
+/* Arithmetic peak of the current device, for roofline reports (no counterpart in the
+ * paper): the rate of fused multiply-adds, FP32 (fp64 = 0) or FP64 (fp64 != 0), measured
+ * by chains of dependent FMAs, eight independent chains per thread, at full occupancy
+ * (eight CTAs of 256 threads per SM), as the better of two timed launches of ~50 ms after
+ * a warm-up launch on `stream`.  Synchronous: returns after the timing with
+ * *fma_per_s set (one FMA = 2 flops).  Allocates a few bytes of device memory for the
+ * kernel's sink and frees them.  SMNN_ERR_CUDA on any CUDA error. */
+smnn_status smnn_fma_rate(int32_t fp64, double* fma_per_s, void* stream);
 
 /* Static string for a status code. */
 const char* smnn_status_string(smnn_status status);

@@ -39,6 +39,9 @@ class SolveConfig:
     # V = 2, R = 2, Q = 2
     V: int = 1
     Q: int = 1
+    # nonzero: one launch per level, pass and stop test even where the warp-fused launches
+    # apply (the same arithmetic; for comparison)
+    per_level_launches: int = 0
 
 
 def get_plan(shape_key, cfg: SolveConfig, tuned: bool = True) -> B.Plan:
@@ -63,7 +66,8 @@ def get_plan(shape_key, cfg: SolveConfig, tuned: bool = True) -> B.Plan:
                       precision=cfg.precision, algo=cfg.algo, max_refine=cfg.max_refine,
                       adjoint_refine=cfg.adjoint_refine,
                       chunk=cfg.chunk, w_gov=cfg.w_gov, w_init=cfg.w_init, w_smooth=cfg.w_smooth,
-                      refine_tol=cfg.refine_tol, V=cfg.V, Q=cfg.Q)
+                      refine_tol=cfg.refine_tol, V=cfg.V, Q=cfg.Q,
+                      per_level_launches=cfg.per_level_launches)
         _PLANS[key] = plan
     return plan
 

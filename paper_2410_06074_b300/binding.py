@@ -37,7 +37,8 @@ class Desc(ctypes.Structure):
                 ("w_init", ctypes.c_double), ("w_smooth", ctypes.c_double),
                 ("refine_tol", ctypes.c_double), ("num_seq", ctypes.c_int64),
                 ("dims_per_seq", ctypes.c_int64), ("T", ctypes.c_int64),
-                ("seq_T", ctypes.POINTER(ctypes.c_int64)), ("V", ctypes.c_int32), ("Q", ctypes.c_int32)]
+                ("seq_T", ctypes.POINTER(ctypes.c_int64)), ("V", ctypes.c_int32), ("Q", ctypes.c_int32),
+                ("per_level_launches", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -72,6 +73,7 @@ SYMBOLS = {
     "smnn_graph_create": (ctypes.c_int, [_VP] * 16 + [ctypes.POINTER(_VP)]),
     "smnn_graph_launch": (ctypes.c_int, [_VP, _VP]),
     "smnn_graph_destroy": (ctypes.c_int, [_VP]),
+    "smnn_fma_rate": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _VP]),
 }
 
 
@@ -93,6 +95,13 @@ LIB_PATH = lib._name
 
 def status_string(status: int) -> str:
     return lib.smnn_status_string(int(status)).decode()
+
+
+def fma_rate(fp64: bool = False, stream=None) -> float:
+    """FMAs per second of the current device in FP32 (or FP64), measured (smnn_fma_rate)."""
+    r = ctypes.c_double()
+    _check(lib.smnn_fma_rate(1 if fp64 else 0, ctypes.byref(r), _stream(stream)), "smnn_fma_rate")
+    return float(r.value)
 
 
 def launch_count() -> int:
@@ -173,6 +182,7 @@ class Plan:
     refine_tol: float = 0.0
     V: int = 1
     Q: int = 1
+    per_level_launches: int = 0
     handle: ctypes.c_void_p = field(default=None, repr=False)
 
     def __post_init__(self):
@@ -182,7 +192,8 @@ class Plan:
             seq = (ctypes.c_int64 * len(self.seq_T))(*self.seq_T)
         d = Desc(self.R, self.R_init, self.T_init, self.precision, self.algo, self.max_refine,
                  self.chunk, self.adjoint_refine, self.w_gov, self.w_init, self.w_smooth, self.refine_tol, self.B,
-                 self.D, int(self.T or 0), ctypes.cast(seq, ctypes.POINTER(ctypes.c_int64)), self.V, self.Q)
+                 self.D, int(self.T or 0), ctypes.cast(seq, ctypes.POINTER(ctypes.c_int64)), self.V, self.Q,
+                 self.per_level_launches)
         h = ctypes.c_void_p()
         _check(lib.smnn_plan_create(ctypes.byref(d), ctypes.byref(h)), "smnn_plan_create")
         self.handle = h

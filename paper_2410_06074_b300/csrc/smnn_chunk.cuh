@@ -786,7 +786,7 @@ __device__ __forceinline__ void shfl_down_n(const Tr (&v)[N], Tr (&o)[N], int h,
 // and in pv; k: the lane's row; m = log2 W.  Writes x_k to x[(base + k) NB ...] for rows that
 // exist.  kFactor: computes and stores al, ga and the final factor; returns 1 + k if a pivot
 // of row k was not positive, else 0.  Replay: applies the stored multipliers to b only.
-template <class Tr, int NB, bool kFactor>
+template <class Tr, int NB, bool kFactor, bool kHoistOk = true>
 __device__ __forceinline__ int pcr_top(const ChunkOut<Tr, NB>& prev, int64_t base, int P, int k, int m,
                                        const PcrView<Tr, NB>& pv, Tr* x, bool in) {
   constexpr int NT = NB * (NB + 1) / 2;
@@ -886,9 +886,9 @@ __device__ __forceinline__ int pcr_top(const ChunkOut<Tr, NB>& prev, int64_t bas
     }
   } else {
     // replay: every stored multiplier is loaded up front (they do not depend on b), so the
-    // m stages wait for memory once rather than once per stage; blocks wider than 4 keep
-    // per-stage loads (the registers would spill)
-    constexpr bool kHoist = NB <= 4;
+    // m stages wait for memory once rather than once per stage; blocks wider than 4, and
+    // callers short of registers (kHoistOk = false), keep per-stage loads
+    constexpr bool kHoist = NB <= 4 && kHoistOk;
     Tr mu[kHoist ? kPcrLevels : 1][2][NN];
     if (kHoist) {
 #pragma unroll

@@ -30,7 +30,7 @@ from dataclasses import dataclass, field, replace
 import numpy as np
 
 __all__ = ["Problem", "config1", "config2", "config2_slice", "config3", "config3b", "config4",
-           "config5", "random_problem", "upstream_gradient", "mse_target", "CONFIGS",
+           "config5", "random_problem", "ragged_problem", "upstream_gradient", "mse_target", "CONFIGS",
            "table5_odes", "table5_batch", "ODE_T", "ODE_H", "random_coupled_problem",
            "LORENZ", "lorenz_trajectory", "lorenz_chunks"]
 
@@ -100,6 +100,20 @@ def random_problem(seed: int = 0, B: int = 4, D: int = 2, T: int = 64, R: int = 
     u = rng.standard_normal((B, D, T_init, R_init + 1))
     return Problem(name, R, R_init, T_init, B, D, T, c, d, s, u,
                    w_gov=w[0], w_init=w[1], w_smooth=w[2])
+
+
+def ragged_problem(seq_T, D: int = 1, R: int = 2, seed: int = 5, s_lo: float = 0.01,
+                   s_hi: float = 0.1) -> Problem:
+    """Ragged batch (packed layout) with the coefficient generator above: sequence b has
+    seq_T[b] steps; draw order c, d, s, u over the packed steps; R_init = R - 1, T_init = 1."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    seq_T = np.asarray(seq_T, np.int64)
+    N = int(D * seq_T.sum())
+    c = _coeffs(rng, (N,), R)
+    d = rng.standard_normal(N)
+    s = rng.uniform(s_lo, s_hi, int(seq_T.sum()))
+    u = rng.standard_normal((len(seq_T) * D, 1, R))
+    return Problem("ragged", R, R - 1, 1, len(seq_T), D, None, c, d, s, u, seq_T=seq_T)
 
 
 def config1() -> Problem:

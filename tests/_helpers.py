@@ -89,3 +89,37 @@ def rel_err_per_system(got, ref, prob):
 
 def rel_err(got, ref):
     return float(np.linalg.norm((got - ref).reshape(-1)) / max(np.linalg.norm(ref.reshape(-1)), 1e-300))
+
+
+def per_sequence(a, prob):
+    """Split a per-sequence array (s and dl/ds: uniform [B, T], ragged [sum T_b]) by sequence."""
+    if prob.seq_T is None:
+        return [x.reshape(-1) for x in a.reshape(prob.B, -1)]
+    off = np.concatenate([[0], np.cumsum(prob.seq_T)])
+    return [a[off[b]:off[b + 1]].reshape(-1) for b in range(prob.B)]
+
+
+def _rel_parts(got, ref):
+    return np.array([np.linalg.norm(g - r) / max(np.linalg.norm(r), 1e-300) for g, r in zip(got, ref)])
+
+
+def grad_errs(got, ref, prob):
+    """Largest relative L2 error over the batch, per system for y, dl/dc, dl/dd and dl/du, and
+    per sequence for dl/ds (which sums over the D systems of a sequence): a gradient wrong on
+    one system is not diluted by the others.  got, ref: (y, gc, gd, gs, gu)."""
+    S = prob.B * prob.D
+    y, gc, gd, gs, gu = got[:5]
+    yo, gco, gdo, gso, guo = ref[:5]
+    return {"y": float(rel_err_per_system(y, yo, prob).max()),
+            "gc": float(rel_err_per_system(gc, gco, prob).max()),
+            "gd": float(rel_err_per_system(gd, gdo, prob).max()),
+            "gs": float(_rel_parts(per_sequence(gs, prob), per_sequence(gso, prob)).max()),
+            "gu": float(_rel_parts(list(gu.reshape(S, -1)), list(guo.reshape(S, -1))).max())}
+
+
+def assert_grads(got, ref, prob, tol, gtol=None):
+    """y within tol and every gradient within gtol (default tol), system by system."""
+    e = grad_errs(got, ref, prob)
+    gtol = tol if gtol is None else gtol
+    assert e["y"] <= tol and max(e[k] for k in ("gc", "gd", "gs", "gu")) <= gtol, e
+    return e

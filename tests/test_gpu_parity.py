@@ -9,9 +9,9 @@ import numpy as np
 import pytest
 
 import oracle as O
-from smnn_workloads import Problem, config1, random_problem, upstream_gradient
-from _helpers import (gpu_grad, gpu_solve, oracle_grad, oracle_solve, per_system, rel_err,
-                      rel_err_per_system, rounded)
+from smnn_workloads import Problem, config1, ragged_problem, random_problem, upstream_gradient
+from _helpers import (assert_grads, gpu_grad, gpu_solve, oracle_grad, oracle_solve, per_system,
+                      rel_err, rel_err_per_system, rounded)
 
 pytestmark = pytest.mark.gpu
 
@@ -21,17 +21,6 @@ TOL_F64, TOL_REF, TOL_F32 = 1e-9, 1e-6, 5e-3
 def P():
     import paper_2410_06074_b300 as pk
     return pk
-
-
-def ragged_problem(seq_T, D=1, R=2, seed=5, s_lo=0.01, s_hi=0.1):
-    rng = np.random.Generator(np.random.PCG64(seed))
-    seq_T = np.asarray(seq_T, np.int64)
-    N = int(D * seq_T.sum())
-    c = rng.standard_normal((N, R + 1)); c[:, R] = 1 + np.abs(c[:, R])
-    d = rng.standard_normal(N)
-    s = rng.uniform(s_lo, s_hi, int(seq_T.sum()))
-    u = rng.standard_normal((len(seq_T) * D, 1, R))
-    return Problem("ragged test", R, R - 1, 1, len(seq_T), D, None, c, d, s, u, seq_T=seq_T)
 
 
 # ----------------------------------------------------------------------------- forward
@@ -88,8 +77,36 @@ def test_fused_pass_equals_per_level_launches(seq_T, D, chunk, prec):
     yo, gco, gdo, gso, guo, _ = oracle_grad(rounded(prob, p), gy.astype(wdt).astype(np.float64))
     assert rel_err_per_system(auto[0], yo, prob).max() <= tol
     if prec != "F32":
-        for a, b in zip(auto[1:5], (gco, gdo, gso, guo)):
-            assert rel_err(a, b) <= (1e-8 if p == pk.F64 else tol)
+        assert_grads(auto, (yo, gco, gdo, gso, guo), prob, tol, 1e-8 if p == pk.F64 else tol)
+
+
+@pytest.mark.parametrize("prec", REFINED)
+@pytest.mark.parametrize("store_factor", [True, False])
+@pytest.mark.parametrize("seq_T,D,tol", [([1024] * 6, 2, 1e-7), ([1000, 700, 33, 1024, 97, 1], 3, 1e-7),
+                                         ([500, 300, 17], 2, 1e-7), ([1024] * 4, 2, 0.0)])
+def test_warp_fused_launches_equal_per_level_launches(seq_T, D, tol, store_factor, prec):
+    """Two-level plans (level-0 chunks of 32 steps, a warp-shuffle PCR on top) whose systems
+    fit a warp run their refined solves one warp per system, one launch per pass boundary;
+    the same plan with per_level_launches runs one launch per level, pass and stop test.  The
+    arithmetic and its order are the same: y, every gradient and both info arrays agree bit
+    for bit, forward and adjoint, with and without the stop test, with the saved factor and
+    with the factor recomputed, for systems of 1 to 32 chunks and PCR groups of 16 and 32."""
+    from paper_2410_06074_b300 import binding as Bd
+    pk = P()
+    prob = ragged_problem(seq_T, D=D, seed=27)
+    gy = upstream_gradient(prob).astype(np.float32)
+    p = getattr(pk, prec)
+    n0 = Bd.launch_count()
+    fused = gpu_grad(prob, gy, p, chunk=32, refine_tol=tol, store_factor=store_factor)
+    n1 = Bd.launch_count()
+    split = gpu_grad(prob, gy, p, chunk=32, refine_tol=tol, store_factor=store_factor, per_level_launches=1)
+    n2 = Bd.launch_count()
+    assert n1 - n0 < n2 - n1          # the fused launches did run
+    for a, b in zip(fused, split):
+        np.testing.assert_array_equal(a, b)
+    assert (fused[-2] == 0).all() and (fused[-1] == 0).all()
+    yo, *_ = oracle_grad(rounded(prob, p), gy.astype(np.float64))
+    assert rel_err_per_system(fused[0], yo, prob).max() <= TOL_REF
 
 
 @pytest.mark.parametrize("T,chunk", [(1000, 0), (2500, 16)])
@@ -163,9 +180,7 @@ def test_pcr_top_level_over_every_size(chunk, tops):
                                                   chunk=chunk)
         yo, gco, gdo, gso, guo, info_o = oracle_grad(rounded(prob, prec), gy.astype(wdt).astype(np.float64))
         assert (info == 0).all() and (info2 == 0).all() and (info_o == 0).all()
-        assert rel_err_per_system(y, yo, prob).max() <= tol
-        for a, b in ((gc, gco), (gd, gdo), (gs, gso), (gu, guo)):
-            assert rel_err(a, b) <= gtol, rel_err(a, b)
+        assert_grads((y, gc, gd, gs, gu), (yo, gco, gdo, gso, guo), prob, tol, gtol)
 
 
 def test_exact_polynomial_recovery_on_gpu():
@@ -242,8 +257,7 @@ def test_gradients_fp64_match_oracle(store_factor):
     gy = upstream_gradient(prob)
     y, gc, gd, gs, gu, info, info2 = gpu_grad(prob, gy, pk.F64, store_factor=store_factor, chunk=8)
     yo, gco, gdo, gso, guo, info_o = oracle_grad(prob, gy)
-    for a, b in ((y, yo), (gc, gco), (gd, gdo), (gs, gso), (gu, guo)):
-        assert rel_err(a, b) <= 1e-8, rel_err(a, b)
+    assert_grads((y, gc, gd, gs, gu), (yo, gco, gdo, gso, guo), prob, 1e-8)
 
 
 @pytest.mark.parametrize("prec", REFINED)
@@ -255,8 +269,7 @@ def test_gradients_refined_fp32_match_oracle(T, chunk, prec):
     r = rounded(prob, pk.F32_REFINED)
     y, gc, gd, gs, gu, info, info2 = gpu_grad(prob, gy.astype(np.float32), getattr(pk, prec), chunk=chunk)
     yo, gco, gdo, gso, guo, _ = oracle_grad(r, gy.astype(np.float32).astype(np.float64))
-    for name, a, b in (("y", y, yo), ("gc", gc, gco), ("gd", gd, gdo), ("gs", gs, gso), ("gu", gu, guo)):
-        assert rel_err(a, b) <= TOL_REF, (name, rel_err(a, b))
+    assert_grads((y, gc, gd, gs, gu), (yo, gco, gdo, gso, guo), prob, TOL_REF)
 
 
 @pytest.mark.parametrize("prec", REFINED)
@@ -269,9 +282,9 @@ def test_saved_and_recomputed_factor_agree(prec):
     a = gpu_grad(prob, gy, getattr(pk, prec), store_factor=True)
     b = gpu_grad(prob, gy, getattr(pk, prec), store_factor=False)
     ref = oracle_grad(rounded(prob, pk.F32_REFINED), gy.astype(np.float64))
-    for x, z, r in zip(a[:5], b[:5], ref[:5]):
-        assert rel_err(x, r) <= TOL_REF and rel_err(z, r) <= TOL_REF
-        assert rel_err(x, z) <= TOL_REF
+    assert_grads(a, ref, prob, TOL_REF)
+    assert_grads(b, ref, prob, TOL_REF)
+    assert_grads(a, b, prob, TOL_REF)
 
 
 def test_gradcheck_config2_slice():
@@ -331,8 +344,7 @@ def test_adaptive_refinement_stop_test(prec):
     gy = upstream_gradient(prob).astype(np.float32)
     out = gpu_grad(prob, gy, getattr(pk, prec), max_refine=4, adjoint_refine=3, refine_tol=1e-8)
     ref = oracle_grad(rounded(prob, pk.F32_REFINED), gy.astype(np.float64))
-    for a, b in zip(out[:5], ref[:5]):
-        assert rel_err(a, b) <= TOL_REF
+    assert_grads(out, ref, prob, TOL_REF)
     assert (out[5] == 0).all() and (out[6] == 0).all()
 
 
@@ -453,9 +465,7 @@ def test_coupled_systems_match_oracle(Q, T, algo, chunk, prec, tol):
     yo, gco, gdo, gso, guo, info_o = oracle_grad(r, g64)
     assert (info == 0).all() and (info2 == 0).all() and (info_o == 0).all()
     assert y.shape == (3, 2, T, 4)
-    assert rel_err_per_system(y, yo, prob).max() <= tol
-    for name, a, b in (("gc", gc, gco), ("gd", gd, gdo), ("gs", gs, gso), ("gu", gu, guo)):
-        assert rel_err(a, b) <= (1e-8 if p == pk.F64 else tol), (name, rel_err(a, b))
+    assert_grads((y, gc, gd, gs, gu), (yo, gco, gdo, gso, guo), prob, tol, 1e-8 if p == pk.F64 else tol)
 
 
 @pytest.mark.parametrize("prec,tol", [("F64", 1e-9), ("F32_REFINED_DF", 1e-6)])
@@ -481,9 +491,7 @@ def test_coupled_six_wide_blocks_match_oracle(V, R, Q, T, algo, chunk, prec, tol
     yo, gco, gdo, gso, guo, info_o = oracle_grad(r, gy.astype(wdt).astype(np.float64))
     assert (info == 0).all() and (info2 == 0).all() and (info_o == 0).all()
     assert y.shape == (3, 2, T, nb)
-    assert rel_err_per_system(y, yo, prob).max() <= tol
-    for name, a, b in (("gc", gc, gco), ("gd", gd, gdo), ("gs", gs, gso), ("gu", gu, guo)):
-        assert rel_err(a, b) <= (1e-8 if p == pk.F64 else tol), (name, rel_err(a, b))
+    assert_grads((y, gc, gd, gs, gu), (yo, gco, gdo, gso, guo), prob, tol, 1e-8 if p == pk.F64 else tol)
 
 
 def test_coupled_decoupled_equations_equal_independent_gpu_solves():
