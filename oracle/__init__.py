@@ -95,6 +95,9 @@ def _load():
         lib.orc_grad_batch.restype = ctypes.c_int
         lib.orc_grad_batch.argtypes = [pp, ctypes.c_int64, _i64, _i64, _i64, _d, _d, _d, _d, _d, _d,
                                        _d, _d, _d, _d, _d, _d, _i32, ctypes.c_int]
+        lib.orc_solve_qr_batch.restype = ctypes.c_int
+        lib.orc_solve_qr_batch.argtypes = [pp, ctypes.c_int64, _i64, _i64, _i64, _d, _d, _d, _d, _d,
+                                           _i32, ctypes.c_int]
         lib.orc_solve_dense_batch.restype = ctypes.c_int
         lib.orc_solve_dense_batch.argtypes = [pp, ctypes.c_int64, _i64, _i64, _i64, _d, _d, _d, _d,
                                               _d, _i32, ctypes.c_int]
@@ -193,8 +196,10 @@ def band_cholesky_solve(band, rhs):
 
 def solve(p: Params, c, d, s, u, *, D: int | None = None, seq_T=None, mode: str = "band",
           nthreads: int = 0):
-    """y for every system (Eq. 9).  mode: 'band' (band Cholesky, any T), 'dense'
-    (dense Cholesky of M) or 'qr' (Householder QR of W^{1/2} A).  Returns (y, info)."""
+    """y for every system (Eq. 9).  mode: 'band' (band Cholesky of M, any T), 'band_qr'
+    (plane-rotation QR of W^{1/2} A in band storage, any T: no normal equations, for
+    ill-conditioned problems), 'dense' (dense Cholesky of M) or 'qr' (Householder QR of
+    W^{1/2} A).  Returns (y, info)."""
     c, d, s, u = _f64(c), _f64(d), _f64(s), _f64(u)
     L = _layout(c, D, seq_T)
     y = _y_like(p, c, seq_T)
@@ -204,6 +209,8 @@ def solve(p: Params, c, d, s, u, *, D: int | None = None, seq_T=None, mode: str 
             _ptr(info, ctypes.c_int32))
     if mode == "band":
         rc = _load().orc_solve_batch(*args, int(nthreads))
+    elif mode == "band_qr":
+        rc = _load().orc_solve_qr_batch(*args, int(nthreads))
     elif mode in ("dense", "qr"):
         rc = _load().orc_solve_dense_batch(*args, 0 if mode == "dense" else 1)
     else:

@@ -26,8 +26,10 @@
  *   2. y = (A^T W A)^{-1} A^T W b (Eq. 9), by forming M = A^T W A and
  *      beta = A^T W b from the rows and factoring M with a textbook scalar
  *      band Cholesky (half-bandwidth 2(R+1)-1), or densely (Cholesky, or
- *      Householder QR of W^{1/2} A) for tiny systems.  No block structure,
- *      no App. A.2 closed forms, no reordering.
+ *      Householder QR of W^{1/2} A) for tiny systems; or, for any T and for
+ *      ill-conditioned problems, as argmin ||W^{1/2}(A y - b)|| by a band QR of
+ *      W^{1/2} A with plane rotations (no normal equations).  No block
+ *      structure, no App. A.2 closed forms, no reordering.
  *   3. Gradients for a loss l(y) given dl/dy (Sec. 3.2, Eq. 14): with
  *      g = M^{-1} dl/dy and per-row residual e_k = b_k - a_k.y,
  *        dl/dtheta = sum_k [ (da_k.g) w_k e_k + (a_k.g) dw_k e_k
@@ -43,8 +45,10 @@
  *   - row count m of Eq. 8;
  *   - exact recovery of degree<=R polynomial trajectories (zero residual);
  *   - w_gov = 0, R_init = R reduces to Taylor propagation y_{t+1}=exp(s_t N)y_t;
- *   - dense Householder QR, dense Cholesky and band Cholesky agree, and the
- *     band factor solves the same system as LAPACK's band Cholesky;
+ *   - dense Householder QR, dense Cholesky, band Cholesky and band QR agree,
+ *     the band factor solves the same system as LAPACK's band Cholesky, and
+ *     band QR matches numpy's least-squares solver where the normal
+ *     equations lose digits;
  *   - symmetry, positive definiteness and A^T W (b - A y) = 0;
  *   - gradients against central finite differences of the solve;
  *   - the closed-form ODE solutions of App. B.1 land near Table 5's errors.
@@ -109,96 +113,102 @@ int64_t orc_num_rows(const orc_params* p, int64_t T) {
   return T * p->Q + (int64_t)p->T_init * p->V * (p->R_init + 1) + 2 * (T - 1) * (int64_t)orc_nb(p);
 }
 
-/* Rows of A, b, W for one system of T steps.
- * c: [T][Q][V(R+1)], d: [T][Q], s: [T] (s[T-1] unused), u: [T_init][V][R_init+1]. */
+/* One row of each kind (App. A.1), written out from its constraint.  c: [T][Q][V(R+1)],
+ * d: [T][Q], s: [T], u: [T_init][V][R_init+1] of one system.  The row is cleared first. */
+
+/* Eq. 4: sum_{v,r} c_{t,q,v,r} y_{t,v,r} = d_{t,q}, weight w_gov^2. */
+static void orc_gov_row(const orc_params* p, int64_t t, int q, const double* c, const double* d,
+                        orc_row* w) {
+  const int nb = orc_nb(p);
+  memset(w, 0, sizeof(*w));
+  w->kind = ROW_GOV; w->t = (int32_t)t; w->r = q; w->nnz = nb;
+  for (int a = 0; a < nb; ++a) {
+    w->col[a] = t * nb + a;
+    w->val[a] = c[(t * p->Q + q) * nb + a];
+  }
+  w->b = d[t * p->Q + q];
+  w->w = p->w_gov * p->w_gov;
+  w->dw_dimp = 2.0 * p->w_gov;
+}
+
+/* Eq. 5: y_{t,v,r} = u_{t,v,r} for t < T_init, r <= R_init, weight w_init^2. */
+static void orc_init_row(const orc_params* p, int64_t t, int v, int r, const double* u, orc_row* w) {
+  const int nb = orc_nb(p), r1 = p->R + 1;
+  memset(w, 0, sizeof(*w));
+  w->kind = ROW_INIT; w->t = (int32_t)t; w->r = v * (p->R_init + 1) + r; w->nnz = 1;
+  w->col[0] = t * nb + v * r1 + r;
+  w->val[0] = 1.0;
+  w->b = u[(t * p->V + v) * (p->R_init + 1) + r];
+  w->w = p->w_init * p->w_init;
+  w->dw_dimp = 2.0 * p->w_init;
+}
+
+/* Eq. 6 as the row  sum_{r'>=r} s^{r'-r}/(r'-r)! y_{t,r'} - y_{t+1,r} = 0
+ * (App. A.1: block t is A+_t, block t+1 is -I); weight (w_smooth s_t^r)^2. */
+static void orc_fwd_row(const orc_params* p, int64_t t, int v, int r, const double* s, orc_row* w) {
+  const int nb = orc_nb(p), r1 = p->R + 1;
+  const double st = s[t];
+  memset(w, 0, sizeof(*w));
+  w->kind = ROW_FWD; w->t = (int32_t)t; w->r = r; w->nnz = 0;
+  for (int rp = r; rp < r1; ++rp) {
+    const int q = rp - r;
+    w->col[w->nnz] = t * nb + v * r1 + rp;
+    w->val[w->nnz] = orc_powi(st, q) / orc_factorial(q);
+    w->dval_ds[w->nnz] = q > 0 ? orc_powi(st, q - 1) / orc_factorial(q - 1) : 0.0;
+    w->nnz++;
+  }
+  w->col[w->nnz] = (t + 1) * nb + v * r1 + r;
+  w->val[w->nnz] = -1.0;
+  w->dval_ds[w->nnz] = 0.0;
+  w->nnz++;
+  w->b = 0.0;
+  w->w = orc_powi(p->w_smooth * orc_powi(st, r), 2);
+  w->dw_ds = r > 0 ? 2.0 * r * p->w_smooth * p->w_smooth * orc_powi(st, 2 * r - 1) : 0.0;
+  w->dw_dimp = 2.0 * p->w_smooth * orc_powi(st, 2 * r);
+}
+
+/* Eq. 7 as the row  -y_{t,r} + sum_{r'>=r} (-s)^{r'-r}/(r'-r)! y_{t+1,r'} = 0
+ * (App. A.1: block t is -I, block t+1 is A-_t); same weight as Eq. 6. */
+static void orc_bwd_row(const orc_params* p, int64_t t, int v, int r, const double* s, orc_row* w) {
+  const int nb = orc_nb(p), r1 = p->R + 1;
+  const double st = s[t];
+  memset(w, 0, sizeof(*w));
+  w->kind = ROW_BWD; w->t = (int32_t)t; w->r = r; w->nnz = 0;
+  w->col[w->nnz] = t * nb + v * r1 + r;
+  w->val[w->nnz] = -1.0;
+  w->dval_ds[w->nnz] = 0.0;
+  w->nnz++;
+  for (int rp = r; rp < r1; ++rp) {
+    const int q = rp - r;
+    w->col[w->nnz] = (t + 1) * nb + v * r1 + rp;
+    w->val[w->nnz] = orc_powi(-st, q) / orc_factorial(q);
+    /* d/ds (-s)^q/q! = -(-s)^{q-1}/(q-1)! */
+    w->dval_ds[w->nnz] = q > 0 ? -orc_powi(-st, q - 1) / orc_factorial(q - 1) : 0.0;
+    w->nnz++;
+  }
+  w->b = 0.0;
+  w->w = orc_powi(p->w_smooth * orc_powi(st, r), 2);
+  w->dw_ds = r > 0 ? 2.0 * r * p->w_smooth * p->w_smooth * orc_powi(st, 2 * r - 1) : 0.0;
+  w->dw_dimp = 2.0 * p->w_smooth * orc_powi(st, 2 * r);
+}
+
+/* Rows of A, b, W for one system of T steps, in App. A.1's order: governing rows, initial
+ * rows, forward smoothness rows, backward smoothness rows. */
 void orc_build_rows(const orc_params* p, int64_t T, const double* c, const double* d,
                     const double* s, const double* u, orc_row* rows) {
-  const int nb = orc_nb(p), r1 = p->R + 1;
+  const int r1 = p->R + 1;
   int64_t k = 0;
-  memset(rows, 0, sizeof(orc_row) * (size_t)orc_num_rows(p, T));
-
-  /* Eq. 4: sum_{v,r} c_{t,q,v,r} y_{t,v,r} = d_{t,q}, weight w_gov^2. */
-  for (int64_t t = 0; t < T; ++t) {
-    for (int q = 0; q < p->Q; ++q, ++k) {
-      orc_row* w = &rows[k];
-      w->kind = ROW_GOV; w->t = (int32_t)t; w->r = q; w->nnz = nb;
-      for (int a = 0; a < nb; ++a) {
-        w->col[a] = t * nb + a;
-        w->val[a] = c[(t * p->Q + q) * nb + a];
-      }
-      w->b = d[t * p->Q + q];
-      w->w = p->w_gov * p->w_gov;
-      w->dw_dimp = 2.0 * p->w_gov;
-    }
-  }
-
-  /* Eq. 5: y_{t,v,r} = u_{t,v,r} for t < T_init, r <= R_init, weight w_init^2. */
-  for (int64_t t = 0; t < p->T_init; ++t) {
-    for (int v = 0; v < p->V; ++v) {
-      for (int r = 0; r <= p->R_init; ++r, ++k) {
-        orc_row* w = &rows[k];
-        w->kind = ROW_INIT; w->t = (int32_t)t; w->r = v * (p->R_init + 1) + r; w->nnz = 1;
-        w->col[0] = t * nb + v * r1 + r;
-        w->val[0] = 1.0;
-        w->b = u[(t * p->V + v) * (p->R_init + 1) + r];
-        w->w = p->w_init * p->w_init;
-        w->dw_dimp = 2.0 * p->w_init;
-      }
-    }
-  }
-
-  /* Eq. 6 as the row  sum_{r'>=r} s^{r'-r}/(r'-r)! y_{t,r'} - y_{t+1,r} = 0
-   * (App. A.1: block t is A+_t, block t+1 is -I); weight (w_smooth s_t^r)^2. */
-  for (int64_t t = 0; t + 1 < T; ++t) {
-    const double st = s[t];
+  for (int64_t t = 0; t < T; ++t)
+    for (int q = 0; q < p->Q; ++q) orc_gov_row(p, t, q, c, d, &rows[k++]);
+  for (int64_t t = 0; t < p->T_init; ++t)
     for (int v = 0; v < p->V; ++v)
-    for (int r = 0; r < r1; ++r, ++k) {
-      orc_row* w = &rows[k];
-      w->kind = ROW_FWD; w->t = (int32_t)t; w->r = r; w->nnz = 0;
-      for (int rp = r; rp < r1; ++rp) {
-        const int q = rp - r;
-        w->col[w->nnz] = t * nb + v * r1 + rp;
-        w->val[w->nnz] = orc_powi(st, q) / orc_factorial(q);
-        w->dval_ds[w->nnz] = q > 0 ? orc_powi(st, q - 1) / orc_factorial(q - 1) : 0.0;
-        w->nnz++;
-      }
-      w->col[w->nnz] = (t + 1) * nb + v * r1 + r;
-      w->val[w->nnz] = -1.0;
-      w->dval_ds[w->nnz] = 0.0;
-      w->nnz++;
-      w->b = 0.0;
-      w->w = orc_powi(p->w_smooth * orc_powi(st, r), 2);
-      w->dw_ds = r > 0 ? 2.0 * r * p->w_smooth * p->w_smooth * orc_powi(st, 2 * r - 1) : 0.0;
-      w->dw_dimp = 2.0 * p->w_smooth * orc_powi(st, 2 * r);
-    }
-  }
-
-  /* Eq. 7 as the row  -y_{t,r} + sum_{r'>=r} (-s)^{r'-r}/(r'-r)! y_{t+1,r'} = 0
-   * (App. A.1: block t is -I, block t+1 is A-_t); same weight as Eq. 6. */
-  for (int64_t t = 0; t + 1 < T; ++t) {
-    const double st = s[t];
+      for (int r = 0; r <= p->R_init; ++r) orc_init_row(p, t, v, r, u, &rows[k++]);
+  for (int64_t t = 0; t + 1 < T; ++t)
     for (int v = 0; v < p->V; ++v)
-    for (int r = 0; r < r1; ++r, ++k) {
-      orc_row* w = &rows[k];
-      w->kind = ROW_BWD; w->t = (int32_t)t; w->r = r; w->nnz = 0;
-      w->col[w->nnz] = t * nb + v * r1 + r;
-      w->val[w->nnz] = -1.0;
-      w->dval_ds[w->nnz] = 0.0;
-      w->nnz++;
-      for (int rp = r; rp < r1; ++rp) {
-        const int q = rp - r;
-        w->col[w->nnz] = (t + 1) * nb + v * r1 + rp;
-        w->val[w->nnz] = orc_powi(-st, q) / orc_factorial(q);
-        /* d/ds (-s)^q/q! = -(-s)^{q-1}/(q-1)! */
-        w->dval_ds[w->nnz] = q > 0 ? -orc_powi(-st, q - 1) / orc_factorial(q - 1) : 0.0;
-        w->nnz++;
-      }
-      w->b = 0.0;
-      w->w = orc_powi(p->w_smooth * orc_powi(st, r), 2);
-      w->dw_ds = r > 0 ? 2.0 * r * p->w_smooth * p->w_smooth * orc_powi(st, 2 * r - 1) : 0.0;
-      w->dw_dimp = 2.0 * p->w_smooth * orc_powi(st, 2 * r);
-    }
-  }
+      for (int r = 0; r < r1; ++r) orc_fwd_row(p, t, v, r, s, &rows[k++]);
+  for (int64_t t = 0; t + 1 < T; ++t)
+    for (int v = 0; v < p->V; ++v)
+      for (int r = 0; r < r1; ++r) orc_bwd_row(p, t, v, r, s, &rows[k++]);
 }
 
 /* ---------------------------------------------------------------------------
@@ -410,6 +420,92 @@ static int orc_solve_one_band(const orc_params* p, int64_t T, const double* c, c
   return info;
 }
 
+/* ---------------------------------------------------------------------------
+ * Band Givens QR of W^{1/2} A, for any T: the least-squares definition of Eq. 9 solved
+ * without forming the normal equations, whose condition number is the square of that of
+ * W^{1/2} A (what an ill-conditioned problem needs; Golub & Van Loan's banded QR by plane
+ * rotations).  A row's nonzeros lie in columns [f, f+kd], kd = 2V(R+1)-1; so do the rows of
+ * R = Q^T W^{1/2} A shifted to their diagonal: R[i][j] for 0 <= j-i <= kd, stored at
+ * rb[i*(kd+1) + (j-i)].  Each row of W^{1/2} A, W^{1/2} b is merged into R and q = Q^T W^{1/2} b
+ * as it is generated (step by step, never all rows at once): for pivot j = f, f+1, ... its
+ * leading entry is annihilated by a rotation with R's row j, after which its nonzeros lie in
+ * [j+1, j+kd]; a row reaching an R row not yet filled becomes that row.  Then R y = q.
+ * ------------------------------------------------------------------------- */
+
+static void orc_qr_merge_row(const orc_row* w, int64_t n, int kd, double* rb, unsigned char* filled,
+                             double* q) {
+  const int ld = kd + 1;
+  double a[2 * ORC_MAX_NZ];
+  const double sw = sqrt(w->w);
+  int64_t j = w->col[0];
+  for (int k = 1; k < w->nnz; ++k) j = w->col[k] < j ? w->col[k] : j;
+  for (int k = 0; k < ld; ++k) a[k] = 0.0;
+  for (int k = 0; k < w->nnz; ++k) a[w->col[k] - j] += sw * w->val[k];
+  double beta = sw * w->b;
+  for (; j < n; ++j) {
+    if (a[0] != 0.0) {
+      double* rj = rb + j * ld;
+      if (!filled[j]) {                      /* the row becomes R's row j */
+        for (int k = 0; k < ld; ++k) rj[k] = a[k];
+        q[j] = beta;
+        filled[j] = 1;
+        return;
+      }
+      const double r = hypot(rj[0], a[0]);
+      const double cs = rj[0] / r, sn = a[0] / r;
+      for (int k = 0; k < ld; ++k) {
+        const double rv = rj[k], av = a[k];
+        rj[k] = cs * rv + sn * av;
+        a[k] = cs * av - sn * rv;
+      }
+      const double qv = q[j];
+      q[j] = cs * qv + sn * beta;
+      beta = cs * beta - sn * qv;
+    }
+    int nz = 0;                              /* next pivot: shift the window by one column */
+    for (int k = 0; k + 1 < ld; ++k) {
+      a[k] = a[k + 1];
+      nz |= a[k] != 0.0;
+    }
+    a[ld - 1] = 0.0;
+    if (!nz) return;                         /* only its residual share beta is left */
+  }
+}
+
+/* y of one system by band QR; returns 0 or (first zero pivot of R)+1. */
+static int orc_solve_one_qr_band(const orc_params* p, int64_t T, const double* c, const double* d,
+                                 const double* s, const double* u, double* y) {
+  const int nb = orc_nb(p), r1 = p->R + 1, kd = orc_band_width(p), ld = kd + 1;
+  const int64_t n = T * nb;
+  double* rb = (double*)calloc((size_t)(n * ld), sizeof(double));
+  double* q = (double*)calloc((size_t)n, sizeof(double));
+  unsigned char* filled = (unsigned char*)calloc((size_t)n, 1);
+  orc_row w;
+  for (int64_t t = 0; t < T; ++t) {          /* the rows of step t and of the pair (t, t+1) */
+    for (int qq = 0; qq < p->Q; ++qq) { orc_gov_row(p, t, qq, c, d, &w); orc_qr_merge_row(&w, n, kd, rb, filled, q); }
+    if (t < p->T_init)
+      for (int v = 0; v < p->V; ++v)
+        for (int r = 0; r <= p->R_init; ++r) { orc_init_row(p, t, v, r, u, &w); orc_qr_merge_row(&w, n, kd, rb, filled, q); }
+    if (t + 1 < T)
+      for (int v = 0; v < p->V; ++v)
+        for (int r = 0; r < r1; ++r) {
+          orc_fwd_row(p, t, v, r, s, &w); orc_qr_merge_row(&w, n, kd, rb, filled, q);
+          orc_bwd_row(p, t, v, r, s, &w); orc_qr_merge_row(&w, n, kd, rb, filled, q);
+        }
+  }
+  int info = 0;
+  for (int64_t i = n - 1; i >= 0; --i) {     /* R y = q */
+    const double* ri = rb + i * ld;
+    if (!filled[i] || ri[0] == 0.0) { info = (int)(i + 1); break; }
+    double acc = q[i];
+    const int64_t kend = i + kd < n - 1 ? i + kd : n - 1;
+    for (int64_t k = i + 1; k <= kend; ++k) acc -= ri[k - i] * y[k];
+    y[i] = acc / ri[0];
+  }
+  free(rb); free(q); free(filled);
+  return info;
+}
+
 /* Gradients of one system (see the file header for the formula).
  * gy: dl/dy [T][R+1]; outputs y, gc [T][R+1], gd [T], gs [T] (this system's
  * share; the last entry is 0), gu [T_init][R_init+1]. */
@@ -518,6 +614,25 @@ int orc_grad_batch(const orc_params* p, int64_t S, const int64_t* T_sys, const i
     for (int64_t t = 0; t < T_sys[i]; ++t) gs[soff[i] + t] = 0.0;
   for (int64_t i = 0; i < S; ++i)
     for (int64_t t = 0; t < T_sys[i]; ++t) gs[soff[i] + t] += gs_sys[off[i] + t];
+  return 0;
+}
+
+/* Band-QR batch (any T, OpenMP over systems); layout and info as orc_solve_batch. */
+int orc_solve_qr_batch(const orc_params* p, int64_t S, const int64_t* T_sys, const int64_t* off,
+                       const int64_t* soff, const double* c, const double* d, const double* s,
+                       const double* u, double* y, int32_t* info, int nthreads) {
+  const int nb = orc_nb(p), nq = p->Q;
+  const int nu = p->T_init * p->V * (p->R_init + 1);
+  if (!orc_params_ok(p)) return -1;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int64_t i = 0; i < S; ++i) {
+    const int r = orc_solve_one_qr_band(p, T_sys[i], c + off[i] * nq * nb, d + off[i] * nq, s + soff[i],
+                                        u + i * nu, y + off[i] * nb);
+    info[i] = r == 0 ? 0 : (int32_t)((r - 1) / nb + 1);
+  }
   return 0;
 }
 

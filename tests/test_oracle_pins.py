@@ -146,7 +146,7 @@ def test_normal_matrix_matches_appendix_a2(case):
 
 @pytest.mark.parametrize("case", CASES)
 def test_band_dense_and_qr_agree_with_brute_force(case):
-    """Band Cholesky, dense Cholesky and Householder QR equal numpy lstsq on W^{1/2}A."""
+    """Band Cholesky, dense Cholesky, Householder QR and band QR equal numpy lstsq on W^{1/2}A."""
     prob = case_problem(*case)
     p = params_of(prob)
     A, b, w = O.dense_system(p, *one(prob))
@@ -154,12 +154,47 @@ def test_band_dense_and_qr_agree_with_brute_force(case):
     y_ls = np.linalg.lstsq(sw[:, None] * A, sw * b, rcond=None)[0]
     M = A.T @ (w[:, None] * A)
     kappa = np.linalg.cond(M)
-    for mode in ("band", "dense", "qr"):
+    for mode in ("band", "dense", "qr", "band_qr"):
         y, info = O.solve(p, prob.c, prob.d, prob.s, prob.u, mode=mode)
         assert info[0] == 0
         err = np.linalg.norm(y.reshape(-1) - y_ls) / np.linalg.norm(y_ls)
         # normal equations lose up to kappa(M) * eps; QR only kappa(A) * eps
         assert err <= 50 * np.finfo(float).eps * kappa, (mode, err, kappa)
+
+
+def test_band_qr_where_normal_equations_lose_digits():
+    """The config-3 generator (R = 3, s ~ U[0.001, 0.01]) at T = 48: kappa(W^{1/2}A) ~ 1e7,
+    so kappa(M) ~ 1e14 and FP64 normal equations keep only ~3 digits of Eq. 9's solution.
+    The band QR of W^{1/2}A (plane rotations, no normal equations) matches numpy's SVD-based
+    least squares and the dense Householder QR to ~kappa(A) eps; band Cholesky of M does not."""
+    prob = W.config3(T=48)
+    p = params_of(prob)
+    A, b, w = O.dense_system(p, *one(prob))
+    sw = np.sqrt(w)
+    kA = np.linalg.cond(sw[:, None] * A)
+    assert kA > 1e6
+    y_ls = np.linalg.lstsq(sw[:, None] * A, sw * b, rcond=None)[0]
+    rel = lambda y: float(np.linalg.norm(y.reshape(-1) - y_ls) / np.linalg.norm(y_ls))
+    yq, iq = O.solve(p, prob.c[:, :1], prob.d[:, :1], prob.s, prob.u[:, :1], mode="band_qr")
+    yd, idq = O.solve(p, prob.c[:, :1], prob.d[:, :1], prob.s, prob.u[:, :1], mode="qr")
+    yc, ic = O.solve(p, prob.c[:, :1], prob.d[:, :1], prob.s, prob.u[:, :1], mode="band")
+    assert iq[0] == 0 and idq[0] == 0 and ic[0] == 0
+    eps = np.finfo(float).eps
+    assert rel(yq) <= 100 * eps * kA, (rel(yq), kA)
+    assert rel(yd) <= 100 * eps * kA
+    assert rel(yc) > 100 * rel(yq)            # the normal equations' loss the QR mode avoids
+
+
+@pytest.mark.parametrize("R,V,Q,T", [(1, 2, 2, 9), (2, 3, 1, 8), (2, 2, 3, 6), (3, 1, 1, 25)])
+def test_band_qr_equals_dense_householder_qr(R, V, Q, T):
+    """Band QR (rows merged step by step into a banded R) against the dense Householder QR
+    of the explicit W^{1/2}A, coupled and scalar shapes."""
+    prob = W.random_coupled_problem(8, 2, 2, T, R, V, Q, s_lo=0.05, s_hi=0.3, T_init=2)
+    p = O.Params(prob.R, prob.R_init, prob.T_init, V=V, Q=Q)
+    yb, ib = O.solve(p, prob.c, prob.d, prob.s, prob.u, mode="band_qr")
+    yq, iq = O.solve(p, prob.c, prob.d, prob.s, prob.u, mode="qr")
+    assert (ib == 0).all() and (iq == 0).all()
+    np.testing.assert_allclose(yb, yq, rtol=1e-9, atol=1e-10 * np.abs(yq).max())
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -220,9 +255,10 @@ def test_exact_polynomial_recovery(R):
     p = O.Params(R, R_init, 1, 1.3, 0.7, 1.9)
     A, b, w = O.dense_system(p, c, d, s, u)
     assert np.abs(A @ y.reshape(-1) - b).max() <= 1e-12 * np.abs(y).max() * 10
-    yo, info = O.solve(p, c[None, None], d[None, None], s[None], u[None, None])
-    assert info[0] == 0
-    assert np.abs(yo.reshape(T, R + 1) - y).max() <= 1e-7 * np.abs(y).max()
+    for mode in ("band", "band_qr"):
+        yo, info = O.solve(p, c[None, None], d[None, None], s[None], u[None, None], mode=mode)
+        assert info[0] == 0
+        assert np.abs(yo.reshape(T, R + 1) - y).max() <= 1e-7 * np.abs(y).max()
 
 
 @pytest.mark.parametrize("R", [1, 2, 3])
