@@ -131,8 +131,21 @@ struct Problem0 {  // level-0 inputs
   const void* u;
   const int64_t* soff;  // [S] offset of each system's step sizes
   double wg2, wi2, ws2;
+  // the squared weights split on the host into FP32 pairs (hi, lo), hi + lo = w^2 to ~2^-48:
+  // the FP32 kernels take them from here, so that no FP64 conversion (on B300's 1/64-rate
+  // FP64 pipe) is left in their loops
+  float wg2p[2], wi2p[2], ws2p[2];
   int T_init, R_init;
 };
+
+// Weights of Problem0 in the kernel's arithmetic: FP32 or FP64, or a number type N.
+template <class Tr> __device__ __forceinline__ Tr w_of(const double& w, const float (&wp)[2]);
+template <> __device__ __forceinline__ float w_of<float>(const double&, const float (&wp)[2]) { return wp[0]; }
+template <> __device__ __forceinline__ double w_of<double>(const double& w, const float (&)[2]) { return w; }
+template <class N> __device__ __forceinline__ N wn_of(const double& w, const float (&wp)[2]) {
+  if constexpr (std::is_same<N, double>::value) return w;
+  else return Num<N>::pair(wp[0], wp[1]);
+}
 
 // Level-0 interleaved arrays: element e of in-chunk position j of level-0 chunk g at
 // [(e*L + j)*G + g] (the layout of the factor), so that the consecutive chunks handled by a
@@ -159,9 +172,9 @@ __device__ __forceinline__ CoefSource<Tr, NB, R1, Q> make_coef(const Problem0& p
   src.g = g;
   src.G = G;
   src.L = L;
-  src.wg2 = Tr(p.wg2);
-  src.wi2 = Tr(p.wi2);
-  src.ws2 = Tr(p.ws2);
+  src.wg2 = w_of<Tr>(p.wg2, p.wg2p);
+  src.wi2 = w_of<Tr>(p.wi2, p.wi2p);
+  src.ws2 = w_of<Tr>(p.ws2, p.ws2p);
   src.T_init = p.T_init;
   src.R_init = p.R_init;
   return src;
@@ -769,9 +782,9 @@ __device__ __forceinline__ void dev_elim0_res(const LevelTables& lt, const Level
   src.rhs = rhs;
   src.u = src.cs.u;
   src.ro_x = kRO;
-  src.wg2 = Num<N>::from_d(p.wg2);
-  src.wi2 = Num<N>::from_d(p.wi2);
-  src.ws2 = Num<N>::from_d(p.ws2);
+  src.wg2 = wn_of<N>(p.wg2, p.wg2p);
+  src.wi2 = wn_of<N>(p.wi2, p.wi2p);
+  src.ws2 = wn_of<N>(p.ws2, p.ws2p);
   src.last = cp.last;
   src.init();
   elim_chunk<float, NB, false, kRO>(src, cp.first, cp.last, cp.k > 0, lb.fac, g, lb.out);
@@ -1106,7 +1119,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
   const int64_t ub = lt.base[cp.i];   // the system's first step in the caller's layout
   constexpr int V = NB / R1;
   const int nu = p.T_init * V * (p.R_init + 1);
-  const N wg2 = Num<N>::from_d(p.wg2), wi2 = Num<N>::from_d(p.wi2), ws2 = Num<N>::from_d(p.ws2);
+  const N wg2 = wn_of<N>(p.wg2, p.wg2p), wi2 = wn_of<N>(p.wi2, p.wi2p), ws2 = wn_of<N>(p.ws2, p.ws2p);
   const bool failed = info[cp.i] > 0;
   N ya[NB], ga[NB];
   int64_t k = g;
@@ -1116,7 +1129,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(LevelTables lt, Problem0 p, L
     ga[a] = ld_pair<N>(g_hi, g_lo, a * es + k);
   }
   constexpr bool kF32 = std::is_same<Tr, float>::value;
-  const float wg2f = float(p.wg2), ws2f = float(p.ws2);
+  const float wg2f = p.wg2p[0], ws2f = p.ws2p[0];
   double wgov = 0.0, winit = 0.0, wsm = 0.0;
   const int len = live ? int(cp.last - cp.first + 1) : 0;
   if (kStage) {
@@ -1402,6 +1415,13 @@ Problem0 problem0(const smnn_plan_s* pl, const void* c, const void* d, const voi
   p.wg2 = pl->desc.w_gov * pl->desc.w_gov;
   p.wi2 = pl->desc.w_init * pl->desc.w_init;
   p.ws2 = pl->desc.w_smooth * pl->desc.w_smooth;
+  auto split = [](double w, float (&o)[2]) {
+    o[0] = float(w);
+    o[1] = float(w - double(o[0]));
+  };
+  split(p.wg2, p.wg2p);
+  split(p.wi2, p.wi2p);
+  split(p.ws2, p.ws2p);
   p.T_init = pl->desc.T_init;
   p.R_init = pl->desc.R_init;
   return p;
