@@ -282,6 +282,60 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(LevelTables lt, const Ts*
   }
 }
 
+// The inputs of a solve into the level-0 interleaved layout in one launch: c (KC values per
+// step) and d (KD) staged through shared memory as in k_tile (a CTA's kTileChunks chunks are
+// one contiguous range of the caller's c and d), and the step sizes of each chunk, one
+// contiguous run of its sequence's s (shared by the D systems of a sequence), staged chunk
+// by chunk.
+template <class Tr, int KC, int KD>
+__global__ void __launch_bounds__(kTileThreads) k_stage_in(LevelTables lt, Problem0 p, Tr* c_out, Tr* d_out,
+                                                           Tr* s_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int64_t s_u[kTileChunks];     // caller's step of each chunk's first step
+  __shared__ int64_t s_s[kTileChunks];     // its step size's position in s
+  __shared__ int s_len[kTileChunks];
+  const int64_t g0 = int64_t(blockIdx.x) * kTileChunks;
+  const int nch = int(min(int64_t(kTileChunks), lt.G - g0));
+  if (threadIdx.x < nch) {
+    const ChunkPos cp = chunk_pos(lt, g0 + threadIdx.x);
+    s_u[threadIdx.x] = lt.base[cp.i] + cp.first;
+    s_s[threadIdx.x] = p.soff[cp.i] + cp.first;
+    s_len[threadIdx.x] = int(cp.last - cp.first + 1);
+  }
+  __syncthreads();
+  const int64_t u0 = s_u[0];
+  const int span = int(s_u[nch - 1] + s_len[nch - 1] - u0);   // contiguous steps of c and d
+  const int L = lt.L;
+  Tr* bc = reinterpret_cast<Tr*>(smem_raw);
+  Tr* bd = bc + pad32(span * KC) + 1;
+  Tr* bs = bd + pad32(span * KD) + 1;       // step sizes, chunk by chunk: [gl][j]
+  const Tr* c = static_cast<const Tr*>(p.c);
+  const Tr* d = static_cast<const Tr*>(p.d);
+  const Tr* sv = static_cast<const Tr*>(p.s);
+#pragma unroll 4
+  for (int x = threadIdx.x; x < span * KC; x += blockDim.x) bc[pad32(x)] = c[u0 * KC + x];
+#pragma unroll 4
+  for (int x = threadIdx.x; x < span * KD; x += blockDim.x) bd[pad32(x)] = d[u0 * KD + x];
+  for (int x = threadIdx.x; x < nch * L; x += blockDim.x) {   // a warp reads a chunk's run of s
+    const int gl = x / L, j = x - gl * L;
+    if (j < s_len[gl]) bs[pad32(x)] = sv[s_s[gl] + j];
+  }
+  __syncthreads();
+  const int64_t es = int64_t(lt.L) * lt.G;
+#pragma unroll 4
+  for (int w = threadIdx.x; w < kTileChunks * lt.L; w += blockDim.x) {
+    const int gl = w % kTileChunks, j = w / kTileChunks;
+    if (gl >= nch || j >= s_len[gl]) continue;
+    const int loc = int(s_u[gl] - u0) + j;
+    const int64_t n = int64_t(j) * lt.G + g0 + gl;
+#pragma unroll
+    for (int e = 0; e < KC; ++e) c_out[e * es + n] = bc[pad32(loc * KC + e)];
+#pragma unroll
+    for (int e = 0; e < KD; ++e) d_out[e * es + n] = bd[pad32(loc * KD + e)];
+    s_out[n] = bs[pad32(gl * L + j)];
+  }
+}
+
 // step sizes: user sequence layout -> interleaved per system chunk (s is shared by the D
 // systems of a sequence, so it is gathered per element)
 template <class Tr>
@@ -881,7 +935,7 @@ __global__ void __launch_bounds__(kThreads, NB <= 4 ? 3 : 1) k_pass(const __grid
 //   kElim  0: none, 1: factorise (rhs, or beta), 2: replay the factor on rhs, 3: residual of
 //          x against rhs (or beta), x_lo unwritten yet when fresh_elim
 // With skip (refine_tol > 0) a system whose stop test passed does nothing in later launches;
-// a launch with kBack = 0 clears the system's flag.
+// a launch with kBack = 0 clears the system's flag (and, with clear_info, its info).
 #ifndef SMNN_WPASS_SMEM
 #define SMNN_WPASS_SMEM 0
 #endif
@@ -893,10 +947,14 @@ __global__ void __launch_bounds__(kThreads, NB <= 3 ? SMNN_WPASS_MIN_BLOCKS : 1)
 k_wpass(LevelTables lt0, LevelBufs<float, NB> lb0, LevelTables lt1, PcrView<float, NB> pcr, int pcr_m,
         int64_t S, const int64_t* T0, Problem0 p, L0In<float> in, const float* rhs, float* xh, float* xl,
         float* part, float* prev, int32_t* skip, float tol, int back_sweep, int K, bool lo_skip_back,
-        bool fresh_elim, int32_t* info) {
+        bool fresh_elim, bool clear_info, int32_t* info) {
   const int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= S) return;                       // whole warps
+  if (kBack == 0 && clear_info) {           // a solve's first launch: info starts at 0
+    if (lane == 0) info[i] = 0;
+    __syncwarp();
+  }
   if (skip) {
     if (kBack == 0) {
       if (lane == 0) skip[i] = 0;
@@ -1013,6 +1071,7 @@ template <class N> __device__ __forceinline__ N ld_pair(const double* hi, const 
 template <class Tr, class N> __device__ __forceinline__ Tr st_n(N v);
 template <> __device__ __forceinline__ float st_n<float, double>(double v) { return float(v); }
 template <> __device__ __forceinline__ float st_n<float, ff>(ff v) { return Num<ff>::to_f(v); }
+template <> __device__ __forceinline__ float st_n<float, ffl>(ffl v) { return Num<ffl>::to_f(v); }
 template <> __device__ __forceinline__ double st_n<double, double>(double v) { return v; }
 
 // -w_s^2 d/ds sum_r s^{2r} (f+_r e+_r + f-_r e-_r) for the pair (t, t+1), g and y held fixed.
@@ -1616,10 +1675,22 @@ smnn_status gather_inputs(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
                           const Tr* vec, Tr* vec_out, float* vec_lo, bool coefs, cudaStream_t st) {
   smnn_status rc = SMNN_OK;
   if (coefs) {
-    rc = tile_copy<Tr, Tr, Q * NB, true>(pl, static_cast<const Tr*>(p.c), nullptr, b.c, nullptr, st);
-    if (rc == SMNN_OK) rc = tile_copy<Tr, Tr, Q, true>(pl, static_cast<const Tr*>(p.d), nullptr, b.d, nullptr, st);
-    if (rc != SMNN_OK) return rc;
-    SMNN_LAUNCH(k_gather_s<Tr>, pl->lv[0].G, st, tables_of(pl->lv[0]), p, b.s);
+    const Level& L0 = pl->lv[0];
+    const int64_t e1 = int64_t(kTileChunks) * L0.L;   // steps of one CTA's chunks
+    const size_t shm = size_t(e1 * (Q * NB + Q + 1) + 3 * ((e1 * (Q * NB + Q + 1)) / 32 + 2)) * sizeof(Tr);
+    if (shm <= 48 * 1024) {   // one launch for c, d and s
+      prof_begin("k_stage_in", st);
+      k_stage_in<Tr, Q * NB, Q><<<unsigned((L0.G + kTileChunks - 1) / kTileChunks), kTileThreads, shm, st>>>(
+          tables_of(L0), p, b.c, b.d, b.s);
+      prof_end(st);
+      count_launch();
+      if (cudaGetLastError() != cudaSuccess) return SMNN_ERR_CUDA;
+    } else {                  // long chunks: per-element copies
+      rc = tile_copy<Tr, Tr, Q * NB, true>(pl, static_cast<const Tr*>(p.c), nullptr, b.c, nullptr, st);
+      if (rc == SMNN_OK) rc = tile_copy<Tr, Tr, Q, true>(pl, static_cast<const Tr*>(p.d), nullptr, b.d, nullptr, st);
+      if (rc != SMNN_OK) return rc;
+      SMNN_LAUNCH(k_gather_s<Tr>, L0.G, st, tables_of(L0), p, b.s);
+    }
   }
   if (vec) rc = tile_copy<Tr, Tr, NB, true>(pl, vec, nullptr, vec_out, vec_lo, st);
   return rc;
@@ -1652,7 +1723,8 @@ smnn_status refine_sweeps(const smnn_plan_s* pl, const Problem0& p, char* fac, c
 
 // A first pass (first 0: none, x already holds a solution; 1: factorise; 2: replay the
 // stored factor) and K refinement sweeps of x against rhs (nullptr: beta) on a plan with
-// wpass set: K + 2 launches of k_wpass (K + 1 without a first pass).
+// wpass set: K + 2 launches of k_wpass (K + 1 without a first pass).  With a first pass its
+// launch also clears info.
 template <class N, int NB, int R1 = NB, int Q = 1>
 smnn_status wpass_refine(const smnn_plan_s* pl, const Problem0& p, char* fac, char* sol, int first,
                          const float* rhs, float* xh, float* xl, int K, int32_t* info, cudaStream_t st) {
@@ -1672,7 +1744,7 @@ smnn_status wpass_refine(const smnn_plan_s* pl, const Problem0& p, char* fac, ch
                            SMNN_WPASS_SMEM);                                                            \
     SMNN_LAUNCH_SMEM(label, (k_wpass<NB, N, kB, kE, R1, Q>), n, SMNN_WPASS_SMEM, st, lt0, lb0, lt1, pcr,  \
                      pl->pcr_m, pl->S, pl->d_sys_T, p, in, rhs, xh, xl, b.part, b.prev, skip, tol, bs, K, \
-                     los, fr, info);                                                                    \
+                     los, fr, first != 0, info);                                                        \
   } while (0)
   // pass 0 is the first solve, passes 1..K the sweeps; launch j back substitutes pass j-1
   // and eliminates pass j
@@ -1779,8 +1851,8 @@ smnn_status factor_solve_t(const smnn_plan_s* pl, const void* c, const void* d, 
   char* fac = factor ? static_cast<char*>(factor) : static_cast<char*>(ws);
   char* sol = static_cast<char*>(ws) + pl->factor_bytes;
   const L0Bufs<Tr> b = l0_bufs<Tr>(pl, fac, sol);
-  const LevelTables lt0 = tables_of(pl->lv[0]);
-  SMNN_LAUNCH(k_fill_i32, pl->S, st, info, pl->S, 0);
+  // the fused refined solve clears info in its first launch
+  if (!(pl->wpass && std::is_same<Tr, float>::value)) SMNN_LAUNCH(k_fill_i32, pl->S, st, info, pl->S, 0);
   SMNN_TRY((gather_inputs<Tr, NB, R1, Q>(pl, p, b, nullptr, nullptr, nullptr, true, st)));
   if constexpr (std::is_same<Tr, float>::value) {
     if (pl->desc.precision == SMNN_F32_REFINED || pl->desc.precision == SMNN_F32_REFINED_DF) {
@@ -1806,7 +1878,9 @@ smnn_status backward_t(const smnn_plan_s* pl, const void* c, const void* d, cons
   char* fac = factor ? static_cast<char*>(const_cast<void*>(factor)) : static_cast<char*>(ws);
   char* sol = static_cast<char*>(ws) + pl->factor_bytes;
   const L0Bufs<Tr> b = l0_bufs<Tr>(pl, fac, sol);
-  SMNN_LAUNCH(k_fill_i32, pl->S, st, info, pl->S, 0);
+  // the fused refined adjoint (saved factor) clears info in its first launch
+  const bool fused_clear = pl->wpass && std::is_same<Tr, float>::value && factor != nullptr;
+  if (!fused_clear) SMNN_LAUNCH(k_fill_i32, pl->S, st, info, pl->S, 0);
   // with the saved factor, the forward's staged c, d, s are still in the factor region
   SMNN_TRY((gather_inputs<Tr, NB, R1, Q>(pl, p, b, static_cast<const Tr*>(gy), b.gy, nullptr, factor == nullptr, st)));
   Tr* gco = static_cast<Tr*>(gc);
@@ -1820,7 +1894,7 @@ smnn_status backward_t(const smnn_plan_s* pl, const void* c, const void* d, cons
     const float* yl = nullptr;
     if (pl->desc.precision == SMNN_F32_REFINED_DF) {
       SMNN_TRY((refine_backward<ffl, NB, R1, Q>(pl, p, fac, sol, factor == nullptr, y32, info, st, &yh, &yl)));
-      return gradients_out<float, ff, NB, R1, Q>(pl, p, b, yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, gwo, st);
+      return gradients_out<float, ffl, NB, R1, Q>(pl, p, b, yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, gwo, st);
     }
     SMNN_TRY((refine_backward<double, NB, R1, Q>(pl, p, fac, sol, factor == nullptr, y32, info, st, &yh, &yl)));
     return gradients_out<float, double, NB, R1, Q>(pl, p, b, yh, yl, b.gh, b.gl, info, gco, gdo, gso, guo, gwo, st);
