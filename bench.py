@@ -64,6 +64,12 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiler mode: run this many eager forward + adjoint steps of the headline "
                          "variant (no timing, no output) and exit, for ncu captures")
+    ap.add_argument("--profile-workload", default="config2",
+                    choices=["config2", "config2_f64", "config2_per_level", "config4", "config3b",
+                             "config5_f64_b16"],
+                    help="profiler mode workload: config 2 on the default path, on SMNN_F64 or with "
+                         "one launch per level and pass; config 4; config 3b; config 5 on SMNN_F64 "
+                         "with 16 of its 256 sequences (a few GB, for captures)")
     ap.add_argument("--refine-tol", type=float, default=1e-7,
                     help="per-system refinement stop test, the library's default (0: run every "
                          "sweep with no convergence check)")
@@ -175,9 +181,9 @@ def measured_peaks():
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the config-2 step, from the
 # ncu capture summarised in the named file (re-taken whenever the kernel changes)
-NCU_TRAFFIC = {"k_wpass[sweep1]": (669.361408e6 + 97.005568e6, "profiles/k_wpass_config2.md"),
-               "k_wpass[sweep2]": (769.498880e6 + 149.028352e6, "profiles/k_wpass_config2.md"),
-               "k_wpass[factor]": (85.301760e6 + 314.200320e6, "profiles/k_wpass_config2.md")}
+NCU_TRAFFIC = {"k_wpass[sweep2]": (770.9e6 + 148.9e6, "profiles/ncu_config2.md"),
+               "k_wpass[sweep1]": (671.0e6 + 97.2e6, "profiles/ncu_config2.md"),
+               "k_wpass[factor]": (85.3e6 + 314.2e6, "profiles/ncu_config2.md")}
 
 
 def alg_bytes(NB: int, D: int, esz: int = 4):
@@ -333,20 +339,33 @@ def run_ours(args, ws, rank, local):
 
 
 def profile_steps(args, local):
-    """Profiler mode: args.profile_steps eager forward + adjoint steps of the headline variant
-    (SMNN_F32_REFINED_DF on the config-2 workload, saved factor), one after another."""
+    """Profiler mode: args.profile_steps eager forward + adjoint steps of one workload (saved
+    factor), one after another; no timing and no output, for ncu captures."""
     import torch
     import paper_2410_06074_b300 as pk
+    from smnn_workloads import config3b, config4, config5
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    prob = config2()
-    p32 = prob.cast(np.float32)
-    inputs = [torch.from_numpy(a).to(dev) for a in (p32.c, p32.d, p32.s, p32.u)]
-    v = Variant(pk, prob, pk.F32_REFINED_DF, dev, inputs, chunk=args.chunk, max_refine=args.max_refine,
-                adjoint_refine=args.adjoint_refine, refine_tol=args.refine_tol, algo=ALGOS[args.algo])
-    v.gy = torch.from_numpy(upstream_gradient(prob, 2).astype(np.float32)).to(dev)
+    w = args.profile_workload
+    prob = {"config4": config4, "config3b": config3b,
+            "config5_f64_b16": lambda: config5(B=16)}.get(w, config2)()
+    prec = pk.F64 if w in ("config2_f64", "config5_f64_b16") else pk.F32_REFINED_DF
+    dt = np.float64 if prec == pk.F64 else np.float32
+    seq_T = None if prob.seq_T is None else tuple(int(x) for x in prob.seq_T)
+    c, d, s, u = (torch.from_numpy(np.ascontiguousarray(a, dt)).to(dev) for a in (prob.c, prob.d, prob.s, prob.u))
+    gy = torch.from_numpy(np.ascontiguousarray(upstream_gradient(prob, 2), dt)).to(dev)
+    cfg = pk.SolveConfig(R_init=prob.R_init, T_init=prob.T_init, precision=prec, chunk=args.chunk,
+                         max_refine=args.max_refine, adjoint_refine=args.adjoint_refine,
+                         refine_tol=args.refine_tol if prec != pk.F64 else 0.0, algo=ALGOS[args.algo],
+                         per_level_launches=1 if w == "config2_per_level" else 0)
+    plan = pk.get_plan(pk.api._shape_key(c, s, prob.D, seq_T, cfg), cfg)
+    ws, fac = plan.workspace(dev), plan.factor_buffer(dev)
+    y = torch.empty_like(c)
+    info, info_b = (torch.empty(plan.S, dtype=torch.int32, device=dev) for _ in range(2))
+    g = [torch.empty_like(t) for t in (c, d, s, u)]
     for _ in range(args.profile_steps):
-        v.step()
+        plan.factor_solve(c, d, s, u, y, info, ws, factor=fac)
+        plan.backward(c, d, s, u, y, gy, *g, info_b, ws, factor=fac)
     torch.cuda.synchronize()
 
 
