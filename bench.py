@@ -372,9 +372,10 @@ def profile_steps(args, local):
 def other_configs(args, ws, stream, flush):
     """Forward + adjoint time of the other large workloads (library defaults, saved factor,
     L2 flushed between steps): config 4 (4096 ragged systems, T in [32, 65536], R = 2),
-    config 3b (4 systems of 2^20 steps, R = 3) and two coupled batches (4096 systems of 1024
-    steps with V = 2 variables, R = 1, Q = 2 equations per step, and with V = 3, R = 1, Q = 3
-    and a diagonally dominant highest-derivative block) on SMNN_F32_REFINED_DF.
+    config 3b (4 systems of 2^20 steps, R = 3) and three coupled batches (4096 systems of 1024
+    steps with V = 2 variables, R = 1, Q = 2 equations per step; with V = 3, R = 1, Q = 3; and
+    with V = 3, R = 2, Q = 3, n_b = 9; the last two with a diagonally dominant
+    highest-derivative block) on SMNN_F32_REFINED_DF.
     Secondary lines: their accuracy against the oracle is covered by the parity tests."""
     import torch
     import paper_2410_06074_b300 as pk
@@ -383,8 +384,9 @@ def other_configs(args, ws, stream, flush):
     peak = measured_peaks()[0]["hbm_gbs"]
     coupled = lambda: random_coupled_problem(0, 512, 8, 1024, R=1, V=2, Q=2)   # noqa: E731
     coupled3 = lambda: random_coupled_problem(0, 512, 8, 1024, R=1, V=3, Q=3, lead_cross=0.25)  # noqa: E731
+    coupled9 = lambda: random_coupled_problem(0, 512, 8, 1024, R=2, V=3, Q=3, lead_cross=0.25)  # noqa: E731
     for name, make in (("config4", config4), ("config3b", config3b), ("coupled_V2_Q2", coupled),
-                       ("coupled_V3_Q3", coupled3)):
+                       ("coupled_V3_Q3", coupled3), ("coupled_V3_R2_Q3", coupled9)):
         prob = make().cast(np.float32)
         seq_T = None if prob.seq_T is None else tuple(int(x) for x in prob.seq_T)
         dev = torch.device("cuda", torch.cuda.current_device())

@@ -52,7 +52,7 @@ extern "C" {
 /* Largest derivative order the kernels are compiled for (R+1 <= 4 unknowns/step). */
 #define SMNN_MAX_R 3
 /* Largest block n_b = V(R+1) and equation count Q of a coupled step (smnn_desc.V, .Q). */
-#define SMNN_MAX_NB 6
+#define SMNN_MAX_NB 9
 #define SMNN_MAX_Q 3
 
 typedef enum {
@@ -120,7 +120,8 @@ typedef struct smnn_desc {
                           /* c [..][Q][V(R+1)], d [..][Q], u [..][T_init][V][R_init+1], */
                           /* y [..][V(R+1)] (gradients likewise).  Built shapes:   */
                           /* V = Q = 1 with R = 1..3; V = 2, R = 1, Q = 1 or 2;    */
-                          /* V = 3, R = 1, Q = 3; V = 2, R = 2, Q = 2.  Other valid */
+                          /* V = 3, R = 1, Q = 3; V = 2, R = 2, Q = 2; V = 3, R = 2, */
+                          /* Q = 3 (n_b = 9).  Other valid                         */
                           /* shapes return SMNN_ERR_UNSUPPORTED at plan creation.   */
   int32_t per_level_launches; /* 0 (default): refined FP32 solves of AUTO plans with   */
                           /* two levels and at most 32 level-0 chunks per system run  */

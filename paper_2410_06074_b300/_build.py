@@ -15,7 +15,7 @@ LIB = os.path.join(HERE, "libsmnn.so")
 MAIN = os.path.join(CSRC, "smnn.cu")
 SHAPE = os.path.join(CSRC, "smnn_shape.cu")
 # (n_b, R+1, Q) of every built step shape: the SMNN_SHAPES list of smnn_impl.cuh
-SHAPES = [(2, 2, 1), (3, 3, 1), (4, 4, 1), (4, 2, 1), (4, 2, 2), (6, 2, 3), (6, 3, 2)]
+SHAPES = [(9, 3, 3), (2, 2, 1), (3, 3, 1), (4, 4, 1), (4, 2, 1), (4, 2, 2), (6, 2, 3), (6, 3, 2)]
 DEPS = [MAIN, SHAPE] + [os.path.join(CSRC, f) for f in ("smnn_impl.cuh", "smnn_chunk.cuh", "smnn_num.cuh")] + \
     [os.path.join(os.path.dirname(HERE), "include", "smnn.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

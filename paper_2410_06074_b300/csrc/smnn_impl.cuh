@@ -1935,12 +1935,13 @@ smnn_status assemble_t(const smnn_plan_s* pl, const void* c, const void* d, cons
 // The instantiated step shapes (n_b = V (R+1), R+1, Q): one variable with R = 1..3 and one
 // governing equation; V = 2 variables of R = 1 with one or two equations per step; V = 3
 // variables of R = 1 with three equations (a first-order system in three states); V = 2
-// variables of R = 2 with two equations (two coupled second-order equations).  Each is
-// compiled by smnn_shape.cu with SMNN_SHAPE_NB, SMNN_SHAPE_R1 and SMNN_SHAPE_Q set.
+// variables of R = 2 with two equations (two coupled second-order equations); V = 3
+// variables of R = 2 with three equations (three coupled second-order states, n_b = 9).
+// Each is compiled by smnn_shape.cu with SMNN_SHAPE_NB, SMNN_SHAPE_R1 and SMNN_SHAPE_Q set.
 #define SMNN_SHAPES(X, ...)                                                           \
   X(2, 2, 1, __VA_ARGS__) X(3, 3, 1, __VA_ARGS__) X(4, 4, 1, __VA_ARGS__)             \
   X(4, 2, 1, __VA_ARGS__) X(4, 2, 2, __VA_ARGS__) X(6, 2, 3, __VA_ARGS__)             \
-  X(6, 3, 2, __VA_ARGS__)
+  X(6, 3, 2, __VA_ARGS__) X(9, 3, 3, __VA_ARGS__)
 
 // The launch sequences of one step shape, for the precision of the plan.
 namespace smnn_shapes {

@@ -77,12 +77,13 @@ def test_fused_pass_needs_every_system_within_one_cta():
 @pytest.mark.parametrize("V,Q,R,ok", [(2, 1, 1, True), (2, 2, 1, True), (3, 3, 1, True), (2, 2, 2, True),
                                       (1, 2, 2, False), (2, 1, 2, False), (3, 1, 1, False),
                                       (4, 1, 1, False), (2, 3, 1, False), (2, 4, 2, False),
-                                      (3, 3, 2, False), (0, 0, 2, True)])
+                                      (3, 3, 2, True), (3, 2, 2, False), (4, 2, 2, False),
+                                      (2, 3, 3, False), (0, 0, 2, True)])
 def test_coupled_descriptor_validation(V, Q, R, ok):
-    """V variables x (R+1) orders must fit a block of SMNN_MAX_NB = 6 and Q <= 3; shapes
+    """V variables x (R+1) orders must fit a block of SMNN_MAX_NB = 9 and Q <= 3; shapes
     outside the instantiated ones (V = Q = 1; V = 2, R = 1, Q <= 2; V = 3, R = 1, Q = 3;
-    V = 2, R = 2, Q = 2) are refused or reported unsupported at plan creation, before any
-    device call; 0 means 1 for both fields."""
+    V = 2, R = 2, Q = 2; V = 3, R = 2, Q = 3) are refused or reported unsupported at plan
+    creation, before any device call; 0 means 1 for both fields."""
     from paper_2410_06074_b300 import binding as B
     d = B.Desc(R, 0, 1, B.F32_REFINED, B.ALGO_CR, 2, 0, 0, 1.0, 1.0, 1.0, 0.0, 2, 2, 16, None, V, Q)
     h = ctypes.c_void_p()

@@ -494,6 +494,31 @@ def test_coupled_six_wide_blocks_match_oracle(V, R, Q, T, algo, chunk, prec, tol
     assert_grads((y, gc, gd, gs, gu), (yo, gco, gdo, gso, guo), prob, tol, 1e-8 if p == pk.F64 else tol)
 
 
+@pytest.mark.parametrize("prec,tol", [("F64", 1e-9), ("F32_REFINED_DF", 1e-6)])
+@pytest.mark.parametrize("T,algo,chunk", [(600, "AUTO", 0), (257, "CR", 8), (120, "SEQ", 0)])
+def test_coupled_nine_wide_blocks_match_oracle(T, algo, chunk, prec, tol):
+    """Steps of n_b = V(R+1) = 9 unknowns: three coupled second-order states with three
+    governing equations per step (Sec. 3.1, Eq. 4-8), forward and adjoint, against the
+    oracle's coupled rows.  Each step's highest-derivative block is kept diagonally dominant
+    (lead_cross), so that the FP32 factor's refinement converges."""
+    import paper_2410_06074_b300 as pk
+    from smnn_workloads import random_coupled_problem
+    V, R, Q = 3, 2, 3
+    prob = random_coupled_problem(90, 2, 2, T, R=R, V=V, Q=Q, T_init=2, w=(1.05, 0.95, 1.1),
+                                  lead_cross=0.5 / (V - 1))
+    p = getattr(pk, prec)
+    nb = V * (R + 1)
+    gy = upstream_gradient(prob)[..., :nb]
+    wdt = np.float64 if p == pk.F64 else np.float32
+    y, gc, gd, gs, gu, info, info2 = gpu_grad(prob, gy.astype(wdt), p,
+                                              algo=getattr(pk, "ALGO_" + algo), chunk=chunk)
+    r = rounded(prob, p)
+    yo, gco, gdo, gso, guo, info_o = oracle_grad(r, gy.astype(wdt).astype(np.float64))
+    assert (info == 0).all() and (info2 == 0).all() and (info_o == 0).all()
+    assert y.shape == (2, 2, T, nb)
+    assert_grads((y, gc, gd, gs, gu), (yo, gco, gdo, gso, guo), prob, tol, 1e-8 if p == pk.F64 else tol)
+
+
 def test_coupled_decoupled_equations_equal_independent_gpu_solves():
     """On the GPU too: two variables whose equations do not couple them solve as two scalar
     systems (FP64)."""

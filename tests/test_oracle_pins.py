@@ -512,7 +512,7 @@ def test_coupled_row_count_is_eq8(R, R_init, T_init, V, Q, T):
 
 
 @pytest.mark.parametrize("R,V,Q,T", [(1, 2, 2, 9), (2, 3, 1, 8), (2, 2, 3, 6), (1, 2, 1, 11), (1, 3, 3, 8),
-                                     (2, 2, 2, 7)])
+                                     (2, 2, 2, 7), (2, 3, 3, 7)])
 def test_coupled_normal_equations_match_qr(R, V, Q, T):
     """Brute force: the band normal-equation solve equals dense Householder QR on W^{1/2}A."""
     prob = W.random_coupled_problem(2, 2, 2, T, R, V, Q, s_lo=0.05, s_hi=0.3)
