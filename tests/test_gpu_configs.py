@@ -211,19 +211,21 @@ def test_cuda_graph_replay_matches_eager():
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("T,chunk", [(1500, 0), (1024, 32)])
 @pytest.mark.parametrize("with_backward,store_factor", [(True, True), (True, False), (False, True)])
-def test_native_step_graph_matches_eager(with_backward, store_factor):
+def test_native_step_graph_matches_eager(with_backward, store_factor, T, chunk):
     """smnn_graph_create records the step once; each smnn_graph_launch replays it on the
     current contents of the same buffers, to the bits of the eager calls on those contents
     (two different input sets in turn), and adds the graph's kernel count to the launch
-    counter."""
+    counter.  T = 1500 gives a plan of several levels (one launch per level); T = 1024 in
+    chunks of 32 a two-level plan whose refined solves run one warp per system."""
     import torch
     import paper_2410_06074_b300 as pk
     from paper_2410_06074_b300 import binding as Bd
     from smnn_workloads import random_problem
-    cfg = pk.SolveConfig(R_init=1, T_init=1, precision=pk.F32_REFINED_DF)
-    plan = pk.get_plan((2, 12, 3, 1500), cfg)
-    probs = [random_problem(seed, 12, 3, 1500, 2).cast(np.float32) for seed in (51, 52)]
+    cfg = pk.SolveConfig(R_init=1, T_init=1, precision=pk.F32_REFINED_DF, chunk=chunk)
+    plan = pk.get_plan((2, 12, 3, T), cfg)
+    probs = [random_problem(seed, 12, 3, T, 2).cast(np.float32) for seed in (51, 52)]
     host = [[torch.from_numpy(np.ascontiguousarray(a)).cuda()
              for a in (p.c, p.d, p.s, p.u, upstream_gradient(p).astype(np.float32))] for p in probs]
     c, d, s, u, gy = (torch.empty_like(t) for t in host[0])

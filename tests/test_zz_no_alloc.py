@@ -19,13 +19,13 @@ pytestmark = pytest.mark.gpu
 
 
 
-def _desc(B, prob, precision, seq=None):
-    return B.Desc(prob.R, prob.R_init, prob.T_init, precision, B.ALGO_AUTO, 3, 0, 3,
+def _desc(B, prob, precision, seq=None, chunk=0):
+    return B.Desc(prob.R, prob.R_init, prob.T_init, precision, B.ALGO_AUTO, 3, chunk, 3,
                   prob.w_gov, prob.w_init, prob.w_smooth, 0.0, prob.B, prob.D, int(prob.T or 0),
                   None if seq is None else ctypes.cast(seq, ctypes.POINTER(ctypes.c_int64)))
 
 
-def _both(B, prob, precision):
+def _both(B, prob, precision, chunk=0):
     """The no-allocation call and the planned call on the same inputs: (y, info) of each."""
     import torch
     dt = torch.float64 if precision == B.F64 else torch.float32
@@ -34,7 +34,7 @@ def _both(B, prob, precision):
     seq_T = None if prob.seq_T is None else tuple(int(x) for x in prob.seq_T)
     plan = B.Plan(R=prob.R, R_init=prob.R_init, T_init=prob.T_init, B=prob.B, D=prob.D,
                   T=None if seq_T else prob.T, seq_T=seq_T, precision=precision,
-                  max_refine=3, adjoint_refine=3)
+                  max_refine=3, adjoint_refine=3, chunk=chunk)
     y_ref = torch.empty_like(c)
     info_ref = torch.empty(plan.S, dtype=torch.int32, device="cuda")
     plan.factor_solve(c, d, s, u, y_ref, info_ref, plan.workspace())
@@ -42,7 +42,7 @@ def _both(B, prob, precision):
     y = torch.full_like(c, float("nan"))
     info = torch.full((plan.S,), 7, dtype=torch.int32, device="cuda")
     seq = None if seq_T is None else (ctypes.c_int64 * len(seq_T))(*seq_T)
-    desc = _desc(B, prob, precision, seq)
+    desc = _desc(B, prob, precision, seq, chunk)
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = B.lib.smnn_factor_solve_noalloc(ctypes.byref(desc), *(ctypes.c_void_p(t.data_ptr())
                                          for t in (c, d, s, u, y, info)), st)
@@ -55,16 +55,18 @@ def test_noalloc_matches_planned_solve_on_two_calls_in_a_row():
     """Same descriptor, same kernels, same inputs: the outputs must agree bit for bit (a slip in
     binding the tables into the shared scratch, or stale scratch from the previous call, cannot
     hide inside a tolerance).  Two uniform calls in a row, then a ragged batch and the FP64
-    path, which lay different tables over the same scratch."""
+    path, which lay different tables over the same scratch, and a plan whose refined solve runs
+    one warp per system."""
     from paper_2410_06074_b300 import binding as B
     from smnn_workloads import ragged_problem
 
-    cases = [(random_problem(31, 3, 2, 700, 2).cast(np.float32), B.F32_REFINED_DF),
-             (random_problem(32, 3, 2, 1500, 2).cast(np.float32), B.F32_REFINED_DF),
-             (ragged_problem([1, 5, 64, 65, 1000, 3001], D=2, seed=34).cast(np.float32), B.F32_REFINED_DF),
-             (random_problem(35, 2, 3, 900, 2), B.F64)]
-    for prob, prec in cases:
-        y, info, y_ref, info_ref = _both(B, prob, prec)
+    cases = [(random_problem(31, 3, 2, 700, 2).cast(np.float32), B.F32_REFINED_DF, 0),
+             (random_problem(32, 3, 2, 1500, 2).cast(np.float32), B.F32_REFINED_DF, 0),
+             (ragged_problem([1, 5, 64, 65, 1000, 3001], D=2, seed=34).cast(np.float32), B.F32_REFINED_DF, 0),
+             (random_problem(35, 2, 3, 900, 2), B.F64, 0),
+             (random_problem(36, 4, 2, 1024, 2).cast(np.float32), B.F32_REFINED_DF, 32)]   # one warp per system
+    for prob, prec, chunk in cases:
+        y, info, y_ref, info_ref = _both(B, prob, prec, chunk)
         assert (info_ref.numpy() == 0).all()
         assert np.array_equal(info.numpy(), info_ref.numpy())
         assert np.array_equal(y.numpy(), y_ref.numpy())
