@@ -935,7 +935,8 @@ __global__ void __launch_bounds__(kThreads, NB <= 4 ? 3 : 1) k_pass(const __grid
 //   kElim  0: none, 1: factorise (rhs, or beta), 2: replay the factor on rhs, 3: residual of
 //          x against rhs (or beta), x_lo unwritten yet when fresh_elim
 // With skip (refine_tol > 0) a system whose stop test passed does nothing in later launches;
-// a launch with kBack = 0 clears the system's flag (and, with clear_info, its info).
+// a launch with kBack = 0 clears the system's flag (and, with clear_info, its info).  rev:
+// warp w takes system S-1-w (the systems are independent; the order only affects caching).
 #ifndef SMNN_WPASS_SMEM
 #define SMNN_WPASS_SMEM 0
 #endif
@@ -947,10 +948,11 @@ __global__ void __launch_bounds__(kThreads, NB <= 3 ? SMNN_WPASS_MIN_BLOCKS : 1)
 k_wpass(LevelTables lt0, LevelBufs<float, NB> lb0, LevelTables lt1, PcrView<float, NB> pcr, int pcr_m,
         int64_t S, const int64_t* T0, Problem0 p, L0In<float> in, const float* rhs, float* xh, float* xl,
         float* part, float* prev, int32_t* skip, float tol, int back_sweep, int K, bool lo_skip_back,
-        bool fresh_elim, bool clear_info, int32_t* info) {
-  const int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+        bool fresh_elim, bool clear_info, bool rev, int32_t* info) {
+  const int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (i >= S) return;                       // whole warps
+  if (w >= S) return;                       // whole warps
+  const int64_t i = rev ? S - 1 - w : w;
   if (kBack == 0 && clear_info) {           // a solve's first launch: info starts at 0
     if (lane == 0) info[i] = 0;
     __syncwarp();
@@ -1744,8 +1746,12 @@ smnn_status wpass_refine(const smnn_plan_s* pl, const Problem0& p, char* fac, ch
                            SMNN_WPASS_SMEM);                                                            \
     SMNN_LAUNCH_SMEM(label, (k_wpass<NB, N, kB, kE, R1, Q>), n, SMNN_WPASS_SMEM, st, lt0, lb0, lt1, pcr,  \
                      pl->pcr_m, pl->S, pl->d_sys_T, p, in, rhs, xh, xl, b.part, b.prev, skip, tol, bs, K, \
-                     los, fr, first != 0, info);                                                        \
+                     los, fr, first != 0, (nlaunch++ & 1) != 0, info);                                 \
   } while (0)
+  // Successive launches take the systems in alternate orders, so that a launch starts with
+  // the systems the previous one finished last, whose factor records, z and x are the most
+  // likely to still be in L2.
+  int nlaunch = 0;
   // pass 0 is the first solve, passes 1..K the sweeps; launch j back substitutes pass j-1
   // and eliminates pass j
   // profiler labels: the sweep whose elimination a launch runs
