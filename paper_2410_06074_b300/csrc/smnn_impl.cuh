@@ -225,6 +225,18 @@ constexpr int kTileThreads = 256;
 
 __device__ __forceinline__ int pad32(int x) { return x + (x >> 5); }
 
+// One element global -> shared memory by cp.async: a thread's copies of a tile are all in
+// flight at once and hold no registers; cp_async_done() waits for this thread's copies,
+// and a barrier after it makes the whole tile visible to the CTA.
+template <class T> __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(int(sizeof(T))) : "memory");
+}
+__device__ __forceinline__ void cp_async_done() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 template <class Tr, class Ts, int K, bool kIn>
 __global__ void __launch_bounds__(kTileThreads) k_tile(LevelTables lt, const Ts* src, const float* src_lo,
                                                        Tr* dst, float* dst_lo) {
@@ -244,10 +256,12 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(LevelTables lt, const Ts*
   const int64_t span = s_u[nch - 1] + s_len[nch - 1] - u0;   // contiguous user steps
   const int64_t es = int64_t(lt.L) * lt.G;
   if (kIn) {
+    if constexpr (std::is_same<Tr, Ts>::value) {
+      for (int64_t x = threadIdx.x; x < span * K; x += blockDim.x) cp_async_elem(buf + pad32(int(x)), src + u0 * K + x);
+      cp_async_done();
+    } else {
 #pragma unroll 4
-    for (int64_t x = threadIdx.x; x < span * K; x += blockDim.x) {
-      Tr v = Tr(src[u0 * K + x]);
-      buf[pad32(int(x))] = v;
+      for (int64_t x = threadIdx.x; x < span * K; x += blockDim.x) buf[pad32(int(x))] = Tr(src[u0 * K + x]);
     }
     __syncthreads();
 #pragma unroll 4
@@ -312,14 +326,13 @@ __global__ void __launch_bounds__(kTileThreads) k_stage_in(LevelTables lt, Probl
   const Tr* c = static_cast<const Tr*>(p.c);
   const Tr* d = static_cast<const Tr*>(p.d);
   const Tr* sv = static_cast<const Tr*>(p.s);
-#pragma unroll 4
-  for (int x = threadIdx.x; x < span * KC; x += blockDim.x) bc[pad32(x)] = c[u0 * KC + x];
-#pragma unroll 4
-  for (int x = threadIdx.x; x < span * KD; x += blockDim.x) bd[pad32(x)] = d[u0 * KD + x];
+  for (int x = threadIdx.x; x < span * KC; x += blockDim.x) cp_async_elem(bc + pad32(x), c + u0 * KC + x);
+  for (int x = threadIdx.x; x < span * KD; x += blockDim.x) cp_async_elem(bd + pad32(x), d + u0 * KD + x);
   for (int x = threadIdx.x; x < nch * L; x += blockDim.x) {   // a warp reads a chunk's run of s
     const int gl = x / L, j = x - gl * L;
-    if (j < s_len[gl]) bs[pad32(x)] = sv[s_s[gl] + j];
+    if (j < s_len[gl]) cp_async_elem(bs + pad32(x), sv + s_s[gl] + j);
   }
+  cp_async_done();
   __syncthreads();
   const int64_t es = int64_t(lt.L) * lt.G;
 #pragma unroll 4
@@ -1321,11 +1334,54 @@ __global__ void __launch_bounds__(256) k_reduce_w(const double* part_w, int64_t 
   if (threadIdx.x < 3) gw[threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// gs: sum of the D systems' shares (system-chunk interleaved) -> user layout of s.  One
-// thread per (sequence chunk q, position j); the sum runs over dd in order.
+// gs: sum of the D systems' shares (system-chunk interleaved) -> user layout of s.  A CTA
+// takes kTileChunks consecutive sequence chunks, whose steps are one contiguous range of
+// the user layout (sequence chunks run in (sequence, chunk) order and sequences are
+// packed): the sums (over dd in order) are read across the chunks (coalesced), staged in
+// shared memory and written as that contiguous range.
 template <class Tr>
-__global__ void k_scatter_gs(GradTables gt, const int64_t* seq_soff, const int64_t* seq_T,
-                             const Tr* gsI, Tr* gs) {
+__global__ void __launch_bounds__(kTileThreads) k_scatter_gs(GradTables gt, const int64_t* seq_soff,
+                                                             const int64_t* seq_T, const Tr* gsI, Tr* gs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Tr* buf = reinterpret_cast<Tr*>(smem_raw);
+  __shared__ int64_t s_u[kTileChunks];   // user position of each sequence chunk's first step
+  __shared__ int64_t s_c[kTileChunks];   // interleaved index of its first system's chunk
+  __shared__ int64_t s_k[kTileChunks];   // chunks per system of its sequence
+  __shared__ int s_len[kTileChunks];
+  const int64_t q0 = int64_t(blockIdx.x) * kTileChunks;
+  const int nq = int(min(int64_t(kTileChunks), gt.Q - q0));
+  const int L = gt.L;
+  if (threadIdx.x < nq) {
+    const int64_t q = q0 + threadIdx.x;
+    const int64_t b = gt.sq_b[q], kc = gt.sq_k[q];
+    s_u[threadIdx.x] = seq_soff[b] + kc * L;
+    s_len[threadIdx.x] = int(min(int64_t(L), seq_T[b] - kc * L));
+    // the D systems of a sequence have the same steps, so their chunk blocks are
+    // consecutive and of equal size in the level table
+    s_c[threadIdx.x] = gt.coff0[b * gt.D] + kc;
+    s_k[threadIdx.x] = gt.coff0[b * gt.D + 1] - gt.coff0[b * gt.D];
+  }
+  __syncthreads();
+  const int64_t u0 = s_u[0];
+  const int span = int(s_u[nq - 1] + s_len[nq - 1] - u0);
+  for (int w = threadIdx.x; w < kTileChunks * L; w += blockDim.x) {
+    const int ql = w % kTileChunks, j = w / kTileChunks;
+    if (ql >= nq || j >= s_len[ql]) continue;
+    const Tr* src = gsI + int64_t(j) * gt.G + s_c[ql];
+    const int64_t kb = s_k[ql];
+    Tr acc = Tr(0);
+#pragma unroll 4
+    for (int dd = 0; dd < gt.D; ++dd) acc += src[dd * kb];
+    buf[pad32(int(s_u[ql] - u0) + j)] = acc;
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < span; x += blockDim.x) gs[u0 + x] = buf[pad32(x)];
+}
+
+// The same, one thread per (sequence chunk q, position j), for chunks too long to stage.
+template <class Tr>
+__global__ void k_scatter_gs_elem(GradTables gt, const int64_t* seq_soff, const int64_t* seq_T,
+                                  const Tr* gsI, Tr* gs) {
   const int64_t n = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (n >= gt.Q * gt.L) return;
   const int64_t q = n % gt.Q;
@@ -1845,7 +1901,17 @@ smnn_status gradients_out(const smnn_plan_s* pl, const Problem0& p, const L0Bufs
     SMNN_LAUNCH((k_grad<Tr, N, NB, false, R1, Q>), L0.G, st, tables_of(L0), p, in, yh, yl, gh, gl, info,
                 gc, gd, b.gs, gu, nullptr);
   }
-  SMNN_LAUNCH(k_scatter_gs<Tr>, pl->Q * int64_t(L0.L), st, gt, pl->d_seq_soff, pl->d_seq_T, b.gs, gs);
+  const size_t shm_gs = size_t(kTileChunks * L0.L + (kTileChunks * L0.L) / 32 + 1) * sizeof(Tr);
+  if (shm_gs <= 48 * 1024) {
+    prof_begin("k_scatter_gs", st);
+    k_scatter_gs<Tr><<<unsigned((pl->Q + kTileChunks - 1) / kTileChunks), kTileThreads, shm_gs, st>>>(
+        gt, pl->d_seq_soff, pl->d_seq_T, b.gs, gs);
+    prof_end(st);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return SMNN_ERR_CUDA;
+  } else {
+    SMNN_LAUNCH(k_scatter_gs_elem<Tr>, pl->Q * int64_t(L0.L), st, gt, pl->d_seq_soff, pl->d_seq_T, b.gs, gs);
+  }
   return SMNN_OK;
 }
 
