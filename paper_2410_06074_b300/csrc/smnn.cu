@@ -137,6 +137,9 @@ smnn_status build_plan_host(smnn_plan_s* pl) {
   }
   // refined FP32 solves of two-level plans whose systems fit a warp at level 0 (top level a
   // warp PCR): one warp per system, one launch per pass boundary (k_wpass)
+  pl->max_chunks0 = 0;
+  for (int64_t i = 0; i < S; ++i)
+    pl->max_chunks0 = std::max(pl->max_chunks0, pl->lv[0].coff[i + 1] - pl->lv[0].coff[i]);
   pl->wpass = false;
   if ((d.precision == SMNN_F32_REFINED || d.precision == SMNN_F32_REFINED_DF) && pl->lv.size() == 2 &&
       pl->up == 1 && pl->pcr_m >= 0 && pl->pcr_m <= 5 && d.per_level_launches == 0) {

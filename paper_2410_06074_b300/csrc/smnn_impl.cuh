@@ -572,6 +572,46 @@ __global__ void k_converge(int64_t S, const int64_t* coff0, const float* part, f
   else if (last && info[i] == 0) info[i] = -1;
 }
 
+// The same stop test with one CTA of kConvThreads per system, for plans whose systems have
+// many chunks (few long systems): thread t sums the chunk partials t, t + kConvThreads, ...
+// in order, each warp reduces with the fixed shuffle tree, and the warp sums are added in
+// warp order (deterministic).
+constexpr int kConvThreads = 256;
+__global__ void __launch_bounds__(kConvThreads) k_converge_cta(const int64_t* coff0, const float* part,
+                                                                float* prev, int32_t* skip, float tol,
+                                                                bool first, bool last, int32_t* info) {
+  const int64_t i = blockIdx.x;
+  if (skip[i]) return;   // uniform over the CTA
+  __shared__ float sd[kConvThreads / 32], sy[kConvThreads / 32];
+  float d2 = 0.f, y2 = 0.f;
+  for (int64_t g = coff0[i] + threadIdx.x; g < coff0[i + 1]; g += kConvThreads) {
+    d2 += part[2 * g];
+    y2 += part[2 * g + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    y2 += __shfl_xor_sync(0xffffffffu, y2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sd[threadIdx.x >> 5] = d2;
+    sy[threadIdx.x >> 5] = y2;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  d2 = sd[0];
+  y2 = sy[0];
+#pragma unroll
+  for (int w = 1; w < kConvThreads / 32; ++w) {
+    d2 += sd[w];
+    y2 += sy[w];
+  }
+  const bool conv = first ? d2 <= 1e-4f * tol * tol * y2 : d2 <= tol * sqrtf(y2 * prev[i]);
+  prev[i] = d2;
+  if (conv) skip[i] = 1;
+  else if (last && info[i] == 0) info[i] = -1;
+}
+
 // ---- refinement residual, in FP64 or float-float ------------------------------------
 template <class N> __device__ __forceinline__ N ld_n(float v) { return Num<N>::from_f(v); }
 template <class N> __device__ __forceinline__ N ld_n(double v) { return Num<N>::from_d(v); }
@@ -1466,6 +1506,7 @@ struct smnn_plan_s {
   int32_t* d_cta_sys = nullptr;
   int up = 0;                          // > 0: levels up..top in one launch (k_upper)
   bool wpass = false;                  // FP32 refined solves by k_wpass (one warp per system)
+  int64_t max_chunks0 = 0;             // most level-0 chunks of one system
   int pcr_m = -1;                      // >= 0: top level solved by warp PCR, 2^pcr_m lanes/system
   size_t o_pcr = 0;                    //   its multipliers and final factors (factor region)
   std::vector<int32_t> up_sys;         //   first system of each of its CTAs
@@ -1772,9 +1813,19 @@ smnn_status refine_sweeps(const smnn_plan_s* pl, const Problem0& p, char* fac, c
     Level0Out<float> oa{nullptr, xh, xl, adaptive ? b.part : nullptr, fresh};
     SMNN_TRY((solve_pass<float, NB, N, R1, Q>(pl, p, nullptr, false, fac, sol, oa, 2, info, st, &ri,
                                        adaptive ? b.skip : nullptr)));
-    if (adaptive)
+    // one warp per system while a lane sums at most 32 partials, a CTA per system beyond
+    if (adaptive && pl->max_chunks0 <= 32 * 32) {
       SMNN_LAUNCH(k_converge, pl->S * 32, st, pl->S, pl->lv[0].d_coff, b.part, b.prev, b.skip,
                   float(pl->desc.refine_tol), it == 0, it + 1 == K, info);
+    } else if (adaptive) {
+      prof_begin("k_converge", st);
+      k_converge_cta<<<unsigned(pl->S), kConvThreads, 0, st>>>(pl->lv[0].d_coff, b.part, b.prev, b.skip,
+                                                              float(pl->desc.refine_tol), it == 0,
+                                                              it + 1 == K, info);
+      prof_end(st);
+      count_launch();
+      if (cudaGetLastError() != cudaSuccess) return SMNN_ERR_CUDA;
+    }
   }
   return SMNN_OK;
 }
