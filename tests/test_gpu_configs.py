@@ -72,16 +72,13 @@ def test_config2_full_size_every_system():
 
 
 def test_config3b_full_size():
-    """T = 2^20, R = 3, s ~ U[0.1, 0.5]: the refined FP32 chunked-CR path."""
+    """T = 2^20, R = 3, s ~ U[0.1, 0.5]: the refined FP32 chunked-CR path (five levels, the
+    stop test one CTA per system), forward and adjoint, all 4 systems' y and gradients against
+    the oracle."""
     prob = config3b()
     out, gy, info, info_b = run_full(prob)
     assert (info == 0).all() and (info_b == 0).all()
-    sp = sub_uniform(prob, [0])
-    # one system through the oracle (T = 2^20 rows in memory per system)
-    one = Problem("one", 3, 2, 1, 1, 1, prob.T, sp.c[:, :1], sp.d[:, :1], sp.s, sp.u[:, :1])
-    yo, info_o = O.solve(oracle_params(one), one.c, one.d, one.s, one.u, nthreads=1)
-    assert info_o[0] == 0
-    assert rel_err(out["y"][0, 0], yo[0, 0]) <= TOL
+    check_uniform(prob, out, gy, [0])
 
 
 def test_config3_as_stated_fp64_and_detected_fp32_breakdown():
